@@ -1,0 +1,620 @@
+// CPU reference ("oracle") for the sparse-dense SDF volume renderer.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+// benchmark's CPU-baseline / reference arm load this library.  It is plain,
+// slow and single-threaded on purpose, written step by step from the paper
+// (arXiv 2305.13220, "Fast Monocular Scene Reconstruction with Global-Sparse
+// Local-Dense Grids"), and shares no source with the CUDA library.
+//
+// Precision: every step runs in FP64, except block activation (Eq. 7-8),
+// which runs in FP32 with a fixed operation order and no fused multiply-add
+// (build with -ffp-contract=off), because the block set it produces must be
+// bit-identical to what any FP32 implementation of the same order gives.
+//
+// Data layout conventions (these are interface, not code):
+//   * grid point (voxel) v in Z^3 sits at world position v * voxel_size;
+//   * block key b = floor(v / 8) per axis; local index v - 8b in [0,8)^3,
+//     stored at linear position lz*64 + ly*8 + lx inside the block;
+//   * block indices are assigned in ascending (z, y, x) key order per
+//     activation batch;
+//   * a ray record is 8 floats: ox, oy, oz, tnear, dx, dy, dz, tfar.
+//
+// Parity pins for every function live in tests/test_oracle_*.py.  Nothing
+// here is "parity unpinned".
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <set>
+#include <vector>
+
+namespace {
+
+struct BKey {
+    int32_t x, y, z;
+};
+// Ascending (z, y, x) order: the order in which an activation batch assigns indices.
+bool operator<(const BKey& a, const BKey& b) {
+    if (a.z != b.z) return a.z < b.z;
+    if (a.y != b.y) return a.y < b.y;
+    return a.x < b.x;
+}
+
+int64_t floordiv(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) q -= 1;
+    return q;
+}
+
+// ---------------------------------------------------------------------------
+// Grid: block map + dense 8^3 voxel arrays per block (Sec. 3.2, "Sparse-Dense
+// Data Structure").  The block map is an ordered map: exact, collision-free.
+// ---------------------------------------------------------------------------
+struct Grid {
+    double vs = 0.01;
+    double beta = 0.005;
+    int n_sem = 0;
+    std::map<BKey, int64_t> index;
+    std::vector<BKey> keys;
+    std::vector<double> sdf;  // [N][512]
+    std::vector<double> rgb;  // [N][512][3]
+    std::vector<double> sem;  // [N][512][n_sem]
+    int64_t lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};  // inclusive block AABB
+};
+
+// Voxel v -> linear storage index, or false if its block is not allocated.
+bool voxel_index(const Grid& g, int64_t vx, int64_t vy, int64_t vz, int64_t* lin, int64_t* blk) {
+    BKey k{(int32_t)floordiv(vx, 8), (int32_t)floordiv(vy, 8), (int32_t)floordiv(vz, 8)};
+    auto it = g.index.find(k);
+    if (it == g.index.end()) return false;
+    int64_t lx = vx - 8 * (int64_t)k.x, ly = vy - 8 * (int64_t)k.y, lz = vz - 8 * (int64_t)k.z;
+    *lin = it->second * 512 + lz * 64 + ly * 8 + lx;
+    if (blk) *blk = it->second;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Trilinear interpolation, Sec. 3.5.2 (f = sum_i r(x, x_i) theta(x_i) over the
+// 8 grid points around x).  A sample whose 8 grid points are not all in
+// allocated blocks is invalid.
+// ---------------------------------------------------------------------------
+struct Stencil {
+    bool valid;
+    int64_t lin[8];
+    int64_t blk[8];
+    double r[8];
+    double f[3];
+};
+
+Stencil stencil_at(const Grid& g, const double x[3]) {
+    Stencil s;
+    int64_t c[3];
+    for (int a = 0; a < 3; ++a) {
+        double gx = x[a] / g.vs;
+        double fl = std::floor(gx);
+        c[a] = (int64_t)fl;
+        s.f[a] = gx - fl;
+    }
+    s.valid = true;
+    for (int e = 0; e < 8; ++e) {
+        int ex = e & 1, ey = (e >> 1) & 1, ez = (e >> 2) & 1;
+        if (!voxel_index(g, c[0] + ex, c[1] + ey, c[2] + ez, &s.lin[e], &s.blk[e])) {
+            s.valid = false;
+            s.lin[e] = -1;
+            s.blk[e] = -1;
+        }
+        s.r[e] = (ex ? s.f[0] : 1.0 - s.f[0]) * (ey ? s.f[1] : 1.0 - s.f[1]) * (ez ? s.f[2] : 1.0 - s.f[2]);
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// SDF -> density, Sec. 3.5.1: alpha(x) = l(f(x)), the Laplace-CDF transform of
+// VolSDF: sigma(d) = (1/beta) * Psi_beta(-d), Psi_beta the CDF of Laplace(0,beta).
+// ---------------------------------------------------------------------------
+double laplace_cdf(double s, double beta) {
+    return s <= 0 ? 0.5 * std::exp(s / beta) : 1.0 - 0.5 * std::exp(-s / beta);
+}
+double density(double d, double beta) { return laplace_cdf(-d, beta) / beta; }
+double density_deriv(double d, double beta) {  // d sigma / d d = -(1/beta) * pdf(-d)
+    return -std::exp(-std::fabs(d) / beta) / (2.0 * beta * beta);
+}
+
+// ---------------------------------------------------------------------------
+// Counter-based uniform numbers for stratified sampling: the PCG integer hash
+// of Jarzynski & Olano, "Hash Functions for GPU Rendering" (JCGT 2020), nested
+// over (seed, ray, k); u = top 24 bits * 2^-24, exact in FP32 and FP64.
+// ---------------------------------------------------------------------------
+uint32_t pcg_hash(uint32_t v) {
+    uint32_t state = v * 747796405u + 2891336453u;
+    uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+uint32_t sample_hash(uint32_t seed, uint32_t ray, uint32_t k) {
+    return pcg_hash(k + pcg_hash(ray + pcg_hash(seed)));
+}
+double sample_u(uint32_t seed, uint32_t ray, uint32_t k) {
+    return (double)(sample_hash(seed, ray, k) >> 8) * (1.0 / 16777216.0);
+}
+
+// ---------------------------------------------------------------------------
+// Empty-space skipping (Sec. 3.5.1: samples only where blocks are allocated).
+// Brute force: every block-boundary plane crossing of the ray inside the
+// grid's AABB splits it into segments; a segment is kept if the block holding
+// its midpoint is allocated; touching kept segments are merged.
+// ---------------------------------------------------------------------------
+struct Interval {
+    double t_in, t_out;
+};
+
+bool clip_to_aabb(const Grid& g, const double o[3], const double d[3], double* t0, double* t1) {
+    if (g.keys.empty()) return false;
+    const double L = 8.0 * g.vs;
+    for (int a = 0; a < 3; ++a) {
+        double lo = g.lo[a] * L, hi = (g.hi[a] + 1) * L;
+        if (d[a] == 0.0) {
+            if (o[a] < lo || o[a] > hi) return false;
+            continue;
+        }
+        double ta = (lo - o[a]) / d[a], tb = (hi - o[a]) / d[a];
+        *t0 = std::max(*t0, std::min(ta, tb));
+        *t1 = std::min(*t1, std::max(ta, tb));
+    }
+    return *t0 < *t1;
+}
+
+std::vector<Interval> traverse(const Grid& g, const double o[3], const double d[3], double tn, double tf) {
+    std::vector<Interval> out;
+    double t0 = tn, t1 = tf;
+    if (!clip_to_aabb(g, o, d, &t0, &t1)) return out;
+    const double L = 8.0 * g.vs;
+    std::vector<double> ts{t0, t1};
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        double xa = o[a] + t0 * d[a], xb = o[a] + t1 * d[a];
+        int64_t m0 = (int64_t)std::ceil(std::min(xa, xb) / L);
+        int64_t m1 = (int64_t)std::floor(std::max(xa, xb) / L);
+        for (int64_t m = m0; m <= m1; ++m) {
+            double t = (m * L - o[a]) / d[a];
+            if (t > t0 && t < t1) ts.push_back(t);
+        }
+    }
+    std::sort(ts.begin(), ts.end());
+    for (size_t i = 0; i + 1 < ts.size(); ++i) {
+        double ta = ts[i], tb = ts[i + 1];
+        if (!(tb > ta)) continue;
+        double tm = 0.5 * (ta + tb);
+        BKey k;
+        k.x = (int32_t)std::floor((o[0] + tm * d[0]) / L);
+        k.y = (int32_t)std::floor((o[1] + tm * d[1]) / L);
+        k.z = (int32_t)std::floor((o[2] + tm * d[2]) / L);
+        if (g.index.find(k) == g.index.end()) continue;
+        if (!out.empty() && out.back().t_out == ta)
+            out.back().t_out = tb;
+        else
+            out.push_back({ta, tb});
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// One ray, forward: samples, interpolation, density, compositing (Eq. 12-15).
+// ---------------------------------------------------------------------------
+struct Sample {
+    double s, t, delta;
+    bool valid;
+    Stencil st;
+    double d, c[3];
+    std::vector<double> sem;
+    double sigma, tau, T, w;
+};
+
+struct RayResult {
+    std::vector<Sample> smp;
+    std::vector<Interval> iv;
+    double S = 0.0, TN = 1.0;
+    double C[3] = {0, 0, 0}, D = 0.0, O = 0.0;
+    std::vector<double> sem;
+    int n_valid = 0;
+    bool degenerate = false;
+};
+
+bool valid_at(const Grid& g, const double x[3]) { return stencil_at(g, x).valid; }
+
+RayResult render_ray(const Grid& g, const float* ray, int N, uint32_t seed, uint32_t ray_id, int stratified,
+                     const double bg[3]) {
+    RayResult R;
+    R.sem.assign(g.n_sem, 0.0);
+    double o[3] = {ray[0], ray[1], ray[2]}, d[3] = {ray[4], ray[5], ray[6]};
+    R.iv = traverse(g, o, d, ray[3], ray[7]);
+    for (auto& v : R.iv) R.S += v.t_out - v.t_in;
+    if (!(R.S > 0.0)) {
+        for (int c = 0; c < 3; ++c) R.C[c] = bg[c];
+        return R;
+    }
+    // interval starts in skip-space
+    std::vector<double> s_start(R.iv.size());
+    double acc = 0.0;
+    for (size_t i = 0; i < R.iv.size(); ++i) {
+        s_start[i] = acc;
+        acc += R.iv[i].t_out - R.iv[i].t_in;
+    }
+    R.smp.resize(N);
+    for (int k = 0; k < N; ++k) {
+        double u = stratified ? sample_u(seed, ray_id, (uint32_t)k) : 0.5;
+        R.smp[k].s = ((double)k + u) * R.S / (double)N;
+    }
+    for (int k = 0; k < N; ++k) {
+        Sample& sm = R.smp[k];
+        sm.delta = (k + 1 < N ? R.smp[k + 1].s : R.S) - sm.s;
+        size_t i = 0;
+        while (i + 1 < R.iv.size() && sm.s >= s_start[i + 1]) ++i;
+        sm.t = R.iv[i].t_in + (sm.s - s_start[i]);
+        double x[3] = {o[0] + sm.t * d[0], o[1] + sm.t * d[1], o[2] + sm.t * d[2]};
+        sm.st = stencil_at(g, x);
+        sm.valid = sm.st.valid;
+        sm.d = 0.0;
+        sm.c[0] = sm.c[1] = sm.c[2] = 0.0;
+        sm.sem.assign(g.n_sem, 0.0);
+        if (sm.valid) {
+            for (int e = 0; e < 8; ++e) {
+                int64_t li = sm.st.lin[e];
+                sm.d += sm.st.r[e] * g.sdf[li];
+                for (int c = 0; c < 3; ++c) sm.c[c] += sm.st.r[e] * g.rgb[li * 3 + c];
+                for (int c = 0; c < g.n_sem; ++c) sm.sem[c] += sm.st.r[e] * g.sem[li * g.n_sem + c];
+            }
+            R.n_valid++;
+        }
+        sm.sigma = sm.valid ? density(sm.d, g.beta) : 0.0;
+        sm.tau = sm.sigma * sm.delta;
+        // degeneracy: a sample next to a skip-space joint, or whose validity flips under a tiny nudge
+        for (size_t j = 1; j < R.iv.size(); ++j)
+            if (std::fabs(sm.s - s_start[j]) < 1e-5) R.degenerate = true;
+        const double eg = 5e-4 * g.vs;
+        for (int a = 0; a < 3 && !R.degenerate; ++a)
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                double y[3] = {x[0], x[1], x[2]};
+                y[a] += sgn * eg;
+                if (valid_at(g, y) != sm.valid) R.degenerate = true;
+            }
+    }
+    double cum = 0.0;
+    for (int k = 0; k < N; ++k) {
+        Sample& sm = R.smp[k];
+        sm.T = std::exp(-cum);
+        sm.w = sm.T * (1.0 - std::exp(-sm.tau));
+        cum += sm.tau;
+        for (int c = 0; c < 3; ++c) R.C[c] += sm.w * sm.c[c];
+        R.D += sm.w * sm.t;
+        R.O += sm.w;
+        for (int c = 0; c < g.n_sem; ++c) R.sem[c] += sm.w * sm.sem[c];
+    }
+    R.TN = std::exp(-cum);
+    for (int c = 0; c < 3; ++c) R.C[c] += R.TN * bg[c];
+    return R;
+}
+
+}  // namespace
+
+extern "C" {
+
+// ----------------------------- activation ----------------------------------
+// Eq. 8 with phi = 1: x = R * Pi^-1(p, D(p)) + t, in FP32 with this exact order:
+//   xc = ((u + 0.5f) - cx) * (1/fx) * d ; yc likewise ; zc = d
+//   x_i = ((R_i0*xc + R_i1*yc) + R_i2*zc) + t_i
+// Pixels with a non-finite or non-positive depth are marked invalid.
+int64_t orc_unproject(const float* depth, int H, int W, const float* K, const float* T, float* xyz,
+                      uint8_t* valid) {
+    const float ifx = 1.0f / K[0], ify = 1.0f / K[1];
+    int64_t nv = 0;
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            int64_t i = (int64_t)v * W + u;
+            float d = depth[i];
+            bool ok = std::isfinite(d) && d > 0.0f;
+            valid[i] = ok ? 1 : 0;
+            float xc = (((float)u + 0.5f) - K[2]) * ifx * d;
+            float yc = (((float)v + 0.5f) - K[3]) * ify * d;
+            float zc = d;
+            for (int a = 0; a < 3; ++a) {
+                float p0 = T[a * 4 + 0] * xc;
+                float p1 = T[a * 4 + 1] * yc;
+                float p2 = T[a * 4 + 2] * zc;
+                xyz[i * 3 + a] = ((p0 + p1) + p2) + T[a * 4 + 3];
+            }
+            nv += ok;
+        }
+    return nv;
+}
+
+void* orc_keyset_new() { return new std::set<BKey>(); }
+void orc_keyset_free(void* ks) { delete (std::set<BKey>*)ks; }
+
+// Eq. 7: union over points of the blocks touched by the voxel cube v + [-r, r]^3,
+// v = floor(x * (1/vs)) in FP32.  The blocks touched along one axis are the
+// integers floor((v-r)/8) .. floor((v+r)/8), so the union is a product of three
+// ranges.  r = 8R reproduces the block dilation Dilate_R of the supplement exactly.
+void orc_keyset_add_points(void* ks, const float* xyz, const uint8_t* valid, int64_t n, float vs, int r) {
+    auto* S = (std::set<BKey>*)ks;
+    const float inv = 1.0f / vs;
+    for (int64_t i = 0; i < n; ++i) {
+        if (valid && !valid[i]) continue;
+        int64_t v[3];
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+            float q = xyz[i * 3 + a] * inv;
+            if (!std::isfinite(q) || std::fabs(q) > 8.0e6f) ok = false;
+            v[a] = ok ? (int64_t)std::floor(q) : 0;
+        }
+        if (!ok) continue;
+        int64_t b0[3], b1[3];
+        for (int a = 0; a < 3; ++a) {
+            b0[a] = floordiv(v[a] - r, 8);
+            b1[a] = floordiv(v[a] + r, 8);
+        }
+        for (int64_t z = b0[2]; z <= b1[2]; ++z)
+            for (int64_t y = b0[1]; y <= b1[1]; ++y)
+                for (int64_t x = b0[0]; x <= b1[0]; ++x) S->insert(BKey{(int32_t)x, (int32_t)y, (int32_t)z});
+    }
+}
+
+int64_t orc_keyset_size(void* ks) { return (int64_t)((std::set<BKey>*)ks)->size(); }
+
+void orc_keyset_get(void* ks, int32_t* out) {
+    int64_t i = 0;
+    for (const BKey& k : *(std::set<BKey>*)ks) {
+        out[i * 3 + 0] = k.x;
+        out[i * 3 + 1] = k.y;
+        out[i * 3 + 2] = k.z;
+        ++i;
+    }
+}
+
+// ------------------------------- grid --------------------------------------
+void* orc_grid_new(double vs, double beta, int n_sem) {
+    Grid* g = new Grid();
+    g->vs = vs;
+    g->beta = beta;
+    g->n_sem = n_sem;
+    return g;
+}
+void orc_grid_free(void* g) { delete (Grid*)g; }
+
+// Blocks keys[i] get index i; the voxel arrays are copied.
+int orc_grid_set(void* gp, const int32_t* keys, int64_t N, const double* sdf, const double* rgb, const double* sem) {
+    Grid* g = (Grid*)gp;
+    g->index.clear();
+    g->keys.resize(N);
+    for (int a = 0; a < 3; ++a) {
+        g->lo[a] = INT64_MAX;
+        g->hi[a] = INT64_MIN;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        BKey k{keys[i * 3], keys[i * 3 + 1], keys[i * 3 + 2]};
+        if (!g->index.emplace(k, i).second) return -1;  // duplicate key
+        g->keys[i] = k;
+        int32_t c[3] = {k.x, k.y, k.z};
+        for (int a = 0; a < 3; ++a) {
+            g->lo[a] = std::min<int64_t>(g->lo[a], c[a]);
+            g->hi[a] = std::max<int64_t>(g->hi[a], c[a]);
+        }
+    }
+    g->sdf.assign(sdf, sdf + N * 512);
+    g->rgb.assign(rgb, rgb + N * 512 * 3);
+    if (g->n_sem) g->sem.assign(sem, sem + N * 512 * g->n_sem);
+    return 0;
+}
+
+void orc_grid_lookup(void* gp, const int32_t* keys, int64_t n, int32_t* idx) {
+    Grid* g = (Grid*)gp;
+    for (int64_t i = 0; i < n; ++i) {
+        auto it = g->index.find(BKey{keys[i * 3], keys[i * 3 + 1], keys[i * 3 + 2]});
+        idx[i] = it == g->index.end() ? -1 : (int32_t)it->second;
+    }
+}
+
+// Allocated intervals of one ray (merged), at most cap of them; returns the count.
+int orc_traverse(void* gp, const float* ray, double* t_in, double* t_out, int cap) {
+    Grid* g = (Grid*)gp;
+    double o[3] = {ray[0], ray[1], ray[2]}, d[3] = {ray[4], ray[5], ray[6]};
+    auto iv = traverse(*g, o, d, ray[3], ray[7]);
+    int n = (int)iv.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        t_in[i] = iv[i].t_in;
+        t_out[i] = iv[i].t_out;
+    }
+    return n;
+}
+
+uint32_t orc_sample_hash(uint32_t seed, uint32_t ray, uint32_t k) { return sample_hash(seed, ray, k); }
+double orc_sample_u(uint32_t seed, uint32_t ray, uint32_t k) { return sample_u(seed, ray, k); }
+double orc_density(double d, double beta) { return density(d, beta); }
+double orc_density_deriv(double d, double beta) { return density_deriv(d, beta); }
+
+// Trilinear query of all channels at points x (n,3): sdf (n), rgb (n,3), valid (n).
+void orc_query(void* gp, const double* x, int64_t n, double* sdf, double* rgb, uint8_t* valid) {
+    Grid* g = (Grid*)gp;
+    for (int64_t i = 0; i < n; ++i) {
+        Stencil s = stencil_at(*g, x + 3 * i);
+        valid[i] = s.valid;
+        double dd = 0, c[3] = {0, 0, 0};
+        if (s.valid)
+            for (int e = 0; e < 8; ++e) {
+                dd += s.r[e] * g->sdf[s.lin[e]];
+                for (int a = 0; a < 3; ++a) c[a] += s.r[e] * g->rgb[s.lin[e] * 3 + a];
+            }
+        sdf[i] = dd;
+        for (int a = 0; a < 3; ++a) rgb[i * 3 + a] = c[a];
+    }
+}
+
+// Forward render of n rays (ray i uses hash id ray_id0 + i).  diag[i] = {S, n_valid, degenerate, T_N}.
+void orc_render(void* gp, const float* rays, int64_t n, int N, uint32_t seed, uint32_t ray_id0, int stratified,
+                const double* bg, double* rgb, double* depth, double* opac, double* sem, double* diag) {
+    Grid* g = (Grid*)gp;
+    for (int64_t i = 0; i < n; ++i) {
+        RayResult R = render_ray(*g, rays + 8 * i, N, seed, ray_id0 + (uint32_t)i, stratified, bg);
+        for (int c = 0; c < 3; ++c) rgb[i * 3 + c] = R.C[c];
+        depth[i] = R.D;
+        opac[i] = R.O;
+        if (sem)
+            for (int c = 0; c < g->n_sem; ++c) sem[i * g->n_sem + c] = R.sem[c];
+        if (diag) {
+            diag[i * 4 + 0] = R.S;
+            diag[i * 4 + 1] = R.n_valid;
+            diag[i * 4 + 2] = R.degenerate ? 1.0 : 0.0;
+            diag[i * 4 + 3] = R.TN;
+        }
+    }
+}
+
+// Per-sample trace of one ray: out[k] = {s, t, delta, valid, d, sigma, T, w}.
+int orc_trace(void* gp, const float* ray, int N, uint32_t seed, uint32_t ray_id, int stratified, double* out) {
+    Grid* g = (Grid*)gp;
+    double bg[3] = {0, 0, 0};
+    RayResult R = render_ray(*g, ray, N, seed, ray_id, stratified, bg);
+    for (int k = 0; k < (int)R.smp.size(); ++k) {
+        const Sample& s = R.smp[k];
+        double row[8] = {s.s, s.t, s.delta, s.valid ? 1.0 : 0.0, s.d, s.sigma, s.T, s.w};
+        std::memcpy(out + 8 * k, row, sizeof(row));
+    }
+    return (int)R.smp.size();
+}
+
+// Backward: accumulates dL/dtheta (+=) for L = sum_i g_rgb_i.C_i + g_depth_i D_i + g_opac_i O_i + g_sem_i.Sem_i.
+// Derivation of Eq. 15 w.r.t. tau_k = sigma_k delta_k (T_k = exp(-sum_{j<k} tau_j)):
+//   dL/dtau_k = T_{k+1} v_k - sum_{j>k} w_j v_j - T_N (g_rgb . bg),   v_k = g_rgb.c_k + g_depth t_k + g_opac + g_sem.s_k
+//   dL/dd_k   = delta_k sigma'(d_k) dL/dtau_k ;  dL/dc_k = w_k g_rgb ;  dL/ds_k = w_k g_sem
+// and the trilinear weights r_e scatter each onto the 8 grid points (Sec. 3.5.2).
+void orc_render_backward(void* gp, const float* rays, int64_t n, int N, uint32_t seed, uint32_t ray_id0,
+                         int stratified, const double* bg, const double* g_rgb, const double* g_depth,
+                         const double* g_opac, const double* g_sem, double* grad_sdf, double* grad_rgb,
+                         double* grad_sem) {
+    Grid* g = (Grid*)gp;
+    const int ns = g->n_sem;
+    for (int64_t i = 0; i < n; ++i) {
+        RayResult R = render_ray(*g, rays + 8 * i, N, seed, ray_id0 + (uint32_t)i, stratified, bg);
+        if (R.smp.empty()) continue;
+        const double* gc = g_rgb + 3 * i;
+        double gd = g_depth ? g_depth[i] : 0.0, go = g_opac ? g_opac[i] : 0.0;
+        const double* gs = (ns && g_sem) ? g_sem + (int64_t)ns * i : nullptr;
+        std::vector<double> v(N);
+        for (int k = 0; k < N; ++k) {
+            const Sample& s = R.smp[k];
+            double vk = gd * s.t + go;
+            for (int c = 0; c < 3; ++c) vk += gc[c] * s.c[c];
+            if (gs)
+                for (int c = 0; c < ns; ++c) vk += gs[c] * s.sem[c];
+            v[k] = vk;
+        }
+        double ubg = gc[0] * bg[0] + gc[1] * bg[1] + gc[2] * bg[2];
+        double suffix = 0.0;  // sum_{j>k} w_j v_j
+        for (int k = N - 1; k >= 0; --k) {
+            const Sample& s = R.smp[k];
+            double dtau = s.T * std::exp(-s.tau) * v[k] - suffix - R.TN * ubg;
+            suffix += s.w * v[k];
+            if (!s.valid) continue;
+            double dd = s.delta * density_deriv(s.d, g->beta) * dtau;
+            for (int e = 0; e < 8; ++e) {
+                int64_t li = s.st.lin[e];
+                double r = s.st.r[e];
+                grad_sdf[li] += r * dd;
+                for (int c = 0; c < 3; ++c) grad_rgb[li * 3 + c] += r * s.w * gc[c];
+                if (gs)
+                    for (int c = 0; c < ns; ++c) grad_sem[li * ns + c] += r * s.w * gs[c];
+            }
+        }
+    }
+}
+
+// Distinct voxels and blocks read by each ray's valid-sample stencils (algorithmic byte count).
+void orc_count_touched(void* gp, const float* rays, int64_t n, int N, uint32_t seed, uint32_t ray_id0,
+                       int stratified, int64_t* voxels, int64_t* blocks) {
+    Grid* g = (Grid*)gp;
+    double bg[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        RayResult R = render_ray(*g, rays + 8 * i, N, seed, ray_id0 + (uint32_t)i, stratified, bg);
+        std::set<int64_t> vx, bl;
+        for (const Sample& s : R.smp)
+            if (s.valid)
+                for (int e = 0; e < 8; ++e) {
+                    vx.insert(s.st.lin[e]);
+                    bl.insert(s.st.blk[e]);
+                }
+        voxels[i] = (int64_t)vx.size();
+        blocks[i] = (int64_t)bl.size();
+    }
+}
+
+// Rendering losses (Eq. 12-13 as configured): L1 colour (mean over rays and channels), lam_d * L1 depth
+// (mean over rays, scale a = 1, shift b = 0), lam_s * squared L2 of semantic logits (mean over rays).
+// Writes the gradient seeds and returns the loss.  sign(0) = 0.
+double orc_loss(int64_t n, int n_sem, const double* rgb, const double* depth, const double* sem, const double* t_rgb,
+                const double* t_depth, const double* t_sem, double lam_d, double lam_s, double* g_rgb,
+                double* g_depth, double* g_sem) {
+    double L = 0.0;
+    auto sgn = [](double x) { return (double)((x > 0) - (x < 0)); };
+    for (int64_t i = 0; i < n; ++i) {
+        for (int c = 0; c < 3; ++c) {
+            double e = rgb[i * 3 + c] - t_rgb[i * 3 + c];
+            L += std::fabs(e) / (3.0 * n);
+            g_rgb[i * 3 + c] = sgn(e) / (3.0 * n);
+        }
+        double e = depth[i] - t_depth[i];
+        L += lam_d * std::fabs(e) / n;
+        g_depth[i] = lam_d * sgn(e) / n;
+        for (int c = 0; c < n_sem; ++c) {
+            double es = sem[i * n_sem + c] - t_sem[i * n_sem + c];
+            L += lam_s * es * es / n;
+            g_sem[i * n_sem + c] = 2.0 * lam_s * es / n;
+        }
+    }
+    return L;
+}
+
+// Adam (Kingma & Ba) with bias correction, step = 1, 2, ...; the gradient is zeroed afterwards.
+void orc_adam(double* theta, double* grad, double* m, double* v, int64_t n, double lr, double b1, double b2,
+              double eps, int step) {
+    double c1 = 1.0 - std::pow(b1, step), c2 = 1.0 - std::pow(b2, step);
+    for (int64_t i = 0; i < n; ++i) {
+        double gi = grad[i];
+        m[i] = b1 * m[i] + (1.0 - b1) * gi;
+        v[i] = b2 * v[i] + (1.0 - b2) * gi * gi;
+        double mh = m[i] / c1, vh = v[i] / c2;
+        theta[i] -= lr * mh / (std::sqrt(vh) + eps);
+        grad[i] = 0.0;
+    }
+}
+
+// RMSProp as the paper states for refinement (Sec. 3.5.4): v = a v + (1-a) g^2, theta -= lr g / (sqrt(v) + eps).
+void orc_rmsprop(double* theta, double* grad, double* v, int64_t n, double lr, double alpha, double eps) {
+    for (int64_t i = 0; i < n; ++i) {
+        double gi = grad[i];
+        v[i] = alpha * v[i] + (1.0 - alpha) * gi * gi;
+        theta[i] -= lr * gi / (std::sqrt(v[i]) + eps);
+        grad[i] = 0.0;
+    }
+}
+
+// Pinhole rays of one H x W view (serve requests): o = t, d = normalize(R * ((u+0.5-cx)/fx, (v+0.5-cy)/fy, 1)).
+void orc_view_rays(int H, int W, const double* K, const double* T, float tnear, float tfar, float* rays) {
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            double dc[3] = {((double)u + 0.5 - K[2]) / K[0], ((double)v + 0.5 - K[3]) / K[1], 1.0};
+            double dw[3];
+            for (int a = 0; a < 3; ++a) dw[a] = T[a * 4] * dc[0] + T[a * 4 + 1] * dc[1] + T[a * 4 + 2] * dc[2];
+            double nn = std::sqrt(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+            float* r = rays + 8 * ((int64_t)v * W + u);
+            r[0] = (float)T[3];
+            r[1] = (float)T[7];
+            r[2] = (float)T[11];
+            r[3] = tnear;
+            r[4] = (float)(dw[0] / nn);
+            r[5] = (float)(dw[1] / nn);
+            r[6] = (float)(dw[2] / nn);
+            r[7] = tfar;
+        }
+}
+
+}  // extern "C"

@@ -1,0 +1,59 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake (a dropped term, a wrong sign or factor, a
+transposed operand, truncation instead of floor) in a copy of the oracle's
+C++ source, builds that copy, and checks that at least one of the pins for
+that step now fails.  The planted mistakes live only in temporary copies on
+the CPU."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import test_oracle_activation as A
+from tests import test_oracle_render as R
+
+MUTANTS = [
+    ("laplace_factor", "? 0.5 * std::exp(s / beta) :", "? std::exp(s / beta) :",
+     [R.test_laplace_density_closed_forms]),
+    ("trilinear_swap", "(ex ? s.f[0] : 1.0 - s.f[0])", "(ex ? 1.0 - s.f[0] : s.f[0])",
+     [R.test_trilinear_reproduces_linear_field]),
+    ("bwd_drop_suffix", "* v[k] - suffix - R.TN * ubg;", "* v[k] - R.TN * ubg;",
+     [lambda: R.test_backward_matches_central_differences(0, (0, 0, 0))]),
+    ("bwd_bg_sign", "* v[k] - suffix - R.TN * ubg;", "* v[k] - suffix + R.TN * ubg;",
+     [lambda: R.test_backward_matches_central_differences(4, (0.3, 0.6, 0.1))]),
+    ("activation_trunc", "v[a] = ok ? (int64_t)std::floor(q) : 0;", "v[a] = ok ? (int64_t)q : 0;",
+     [A.test_activation_floor_semantics_by_hand]),
+    ("unproject_transpose", "float p1 = T[a * 4 + 1] * yc;", "float p1 = T[1 * 4 + a] * yc;",
+     [A.test_unprojected_points_lie_on_the_surface]),
+    ("last_delta", "(k + 1 < N ? R.smp[k + 1].s : R.S)", "(k + 1 < N ? R.smp[k + 1].s : sm.s)",
+     [R.test_stratified_sampling_and_deltas]),
+    ("inclusive_transmittance", "sm.T = std::exp(-cum);\n        sm.w", "sm.T = std::exp(-cum - sm.tau);\n        sm.w",
+     [lambda: R.test_plane_depth_matches_quadrature_and_converges(0.01)]),
+    ("adam_no_bias_correction", "double mh = m[i] / c1,", "double mh = m[i],",
+     [R.test_adam_step_one_closed_form_and_torch]),
+    ("traverse_start_point", "double tm = 0.5 * (ta + tb);", "double tm = ta;",
+     [R.test_traversal_matches_dense_classification]),
+    ("dilation_off_by_one", "b1[a] = floordiv(v[a] + r, 8);", "b1[a] = floordiv(v[a] + r - 1, 8);",
+     [lambda: A.test_activation_matches_voxel_cube_enumeration(3)]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, old, new, pins, tmp_path):
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mutated = tmp_path / f"{name}.cpp"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / f"lib{name}.so"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", str(mutated),
+                           "-o", str(so)])
+    with oracle.use_library(str(so)):
+        caught = False
+        for pin in pins:
+            try:
+                pin()
+            except AssertionError:
+                caught = True
+        assert caught, f"no pin caught the planted mistake {name}"
