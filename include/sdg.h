@@ -1,0 +1,357 @@
+/*
+ * sdg.h -- C ABI of libsdg: differentiable volume rendering of an SDF (with
+ * colour and semantic channels) stored in a globally sparse, locally dense
+ * voxel-block grid, on one NVIDIA B300 (sm_103a).
+ *
+ * Paper: "Fast Monocular Scene Reconstruction with Global-Sparse Local-Dense
+ * Grids" (arXiv 2305.13220).  Each entry point cites the passage that defines
+ * the operation it performs.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  * Every call returns an int status (SDG_OK = 0 or an SDG_ERR_* code); no
+ *    exception crosses the ABI.  sdg_last_error() returns a thread-local
+ *    message for the last failing call of the calling thread.
+ *  * Pointers named *_dev are device pointers on the grid's device; all other
+ *    pointers are host pointers.  Device arrays are dense and row-major, FP32
+ *    unless stated.  The caller owns every buffer it passes in and must keep
+ *    it alive until the work enqueued on the grid's stream has finished.
+ *  * The grid owns its hash table, voxel channels, gradients, optimiser
+ *    state, neighbour table and occupancy bitmap.  sdg_grid_channel exposes
+ *    channels zero-copy; those pointers stay valid until sdg_grid_destroy.
+ *  * All work is enqueued on the stream given in sdg_grid_desc.  Calls are
+ *    asynchronous, except those that return a count to the host
+ *    (activation's n_new, sdg_grid_num_blocks) and save/load, which
+ *    synchronise that stream.
+ *  * Voxel layout: grid point (voxel) v in Z^3 sits at world position
+ *    v * voxel_size.  Its block key is b = floor(v / 8) per axis, its local
+ *    coordinate l = v - 8b in [0,8)^3, stored at linear position
+ *    lz*64 + ly*8 + lx inside block index i, i.e. element i*512 + that.
+ *  * Block indices are dense in [0, num_blocks).  Each activation batch
+ *    appends its new blocks after the existing ones, in ascending
+ *    (z, y, x) key order.
+ *  * Ray records are 8 floats: ox, oy, oz, tnear, dx, dy, dz, tfar.
+ *  * Block keys are limited to [-2^20, 2^20) per axis.
+ */
+#ifndef SDG_H
+#define SDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------------- */
+/* Status codes                                                             */
+/* ----------------------------------------------------------------------- */
+#define SDG_OK 0
+#define SDG_ERR_ARG 1       /* invalid argument (null pointer, bad size, wrong layout) */
+#define SDG_ERR_OOM 2       /* a device or host allocation failed */
+#define SDG_ERR_CAPACITY 3  /* a fixed capacity would be exceeded; the object is unchanged */
+#define SDG_ERR_CUDA 4      /* a CUDA runtime call or kernel launch failed */
+#define SDG_ERR_TIMEOUT 5   /* a wait ran out of time */
+#define SDG_ERR_BUSY 6      /* the result is not ready yet (poll again) */
+#define SDG_ERR_IO 7        /* file read/write failed or the file is malformed */
+#define SDG_ERR_NOT_FOUND 8 /* unknown ticket / scene id */
+
+/* Storage types of the colour channel. */
+#define SDG_F32 0
+#define SDG_BF16 1
+
+/* Channel groups (sdg_grid_channel). */
+#define SDG_GROUP_GEO 0    /* SDG_F32 grids: float4 {sdf, r, g, b} per voxel, [max_blocks][512][4] */
+#define SDG_GROUP_SDF 1    /* SDG_BF16 grids: float sdf, [max_blocks][512] */
+#define SDG_GROUP_RGB 2    /* SDG_BF16 grids: bfloat16 {r, g, b, 0}, [max_blocks][512][4] */
+#define SDG_GROUP_SEM 3    /* bfloat16 semantic logits, [max_blocks][512][n_sem] (n_sem > 0 only) */
+#define SDG_GROUP_WEIGHT 4 /* float fusion weight, [max_blocks][512] (not read by the renderer) */
+
+/* Channel kinds. */
+#define SDG_KIND_VALUE 0
+#define SDG_KIND_GRAD 1   /* float, same element count as the value (the RGB group keeps 4 lanes) */
+#define SDG_KIND_ADAM_M 2 /* float first moment (unused by RMSProp) */
+#define SDG_KIND_ADAM_V 3 /* float second moment (RMSProp's running mean of g^2) */
+
+/* Backward modes (sdg_render_opts.mode). */
+#define SDG_MODE_RECOMPUTE 0 /* backward re-traverses and re-samples each ray: O(rays) saved state */
+#define SDG_MODE_STORE 1     /* forward keeps every sample's position and values for the backward */
+
+/* Optimisers (sdg_adam_opts.algo). */
+#define SDG_OPT_ADAM 0
+#define SDG_OPT_RMSPROP 1
+
+typedef struct sdg_grid_s* sdg_grid;
+typedef struct sdg_ctx_s* sdg_ctx;
+typedef struct sdg_server_s* sdg_server;
+
+/* ----------------------------------------------------------------------- */
+/* Grid                                                                     */
+/* ----------------------------------------------------------------------- */
+
+/* Sec. 3.2 ("Sparse-Dense Data Structure"): voxels exist only inside
+ * allocated 8^3 blocks, indexed by a collision-free hash map; each voxel
+ * stores an SDF (theta_d), a colour (theta_c) and optionally semantic logits
+ * (theta_s).  Sec. 4.1 uses 8^3 blocks. */
+typedef struct {
+    float voxel_size;   /* metres, > 0 */
+    float beta;         /* Laplace scale of the SDF-to-density transform (Sec. 3.5.1), metres;
+                           <= 0 selects voxel_size / 2 */
+    int64_t max_blocks; /* block capacity; every per-block array is allocated for it up front */
+    int32_t rgb_dtype;  /* SDG_F32 or SDG_BF16 */
+    int32_t n_sem;      /* semantic channels per voxel: 0 or a multiple of 4, at most 32 */
+    int32_t device;     /* CUDA device ordinal */
+    int32_t reserved;   /* must be 0 */
+    void* stream;       /* cudaStream_t for all work on this grid; NULL = the legacy default stream */
+} sdg_grid_desc;
+
+/* Creates an empty grid; all channels, gradients and optimiser state start at zero.
+ * Errors: SDG_ERR_ARG (bad descriptor), SDG_ERR_OOM, SDG_ERR_CUDA. */
+int sdg_grid_create(const sdg_grid_desc* desc, sdg_grid* out);
+
+/* Frees every device buffer the grid owns.  Safe on NULL. */
+int sdg_grid_destroy(sdg_grid g);
+
+/* Block activation, Sec. 3.4.1 Eq. 7-8 (phi = 1): for every point x, the
+ * voxel v = floor(x * (1/voxel_size)) (FP32, (1/voxel_size) rounded to FP32)
+ * is grown to the cube v + [-dilate_voxels, dilate_voxels]^3 and every block
+ * touched by that cube is activated.  dilate_voxels = 8R reproduces the
+ * supplement's block dilation Dilate_R exactly (R = 2 in the paper).
+ * xyz_dev: [n][3] float device points.  Points whose scaled coordinates are
+ * non-finite or beyond 8e6 voxels are skipped.  0 <= dilate_voxels <= 64.
+ * n_new (host, may be NULL): number of blocks added.  Synchronises.
+ * All-or-nothing: on SDG_ERR_CAPACITY (more than max_blocks in total) the
+ * grid is unchanged. */
+int sdg_grid_activate_points(sdg_grid g, const float* xyz_dev, int64_t n, int32_t dilate_voxels, int64_t* n_new);
+
+/* Same as sdg_grid_activate_points on the points of a depth map, unprojected
+ * per Eq. 8 with this exact FP32 operation order (no fused multiply-add):
+ *   xc = (((u + 0.5f) - cx) * (1/fx)) * d;  yc = (((v + 0.5f) - cy) * (1/fy)) * d;  zc = d
+ *   x_i = ((Twc[i][0]*xc + Twc[i][1]*yc) + Twc[i][2]*zc) + Twc[i][3]
+ * depth_dev: [H][W] float z-depth; pixels with non-finite or non-positive
+ * depth are skipped.  K (host): fx, fy, cx, cy.  Twc (host): row-major 3x4
+ * camera-to-world.  Synchronises; all-or-nothing like activate_points. */
+int sdg_grid_activate_depth(sdg_grid g, const float* depth_dev, int32_t H, int32_t W, const float K[4],
+                            const float Twc[12], int32_t dilate_voxels, int64_t* n_new);
+
+/* Activates an explicit list of block keys keys_dev [n][3] int32 (duplicates
+ * and already active keys allowed).  Synchronises; all-or-nothing. */
+int sdg_grid_activate_keys(sdg_grid g, const int32_t* keys_dev, int64_t n, int64_t* n_new);
+
+/* Number of active blocks (host).  Synchronises. */
+int sdg_grid_num_blocks(sdg_grid g, int64_t* n);
+
+/* Copies the active keys, in index order, to keys_dev [num_blocks][3] int32. */
+int sdg_grid_keys(sdg_grid g, int32_t* keys_dev);
+
+/* Hash-map lookup (Sec. 3.2, the collision-free block index): keys_dev [n][3]
+ * int32 -> idx_dev [n] int32 block index, -1 if the block is not active. */
+int sdg_grid_lookup(sdg_grid g, const int32_t* keys_dev, int64_t n, int32_t* idx_dev);
+
+/* Zero-copy view of one channel: *dev_ptr and its size in bytes (for
+ * max_blocks blocks; only the first num_blocks are meaningful).
+ * SDG_ERR_ARG if the group/kind does not exist in this grid's layout. */
+int sdg_grid_channel(sdg_grid g, int32_t group, int32_t kind, void** dev_ptr, int64_t* bytes);
+
+/* Sets every gradient channel to zero (enqueued). */
+int sdg_grid_zero_grad(sdg_grid g);
+
+/* Writes / reads the grid: header (voxel size, beta, layout, block count,
+ * optimiser step), keys in index order, then every value, gradient and
+ * optimiser-state channel of the active blocks.  Load creates a new grid; a
+ * non-NULL desc overrides device, stream and max_blocks (which must be at
+ * least the stored block count).  Both synchronise.  SDG_ERR_IO on failure. */
+int sdg_grid_save(sdg_grid g, const char* path);
+int sdg_grid_load(const char* path, const sdg_grid_desc* desc, sdg_grid* out);
+
+/* Optimiser step counter kept with the grid (saved and loaded with it). */
+int sdg_grid_get_step(sdg_grid g, int32_t* step);
+int sdg_grid_set_step(sdg_grid g, int32_t step);
+
+/* Blocks the host until all work on the grid's stream has finished. */
+int sdg_grid_sync(sdg_grid g);
+
+/* ----------------------------------------------------------------------- */
+/* Rendering                                                                */
+/* ----------------------------------------------------------------------- */
+
+/* Sec. 3.5.1, Eq. 12-15.  For each ray x(t) = o + t d on [tnear, tfar]
+ * (clipped to the box of active blocks), the allocated stretches
+ * [t_in, t_out) are found by a block-level traversal that skips
+ * unallocated space; their total length S defines a skip-space coordinate
+ * s.  Sample k of N sits at s_k = (k + u_k) S / N (u_k = 0.5, or a PCG hash
+ * of (seed, ray_id0 + ray, k) when stratified), mapped back to t_k.
+ * delta_k = s_{k+1} - s_k, delta_{N-1} = S - s_{N-1}.  At each sample the
+ * SDF, colour and logits are trilinear interpolations of the 8 surrounding
+ * voxels (Eq. 17); a sample whose 8 voxels are not all allocated is invalid
+ * (density 0, no gradient).  Density: sigma = Psi_beta(-d) / beta (the
+ * Laplace CDF transform of VolSDF).  Weights w_k = T_k (1 - exp(-sigma_k
+ * delta_k)), T_k = exp(-sum_{j<k} sigma_j delta_j) (Eq. 15).  Outputs per
+ * ray: rgb = sum w c + T_N bg, depth = sum w t, opac = sum w, sem = sum w s. */
+typedef struct {
+    int32_t n_samples;  /* N per ray, 1..512 */
+    uint32_t seed;      /* stratification seed */
+    uint32_t ray_id0;   /* hash id of ray 0 of this call (ray i uses ray_id0 + i) */
+    int32_t stratified; /* 1: jittered u_k; 0: u_k = 0.5 */
+    int32_t mode;       /* SDG_MODE_RECOMPUTE or SDG_MODE_STORE */
+    float bg[3];        /* background colour, weighted by T_N */
+} sdg_render_opts;
+
+typedef struct {
+    float* rgb;   /* [n][3] device */
+    float* depth; /* [n] device */
+    float* opac;  /* [n] device */
+    float* sem;   /* [n][n_sem] device, or NULL to skip the semantic output */
+} sdg_render_out;
+
+/* Forward render of n rays (rays_dev [n][8]).  When ctx is non-NULL, a
+ * context for sdg_render_backward is returned; it refers to rays_dev, which
+ * must stay unchanged until the backward has run.  In SDG_MODE_STORE the
+ * context holds 5 + n_sem floats per sample (device memory allocated on the
+ * grid's stream, freed by sdg_ctx_release).  Errors: SDG_ERR_ARG, SDG_ERR_OOM,
+ * SDG_ERR_CUDA. */
+int sdg_render_forward(sdg_grid g, const float* rays_dev, int64_t n, const sdg_render_opts* opts,
+                       const sdg_render_out* out, sdg_ctx* ctx);
+
+/* Backward of sdg_render_forward: given dL/d(rgb, depth, opac, sem) per ray
+ * (device, [n][3], [n], [n], [n][n_sem]; depth/opac/sem may be NULL = 0),
+ * ACCUMULATES (+=) dL/dtheta into the grid's gradient channels:
+ *   dL/dtau_k = T_{k+1} v_k - sum_{j>k} w_j v_j - T_N (g_rgb . bg),
+ *   v_k = g_rgb . c_k + g_depth t_k + g_opac + g_sem . s_k,
+ *   dL/dd_k = delta_k sigma'(d_k) dL/dtau_k,  dL/dc_k = w_k g_rgb,  dL/ds_k = w_k g_sem,
+ * each scattered to the 8 voxels with the trilinear weights (Eq. 17). */
+int sdg_render_backward(sdg_ctx ctx, const float* g_rgb_dev, const float* g_depth_dev, const float* g_opac_dev,
+                        const float* g_sem_dev);
+
+/* Releases a context (enqueues the release of its device memory).  Safe on NULL. */
+int sdg_ctx_release(sdg_ctx ctx);
+
+/* Loss weights.  Eq. 12-13 and the supplement's hyper-parameters
+ * (lambda_d = 0.1); the colour loss is L1 per channel, the depth loss L1 on
+ * metric depth (scale a = 1, shift b = 0), and the semantic loss the squared
+ * L2 of rendered logits (following the L2 label fusion of Eq. 11), weighted
+ * lambda_s. */
+typedef struct {
+    float lambda_depth; /* 0.1 */
+    float lambda_sem;   /* 0.1 */
+} sdg_loss_opts;
+
+/* Per-ray loss and gradient seeds for n rays:
+ *   loss_i = sum_c |rgb - t_rgb| / (3n) + lambda_d |depth - t_depth| / n + lambda_s ||sem - t_sem||^2 / n
+ *   g_rgb = sign(rgb - t_rgb) / (3n), g_depth = lambda_d sign(depth - t_depth) / n,
+ *   g_sem = 2 lambda_s (sem - t_sem) / n,  sign(0) = 0.
+ * sem/t_sem/g_sem may be NULL (no semantic term).  loss_dev [n] per-ray
+ * terms (may be NULL). */
+int sdg_loss_l1(sdg_grid g, int64_t n, const float* rgb_dev, const float* depth_dev, const float* sem_dev,
+                const float* t_rgb_dev, const float* t_depth_dev, const float* t_sem_dev, const sdg_loss_opts* lo,
+                float* g_rgb_dev, float* g_depth_dev, float* g_sem_dev, float* loss_dev);
+
+/* One fused training pass (forward, sdg_loss_l1 and backward of the same
+ * rays in a single kernel; no per-sample state leaves the SM): accumulates
+ * the gradients and writes the per-ray loss terms to loss_dev [n] (may be
+ * NULL) and their sum to loss_sum_dev [1] (may be NULL; deterministic
+ * reduction).  t_sem_dev may be NULL when the grid has no semantics or the
+ * semantic term is not wanted.  opts->mode is ignored. */
+int sdg_train_step_rays(sdg_grid g, const float* rays_dev, int64_t n, const float* t_rgb_dev,
+                        const float* t_depth_dev, const float* t_sem_dev, const sdg_render_opts* opts,
+                        const sdg_loss_opts* lo, float* loss_dev, float* loss_sum_dev);
+
+/* ----------------------------------------------------------------------- */
+/* Optimiser                                                                */
+/* ----------------------------------------------------------------------- */
+
+/* Sec. 3.5.4 optimises theta_d, theta_c, theta_s with RMSProp at learning
+ * rate 1e-3; Adam is the default here (SDG_OPT_RMSPROP selects RMSProp with
+ * alpha = beta2).  One step over every voxel of the active blocks and every
+ * trainable channel (SDF, colour, semantics; not the fusion weight), in FP32;
+ * BF16 channels are updated in FP32 and rounded to nearest-even on store.
+ * Gradients are zeroed.  Adam: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * theta -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * step <= 0 uses (and increments) the grid's own step counter. */
+typedef struct {
+    float lr;    /* 1e-3 */
+    float beta1; /* 0.9 */
+    float beta2; /* 0.999 (RMSProp: alpha, 0.99) */
+    float eps;   /* 1e-8 */
+    int32_t step;
+    int32_t algo; /* SDG_OPT_ADAM or SDG_OPT_RMSPROP */
+} sdg_adam_opts;
+
+int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a);
+
+/* ----------------------------------------------------------------------- */
+/* Serving: continuous batching of render requests over several grids       */
+/* ----------------------------------------------------------------------- */
+
+/* Inference rendering (Sec. 4.2, colour and depth of whole images) as a
+ * service.  A host scheduler thread admits requests while slots and the
+ * device-memory budget allow, splits each into ray chunks, and launches
+ * batches that mix chunks of different requests, resolutions and scenes on
+ * several streams, so batches overlap on the device.  A request's result
+ * does not depend on what it was batched with: every ray is computed by the
+ * same per-ray code, from its own pixel index. */
+typedef struct {
+    int64_t hbm_budget_bytes; /* device memory for in-flight outputs (the server allocates it once) */
+    int32_t max_slots;        /* requests in flight at once, >= 1 */
+    int32_t n_streams;        /* 1..8 */
+    int32_t chunk_rays;       /* rays per chunk, multiple of 32 */
+    int32_t max_batch_rays;   /* rays per launch, multiple of chunk_rays */
+    int32_t device;
+    int32_t reserved;
+} sdg_server_opts;
+
+typedef struct {
+    int32_t scene_id;  /* from sdg_server_add_scene */
+    int32_t H, W;      /* image size */
+    float K[4];        /* fx, fy, cx, cy */
+    float Twc[12];     /* row-major camera-to-world; ray of pixel (u, v) has direction
+                          normalize(R ((u+0.5-cx)/fx, (v+0.5-cy)/fy, 1)), origin Twc[:,3] */
+    int32_t n_samples; /* samples per ray */
+    uint32_t seed;     /* stratification seed; ray id = pixel index v*W + u */
+    int32_t stratified;
+    float tnear, tfar;
+} sdg_request;
+
+typedef struct {
+    int32_t status;     /* SDG_OK when done */
+    int32_t H, W;
+    const float* rgb;   /* device [H*W][3], owned by the server until sdg_server_release */
+    const float* depth; /* device [H*W] */
+    const float* opac;  /* device [H*W] */
+    double t_submit_ms; /* host clock (monotonic, ms) */
+    double t_admit_ms;
+    double t_done_ms;   /* when the scheduler saw the last chunk complete */
+} sdg_result;
+
+typedef struct {
+    int64_t submitted, admitted, completed, launches, rays_rendered;
+    int64_t bytes_in_use, peak_bytes_in_use;
+    int32_t in_flight, queued;
+} sdg_server_stats;
+
+int sdg_server_create(const sdg_server_opts* o, sdg_server* out);
+/* Registers a grid (not owned; it must outlive the server).  All scenes of a
+ * server must share rgb_dtype and n_sem.  Not allowed once requests exist. */
+int sdg_server_add_scene(sdg_server s, sdg_grid g, int32_t* scene_id);
+/* Queues a request; SDG_ERR_CAPACITY if its outputs can never fit the budget. */
+int sdg_server_submit(sdg_server s, const sdg_request* q, uint64_t* ticket);
+/* Non-blocking: SDG_OK and a filled result when done, SDG_ERR_BUSY before. */
+int sdg_server_poll(sdg_server s, uint64_t ticket, sdg_result* r);
+/* Blocks up to timeout_ms (host clock); SDG_ERR_TIMEOUT if not done by then. */
+int sdg_server_wait(sdg_server s, uint64_t ticket, int64_t timeout_ms, sdg_result* r);
+/* Frees a completed request's outputs; cancels a queued one. */
+int sdg_server_release(sdg_server s, uint64_t ticket);
+int sdg_server_get_stats(sdg_server s, sdg_server_stats* st);
+/* Waits for in-flight work, stops the scheduler, frees everything. */
+int sdg_server_destroy(sdg_server s);
+
+/* Thread-local message of the calling thread's last error ("" if none). */
+const char* sdg_last_error(void);
+
+/* Library version string. */
+const char* sdg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDG_H */
