@@ -188,7 +188,7 @@ int sdg_grid_sync(sdg_grid g);
  * delta_k)), T_k = exp(-sum_{j<k} sigma_j delta_j) (Eq. 15).  Outputs per
  * ray: rgb = sum w c + T_N bg, depth = sum w t, opac = sum w, sem = sum w s. */
 typedef struct {
-    int32_t n_samples;  /* N per ray, 1..512 */
+    int32_t n_samples;  /* N per ray, 1..256 */
     uint32_t seed;      /* stratification seed */
     uint32_t ray_id0;   /* hash id of ray 0 of this call (ray i uses ray_id0 + i) */
     int32_t stratified; /* 1: jittered u_k; 0: u_k = 0.5 */

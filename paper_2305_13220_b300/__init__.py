@@ -1,0 +1,16 @@
+"""sdg: differentiable volume rendering of SDF + colour + semantic channels in a globally sparse, locally
+dense voxel-block grid (arXiv 2305.13220), as hand-written sm_103a CUDA behind a C ABI (include/sdg.h).
+
+This package is a thin binding: it marshals torch tensors (device memory, streams) to libsdg.so.  Importing it
+loads libsdg.so and raises ImportError if the library has not been built -- there is no CPU fallback."""
+from . import _abi
+from ._abi import SdgError
+
+_abi.lib()  # fail loudly at import when the CUDA library is missing
+
+from .grid import Grid, render_opts  # noqa: E402
+from .render import (DifferentiableRenderer, RenderContext, backward, loss_l1, render,  # noqa: E402
+                     train_step_rays)
+
+__all__ = ["Grid", "render_opts", "render", "backward", "loss_l1", "train_step_rays", "DifferentiableRenderer",
+           "RenderContext", "SdgError"]

@@ -1,0 +1,127 @@
+// Optimiser step over the voxel parameters (Sec. 3.5.4: theta_d, theta_c,
+// theta_s optimised directly; RMSProp at lr 1e-3 in the paper, Adam by
+// default here).  A streaming kernel: every parameter is read and written once
+// per step (theta, g, m, v in; theta, m, v out; g zeroed), so it is bound by
+// HBM bandwidth.  Paper: arXiv 2305.13220.
+#include <cmath>
+
+#include "internal.h"
+
+using namespace sdg;
+
+namespace {
+
+struct OptParams {
+    float lr, b1, b2, eps;
+    float c1, c2;  // Adam bias corrections 1 - b^step
+};
+
+template <int ALGO>
+__device__ __forceinline__ float update(float th, float g, float& m, float& v, const OptParams& p) {
+    if (ALGO == SDG_OPT_ADAM) {
+        m = fmaf(p.b1, m, (1.f - p.b1) * g);
+        v = fmaf(p.b2, v, (1.f - p.b2) * g * g);
+        const float mh = m / p.c1, vh = v / p.c2;
+        return th - p.lr * mh / (sqrtf(vh) + p.eps);
+    } else {  // RMSProp, alpha = b2
+        v = fmaf(p.b2, v, (1.f - p.b2) * g * g);
+        return th - p.lr * g / (sqrtf(v) + p.eps);
+    }
+}
+
+// FP32 parameters, four per thread-iteration (16-byte streaming accesses).
+template <int ALGO>
+__global__ void __launch_bounds__(256) k_opt_f32(float4* __restrict__ th, float4* __restrict__ gr,
+                                                 float4* __restrict__ m, float4* __restrict__ v, int64_t n4,
+                                                 OptParams p) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 t = __ldcs(th + i), g = __ldcs(gr + i), mm = __ldcs(m + i), vv = __ldcs(v + i);
+        t.x = update<ALGO>(t.x, g.x, mm.x, vv.x, p);
+        t.y = update<ALGO>(t.y, g.y, mm.y, vv.y, p);
+        t.z = update<ALGO>(t.z, g.z, mm.z, vv.z, p);
+        t.w = update<ALGO>(t.w, g.w, mm.w, vv.w, p);
+        __stcs(th + i, t);
+        __stcs(gr + i, z);
+        if (ALGO == SDG_OPT_ADAM) __stcs(m + i, mm);
+        __stcs(v + i, vv);
+    }
+}
+
+__device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);  // round to nearest even
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// BF16 parameters in groups of four (uint2) with FP32 gradient and moments;
+// lanes >= nlanes of each group are padding and left untouched.
+template <int ALGO>
+__global__ void __launch_bounds__(256) k_opt_bf16(uint2* __restrict__ th, float4* __restrict__ gr,
+                                                  float4* __restrict__ m, float4* __restrict__ v, int64_t n4,
+                                                  int nlanes, OptParams p) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        uint2 t = __ldcs(th + i);
+        float4 g = __ldcs(gr + i), mm = __ldcs(m + i), vv = __ldcs(v + i);
+        float a0 = bf_lo(t.x), a1 = bf_hi(t.x), a2 = bf_lo(t.y), a3 = bf_hi(t.y);
+        a0 = update<ALGO>(a0, g.x, mm.x, vv.x, p);
+        a1 = update<ALGO>(a1, g.y, mm.y, vv.y, p);
+        a2 = update<ALGO>(a2, g.z, mm.z, vv.z, p);
+        if (nlanes == 4) a3 = update<ALGO>(a3, g.w, mm.w, vv.w, p);
+        t.x = pack_bf2(a0, a1);
+        t.y = pack_bf2(a2, a3);
+        __stcs(th + i, t);
+        __stcs(gr + i, z);
+        if (ALGO == SDG_OPT_ADAM) __stcs(m + i, mm);
+        __stcs(v + i, vv);
+    }
+}
+
+int opt_blocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    const int64_t cap = 148 * 8;  // enough resident warps to saturate HBM; grid-stride beyond
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <int ALGO>
+int run(sdg_grid g, const OptParams& p) {
+    const int64_t V = g->n_blocks * 512;
+    cudaStream_t s = g->stream;
+    if (g->desc.rgb_dtype == SDG_F32) {
+        k_opt_f32<ALGO><<<opt_blocks(V), 256, 0, s>>>(g->geo, g->ggeo, g->m_geo, g->v_geo, V, p);
+    } else {
+        k_opt_f32<ALGO><<<opt_blocks(V / 4), 256, 0, s>>>((float4*)g->sdf, (float4*)g->gsdf, (float4*)g->m_sdf,
+                                                           (float4*)g->v_sdf, V / 4, p);
+        k_opt_bf16<ALGO><<<opt_blocks(V), 256, 0, s>>>(g->rgbh, g->grgb, g->m_rgb, g->v_rgb, V, 3, p);
+    }
+    if (g->desc.n_sem) {
+        const int64_t n4 = V * g->desc.n_sem / 4;
+        k_opt_bf16<ALGO><<<opt_blocks(n4), 256, 0, s>>>((uint2*)g->sem, (float4*)g->gsem, (float4*)g->m_sem,
+                                                         (float4*)g->v_sem, n4, 4, p);
+    }
+    SDG_LAUNCH_CHECK("optimiser");
+    return SDG_OK;
+}
+
+}  // namespace
+
+extern "C" int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a) {
+    if (!g || !a || !(a->lr >= 0.f) || !(a->beta1 >= 0.f && a->beta1 < 1.f) || !(a->beta2 >= 0.f && a->beta2 < 1.f) ||
+        !(a->eps > 0.f) || (a->algo != SDG_OPT_ADAM && a->algo != SDG_OPT_RMSPROP))
+        return fail(SDG_ERR_ARG, "sdg_adam_step: invalid options");
+    int rc = use_device(g);
+    if (rc) return rc;
+    const int32_t step = a->step > 0 ? a->step : g->step + 1;
+    g->step = step;
+    if (g->n_blocks == 0) return SDG_OK;
+    OptParams p;
+    p.lr = a->lr;
+    p.b1 = a->beta1;
+    p.b2 = a->beta2;
+    p.eps = a->eps;
+    p.c1 = (float)(1.0 - std::pow((double)a->beta1, step));
+    p.c2 = (float)(1.0 - std::pow((double)a->beta2, step));
+    return a->algo == SDG_OPT_ADAM ? run<SDG_OPT_ADAM>(g, p) : run<SDG_OPT_RMSPROP>(g, p);
+}

@@ -78,13 +78,13 @@ __device__ __forceinline__ int32_t sdg_table_find(const ulonglong2* __restrict__
     return -1;
 }
 
-// Same lookup through the coherent path, for kernels that read a table that
-// an earlier kernel of the same stream (or this one) may have written.
+// Same lookup through L2 only (no L1 copy), for kernels that read a table an
+// earlier kernel of the same stream has just written.
 __device__ __forceinline__ int32_t sdg_table_find_rw(const ulonglong2* t, uint32_t mask, uint64_t key) {
     uint32_t h = sdg_slot_hash(key) & mask;
 #pragma unroll 1
     for (uint32_t p = 0; p <= mask; ++p) {
-        ulonglong2 s = *reinterpret_cast<const volatile ulonglong2*>(t + h);
+        ulonglong2 s = __ldcg(t + h);
         if (s.x == key) return (int32_t)s.y;
         if (s.x == SDG_EMPTY_KEY) return -1;
         h = (h + 1) & mask;

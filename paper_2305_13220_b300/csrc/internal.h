@@ -1,0 +1,85 @@
+// Host-side grid object shared by the .cu files of libsdg (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+struct sdg_grid_s {
+    sdg_grid_desc desc;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int64_t max_blocks = 0;
+    int64_t n_blocks = 0;
+    uint32_t cap = 0, mask = 0;  // hash capacity (power of two) and cap - 1
+    float beta = 0.f;
+    int32_t step = 0;
+
+    // hash map (main) and the de-duplication set used by activation
+    ulonglong2* table = nullptr;
+    ulonglong2* tmp_table = nullptr;
+    int4* keys = nullptr;  // [max_blocks] {x, y, z, 0} in index order
+    int4* nbr = nullptr;   // [max_blocks][2]
+    uint32_t* bitmap = nullptr;
+    int64_t bitmap_words = 0, bitmap_words_cap = 0;
+    int bmin[3] = {0, 0, 0}, bdim[3] = {0, 0, 0};
+
+    // channels
+    float4 *geo = nullptr, *ggeo = nullptr, *m_geo = nullptr, *v_geo = nullptr;                  // SDG_F32
+    float *sdf = nullptr, *gsdf = nullptr, *m_sdf = nullptr, *v_sdf = nullptr;                   // SDG_BF16
+    uint2* rgbh = nullptr;                                                                        // SDG_BF16
+    float4 *grgb = nullptr, *m_rgb = nullptr, *v_rgb = nullptr;                                   // SDG_BF16
+    __nv_bfloat16* sem = nullptr;
+    float *gsem = nullptr, *m_sem = nullptr, *v_sem = nullptr;
+    float* weight = nullptr;
+
+    // activation scratch
+    uint64_t* sort_buf = nullptr;  // [sort_cap]
+    int64_t sort_cap = 0;
+    unsigned long long* counters = nullptr;    // device [8]
+    unsigned long long* h_counters = nullptr;  // pinned host [8]
+    int* minmax = nullptr;                     // device [6]
+    int* h_minmax = nullptr;                   // pinned host [6]
+    float* loss_buf = nullptr;                 // per-ray loss scratch of the fused training pass
+    int64_t loss_cap = 0;
+
+    std::mutex mu;  // serialises host-side mutation (activation, load) of this grid
+
+    GridDev dev() const {
+        GridDev d{};
+        d.table = table;
+        d.nbr = nbr;
+        d.bitmap = bitmap;
+        d.keys = keys;
+        d.mask = mask;
+        d.n_sem = desc.n_sem;
+        for (int a = 0; a < 3; ++a) {
+            d.bmin[a] = bmin[a];
+            d.bdim[a] = bdim[a];
+        }
+        d.vs = desc.voxel_size;
+        d.inv_vs = 1.0f / desc.voxel_size;
+        d.L = 8.0f * desc.voxel_size;
+        d.inv_L = 1.0f / d.L;
+        d.beta = beta;
+        d.inv_beta = 1.0f / beta;
+        d.n_blocks = n_blocks;
+        d.geo = geo;
+        d.ggeo = ggeo;
+        d.sdf = sdf;
+        d.rgbh = rgbh;
+        d.gsdf = gsdf;
+        d.grgb = grgb;
+        d.sem = sem;
+        d.gsem = gsem;
+        return d;
+    }
+};
+
+namespace sdg {
+// Makes g's device current for the calling thread.
+int use_device(sdg_grid g);
+}  // namespace sdg

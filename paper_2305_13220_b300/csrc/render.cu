@@ -1,0 +1,247 @@
+// Rendering entry points: forward, backward (recompute or stored samples),
+// rendering losses and the fused training pass.  Paper: arXiv 2305.13220,
+// Sec. 3.5.1 (Eq. 12-15), Sec. 3.5.4 and the supplement's hyper-parameters.
+#include <new>
+
+#include "internal.h"
+#include "render_core.cuh"
+
+using namespace sdg;
+
+struct sdg_ctx_s {
+    sdg_grid g;
+    const float* rays;
+    int64_t n;
+    sdg_render_opts opts;
+    int Q;
+    float* rec;  // store mode
+    float* rec_S;
+};
+
+namespace sdg {
+template <int MODE, bool BF16, bool SEM>
+int launch_q(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs& a, int Q, cudaStream_t s);
+}
+
+namespace {
+
+int pick_q(int N) { return N <= 64 ? 2 : N <= 128 ? 4 : N <= 192 ? 6 : 8; }
+
+template <int MODE>
+int launch_pass(sdg_grid g, const float* rays, uint32_t id0, const PassArgs& a) {
+    if (a.n == 0) return SDG_OK;
+    const GridDev gd = g->dev();
+    const int Q = pick_q(a.N);
+    const bool bf16 = g->desc.rgb_dtype == SDG_BF16;
+    const bool sem = g->desc.n_sem > 0;
+    if (!bf16 && !sem) return launch_q<MODE, false, false>(gd, rays, id0, a, Q, g->stream);
+    if (!bf16 && sem) return launch_q<MODE, false, true>(gd, rays, id0, a, Q, g->stream);
+    if (bf16 && !sem) return launch_q<MODE, true, false>(gd, rays, id0, a, Q, g->stream);
+    return launch_q<MODE, true, true>(gd, rays, id0, a, Q, g->stream);
+}
+
+int check_opts(const sdg_render_opts* o) {
+    if (!o || o->n_samples < 1 || o->n_samples > 256 || (o->mode != SDG_MODE_RECOMPUTE && o->mode != SDG_MODE_STORE))
+        return fail(SDG_ERR_ARG, "render opts: n_samples must be in [1, 256] and mode RECOMPUTE or STORE");
+    return SDG_OK;
+}
+
+PassArgs base_args(const sdg_render_opts* o, int64_t n) {
+    PassArgs a{};
+    a.N = o->n_samples;
+    a.seed = o->seed;
+    a.strat = o->stratified ? 1 : 0;
+    a.bg[0] = o->bg[0];
+    a.bg[1] = o->bg[1];
+    a.bg[2] = o->bg[2];
+    a.n = n;
+    return a;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ---------------------------------------------------------------------------
+// Losses
+// ---------------------------------------------------------------------------
+__global__ void k_loss_l1(int64_t n, int ns, const float* __restrict__ rgb, const float* __restrict__ depth,
+                          const float* __restrict__ sem, const float* __restrict__ trgb,
+                          const float* __restrict__ tdepth, const float* __restrict__ tsem, float lam_d, float lam_s,
+                          float inv_n, float* grgb, float* gdepth, float* gsem, float* loss) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float third = inv_n * (1.0f / 3.0f);
+        float L = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            const float e = rgb[3 * i + c] - trgb[3 * i + c];
+            L += fabsf(e) * third;
+            grgb[3 * i + c] = sgnf(e) * third;
+        }
+        const float ed = depth[i] - tdepth[i];
+        L += lam_d * fabsf(ed) * inv_n;
+        gdepth[i] = lam_d * sgnf(ed) * inv_n;
+        if (sem && tsem)
+            for (int c = 0; c < ns; ++c) {
+                const float es = sem[i * ns + c] - tsem[i * ns + c];
+                L += lam_s * es * es * inv_n;
+                if (gsem) gsem[i * ns + c] = 2.f * lam_s * es * inv_n;
+            }
+        if (loss) loss[i] = L;
+    }
+}
+
+// Deterministic sum: fixed per-thread strided order, then a fixed tree.
+__global__ void __launch_bounds__(1024) k_sum(const float* __restrict__ x, int64_t n, float* out) {
+    __shared__ float s[1024];
+    float acc = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) acc += x[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = s[0];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" int sdg_render_forward(sdg_grid g, const float* rays, int64_t n, const sdg_render_opts* o,
+                                  const sdg_render_out* out, sdg_ctx* ctx) {
+    if (ctx) *ctx = nullptr;
+    if (!g || !out || n < 0 || (n > 0 && (!rays || !out->rgb || !out->depth || !out->opac)))
+        return fail(SDG_ERR_ARG, "sdg_render_forward: null argument");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (n > 0 && !aligned16(rays)) return fail(SDG_ERR_ARG, "sdg_render_forward: rays must be 16-byte aligned");
+    if (n > (int64_t)1 << 31) return fail(SDG_ERR_ARG, "sdg_render_forward: at most 2^31 rays per call");
+    if ((rc = use_device(g))) return rc;
+    PassArgs a = base_args(o, n);
+    a.out_rgb = out->rgb;
+    a.out_depth = out->depth;
+    a.out_opac = out->opac;
+    a.out_sem = g->desc.n_sem ? out->sem : nullptr;
+    const int Q = pick_q(o->n_samples);
+    float *rec = nullptr, *rec_S = nullptr;
+    const bool store = o->mode == SDG_MODE_STORE && ctx;
+    if (store && n > 0) {
+        SDG_CUDA_TRY(cudaMallocAsync((void**)&rec, sizeof(float) * 5 * (size_t)n * 32 * Q, g->stream));
+        cudaError_t e = cudaMallocAsync((void**)&rec_S, sizeof(float) * (size_t)n, g->stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(rec, g->stream);
+            return cuda_fail(e, "cudaMallocAsync(store records)");
+        }
+        a.rec = rec;
+        a.rec_S = rec_S;
+        rc = launch_pass<PASS_FWD_STORE>(g, rays, o->ray_id0, a);
+    } else {
+        rc = launch_pass<PASS_FWD>(g, rays, o->ray_id0, a);
+    }
+    if (rc) {
+        if (rec) cudaFreeAsync(rec, g->stream);
+        if (rec_S) cudaFreeAsync(rec_S, g->stream);
+        return rc;
+    }
+    if (ctx) {
+        sdg_ctx c = new (std::nothrow) sdg_ctx_s{g, rays, n, *o, Q, rec, rec_S};
+        if (!c) {
+            if (rec) cudaFreeAsync(rec, g->stream);
+            if (rec_S) cudaFreeAsync(rec_S, g->stream);
+            return fail(SDG_ERR_OOM, "context");
+        }
+        c->opts.mode = store ? SDG_MODE_STORE : SDG_MODE_RECOMPUTE;
+        *ctx = c;
+    }
+    return SDG_OK;
+}
+
+extern "C" int sdg_render_backward(sdg_ctx c, const float* g_rgb, const float* g_depth, const float* g_opac,
+                                   const float* g_sem) {
+    if (!c || (c->n > 0 && !g_rgb)) return fail(SDG_ERR_ARG, "sdg_render_backward: null argument");
+    sdg_grid g = c->g;
+    int rc = use_device(g);
+    if (rc) return rc;
+    PassArgs a = base_args(&c->opts, c->n);
+    a.g_rgb = g_rgb;
+    a.g_depth = g_depth;
+    a.g_opac = g_opac;
+    a.g_sem = g->desc.n_sem ? g_sem : nullptr;
+    if (c->opts.mode == SDG_MODE_STORE && c->rec) {
+        a.rec = c->rec;
+        a.rec_S = c->rec_S;
+        return launch_pass<PASS_BWD_STORE>(g, c->rays, c->opts.ray_id0, a);
+    }
+    return launch_pass<PASS_BWD>(g, c->rays, c->opts.ray_id0, a);
+}
+
+extern "C" int sdg_ctx_release(sdg_ctx c) {
+    if (!c) return SDG_OK;
+    cudaSetDevice(c->g->device);
+    if (c->rec) cudaFreeAsync(c->rec, c->g->stream);
+    if (c->rec_S) cudaFreeAsync(c->rec_S, c->g->stream);
+    delete c;
+    return SDG_OK;
+}
+
+extern "C" int sdg_loss_l1(sdg_grid g, int64_t n, const float* rgb, const float* depth, const float* sem,
+                           const float* trgb, const float* tdepth, const float* tsem, const sdg_loss_opts* lo,
+                           float* grgb, float* gdepth, float* gsem, float* loss) {
+    if (!g || !lo || n < 0 || (n > 0 && (!rgb || !depth || !trgb || !tdepth || !grgb || !gdepth)))
+        return fail(SDG_ERR_ARG, "sdg_loss_l1: null argument");
+    int rc = use_device(g);
+    if (rc) return rc;
+    if (n == 0) return SDG_OK;
+    const int ns = g->desc.n_sem;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    k_loss_l1<<<blocks, 256, 0, g->stream>>>(n, ns, rgb, depth, ns ? sem : nullptr, trgb, tdepth, ns ? tsem : nullptr,
+                                             lo->lambda_depth, lo->lambda_sem, 1.0f / (float)n, grgb, gdepth,
+                                             ns ? gsem : nullptr, loss);
+    SDG_LAUNCH_CHECK("loss");
+    return SDG_OK;
+}
+
+extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, const float* trgb, const float* tdepth,
+                                   const float* tsem, const sdg_render_opts* o, const sdg_loss_opts* lo, float* loss,
+                                   float* loss_sum) {
+    if (!g || !lo || n < 0 || (n > 0 && (!rays || !trgb || !tdepth)))
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays: null argument");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (n > 0 && !aligned16(rays)) return fail(SDG_ERR_ARG, "sdg_train_step_rays: rays must be 16-byte aligned");
+    if (n > (int64_t)1 << 31) return fail(SDG_ERR_ARG, "sdg_train_step_rays: at most 2^31 rays per call");
+    if ((rc = use_device(g))) return rc;
+    if (n == 0) {
+        if (loss_sum) SDG_CUDA_TRY(cudaMemsetAsync(loss_sum, 0, sizeof(float), g->stream));
+        return SDG_OK;
+    }
+    float* per_ray = loss;
+    if (!per_ray && loss_sum) {
+        if (g->loss_cap < n) {  // grid-owned per-ray loss scratch, grown on demand
+            if (g->loss_buf) {
+                SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
+                cudaFree(g->loss_buf);
+            }
+            g->loss_buf = nullptr;
+            g->loss_cap = 0;
+            SDG_CUDA_TRY(cudaMalloc((void**)&g->loss_buf, sizeof(float) * n));
+            g->loss_cap = n;
+        }
+        per_ray = g->loss_buf;
+    }
+    PassArgs a = base_args(o, n);
+    a.t_rgb = trgb;
+    a.t_depth = tdepth;
+    a.t_sem = g->desc.n_sem ? tsem : nullptr;
+    a.lam_d = lo->lambda_depth;
+    a.lam_s = lo->lambda_sem;
+    a.inv_n = 1.0f / (float)n;
+    a.loss = per_ray;
+    rc = launch_pass<PASS_TRAIN>(g, rays, o->ray_id0, a);
+    if (rc) return rc;
+    if (loss_sum) {
+        k_sum<<<1, 1024, 0, g->stream>>>(per_ray, n, loss_sum);
+        SDG_LAUNCH_CHECK("loss sum");
+    }
+    return SDG_OK;
+}

@@ -1,0 +1,46 @@
+// Render kernel template and its launcher, instantiated per (layout, semantics,
+// pass) in the render_inst_*.cu files so that they compile in parallel.
+#pragma once
+
+#include "render_core.cuh"
+
+namespace sdg {
+
+template <int MODE, bool BF16, bool SEM, int Q>
+__global__ void __launch_bounds__(256) k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0,
+                                                PassArgs a) {
+    __shared__ float smem[kWarpsPerBlock][64 * Q + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (r >= a.n) return;  // warp-uniform
+    const float4 r0 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r);
+    const float4 r1 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r + 1);
+    RayJob j;
+    j.o = make_float3(r0.x, r0.y, r0.z);
+    j.tn = r0.w;
+    j.d = make_float3(r1.x, r1.y, r1.z);
+    j.tf = r1.w;
+    j.ray_id = ray_id0 + (uint32_t)r;
+    j.idx = r;
+    ray_program<MODE, BF16, SEM, Q>(g, a, j, smem[warp], smem[warp] + 32 * Q, lane);
+}
+
+template <int MODE, bool BF16, bool SEM>
+int launch_q(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs& a, int Q, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((a.n + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    switch (Q) {
+        case 2: k_render<MODE, BF16, SEM, 2><<<blocks, 256, 0, s>>>(gd, rays, id0, a); break;
+        case 4: k_render<MODE, BF16, SEM, 4><<<blocks, 256, 0, s>>>(gd, rays, id0, a); break;
+        case 6: k_render<MODE, BF16, SEM, 6><<<blocks, 256, 0, s>>>(gd, rays, id0, a); break;
+        default: k_render<MODE, BF16, SEM, 8><<<blocks, 256, 0, s>>>(gd, rays, id0, a); break;
+    }
+    SDG_LAUNCH_CHECK("render kernel");
+    return SDG_OK;
+}
+
+
+}  // namespace sdg
+
+#define SDG_INSTANTIATE_LAUNCH(MODE, BF16, SEM)                                                         \
+    template int sdg::launch_q<MODE, BF16, SEM>(const GridDev&, const float*, uint32_t, const PassArgs&, int, \
+                                                cudaStream_t);

@@ -1,0 +1,117 @@
+"""Rendering calls and the autograd wrapper (argument marshalling over the C ABI; all compute is in libsdg)."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import torch
+
+from . import _abi as A
+from .grid import Grid, _ptr, render_opts
+
+
+class RenderContext:
+    """Saved state of one forward for its backward (owns the ABI context; rays are kept alive)."""
+
+    def __init__(self, handle: C.c_void_p, grid: Grid, rays: torch.Tensor):
+        self._h = handle
+        self.grid = grid
+        self.rays = rays
+
+    def release(self):
+        if self._h is not None and self._h.value:
+            A.lib().sdg_ctx_release(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def render(grid: Grid, rays: torch.Tensor, n_samples: int, seed: int = 0, ray_id0: int = 0, stratified: bool = True,
+           mode: str = "recompute", bg=(0.0, 0.0, 0.0), want_ctx: bool = False, want_sem: bool = True):
+    """Forward render (Eq. 12-15) of rays [n, 8] -> dict(rgb [n,3], depth [n], opac [n], sem [n,n_sem], ctx)."""
+    n = rays.shape[0]
+    dev = rays.device
+    out = {"rgb": torch.empty((n, 3), device=dev), "depth": torch.empty(n, device=dev),
+           "opac": torch.empty(n, device=dev)}
+    sem_p = None
+    if grid.n_sem and want_sem:
+        out["sem"] = torch.empty((n, grid.n_sem), device=dev)
+        sem_p = _ptr(out["sem"])
+    ro = A.RenderOut(rgb=_ptr(out["rgb"]), depth=_ptr(out["depth"]), opac=_ptr(out["opac"]), sem=sem_p)
+    o = render_opts(n_samples, seed, ray_id0, stratified, mode, bg)
+    h = C.c_void_p()
+    A.call("sdg_render_forward", grid.handle, _ptr(rays, torch.float32, "rays"), n, C.byref(o), C.byref(ro),
+           C.byref(h) if want_ctx else None)
+    out["ctx"] = RenderContext(h, grid, rays) if want_ctx else None
+    return out
+
+
+def backward(ctx: RenderContext, g_rgb: torch.Tensor, g_depth: Optional[torch.Tensor] = None,
+             g_opac: Optional[torch.Tensor] = None, g_sem: Optional[torch.Tensor] = None):
+    """Accumulates dL/dtheta into the grid's gradient channels."""
+    A.call("sdg_render_backward", ctx._h, _ptr(g_rgb.contiguous(), torch.float32, "g_rgb"),
+           _ptr(None if g_depth is None else g_depth.contiguous()),
+           _ptr(None if g_opac is None else g_opac.contiguous()),
+           _ptr(None if g_sem is None else g_sem.contiguous()))
+
+
+def loss_l1(grid: Grid, rgb, depth, t_rgb, t_depth, sem=None, t_sem=None, lambda_depth=0.1, lambda_sem=0.1):
+    """Per-ray L1 colour / depth (+ squared L2 logits) loss terms and their gradient seeds."""
+    n = rgb.shape[0]
+    g = {"rgb": torch.empty_like(rgb), "depth": torch.empty_like(depth)}
+    if sem is not None:
+        g["sem"] = torch.empty_like(sem)
+    loss = torch.empty(n, device=rgb.device)
+    lo = A.LossOpts(lambda_depth=lambda_depth, lambda_sem=lambda_sem)
+    A.call("sdg_loss_l1", grid.handle, n, _ptr(rgb), _ptr(depth), _ptr(sem), _ptr(t_rgb), _ptr(t_depth), _ptr(t_sem),
+           C.byref(lo), _ptr(g["rgb"]), _ptr(g["depth"]), _ptr(g.get("sem")), _ptr(loss))
+    return loss, g
+
+
+def train_step_rays(grid: Grid, rays: torch.Tensor, t_rgb: torch.Tensor, t_depth: torch.Tensor,
+                    t_sem: Optional[torch.Tensor] = None, n_samples: int = 128, seed: int = 0, ray_id0: int = 0,
+                    stratified: bool = True, bg=(0.0, 0.0, 0.0), lambda_depth: float = 0.1, lambda_sem: float = 0.1,
+                    loss: Optional[torch.Tensor] = None, loss_sum: Optional[torch.Tensor] = None):
+    """Fused forward + L1 losses + backward; gradients accumulate into the grid."""
+    o = render_opts(n_samples, seed, ray_id0, stratified, "recompute", bg)
+    lo = A.LossOpts(lambda_depth=lambda_depth, lambda_sem=lambda_sem)
+    A.call("sdg_train_step_rays", grid.handle, _ptr(rays, torch.float32, "rays"), rays.shape[0],
+           _ptr(t_rgb, torch.float32, "t_rgb"), _ptr(t_depth, torch.float32, "t_depth"), _ptr(t_sem), C.byref(o),
+           C.byref(lo), _ptr(loss), _ptr(loss_sum))
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, anchor, grid, rays, n_samples, seed, ray_id0, stratified, mode, bg):
+        out = render(grid, rays, n_samples, seed, ray_id0, stratified, mode, bg, want_ctx=True)
+        fctx.sdg = out["ctx"]
+        fctx.has_sem = "sem" in out
+        res = [out["rgb"], out["depth"], out["opac"]]
+        if fctx.has_sem:
+            res.append(out["sem"])
+        return tuple(res)
+
+    @staticmethod
+    def backward(fctx, g_rgb, g_depth, g_opac, *rest):
+        g_sem = rest[0] if fctx.has_sem and rest else None
+        backward(fctx.sdg, g_rgb, g_depth, g_opac, g_sem)
+        fctx.sdg.release()
+        return (None,) * 9
+
+
+class DifferentiableRenderer:
+    """torch.autograd entry: outputs are differentiable w.r.t. the grid's voxels; loss.backward() ACCUMULATES
+    dL/dtheta into the grid's gradient channels (read them with Grid.channel(group, KIND_GRAD)).  The anchor
+    tensor only connects the outputs to the autograd graph; it receives no gradient."""
+
+    def __init__(self, grid: Grid):
+        self.grid = grid
+        self.anchor = torch.zeros(1, device=f"cuda:{grid.device}", requires_grad=True)
+
+    def __call__(self, rays, n_samples: int, seed: int = 0, ray_id0: int = 0, stratified: bool = True,
+                 mode: str = "recompute", bg=(0.0, 0.0, 0.0)):
+        return _RenderFn.apply(self.anchor, self.grid, rays, n_samples, seed, ray_id0, stratified, mode, tuple(bg))

@@ -1,0 +1,127 @@
+"""GPU parity of block activation (Eq. 7-8) and the block hash map against the oracle: bit-exact key sets,
+index order, lookups, capacity behaviour and checkpoints."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sdg():
+    import paper_2305_13220_b300 as m
+    return m
+
+
+@pytest.mark.parametrize("r", [0, 3, 4, 16])
+def test_activate_points_bit_exact(sdg, r):
+    rng = np.random.default_rng(100 + r)
+    pts = np.concatenate([rng.uniform(-1.3, 2.1, size=(60000, 3)),
+                          rng.normal(0.5, 0.01, size=(20000, 3))]).astype(np.float32)
+    pts[:5] = [[np.nan, 0, 0], [np.inf, 1, 1], [0.0, -0.0, 0.079999995], [-1e-9, 0, 0], [1e30, 0, 0]]
+    ks = oracle.KeySet()
+    ks.add_points(pts, 0.01, r)
+    want = ks.keys()
+    G = sdg.Grid(0.01, len(want) + 10)
+    n = G.activate_points(torch.as_tensor(pts, device="cuda"), r)
+    assert n == len(want)
+    np.testing.assert_array_equal(G.keys().cpu().numpy(), want)
+
+
+def _expected_batches(views, K, vs, r):
+    """Oracle index order: each activation batch appends its new keys in ascending (z, y, x) order."""
+    ks = oracle.KeySet()
+    order = np.zeros((0, 3), np.int32)
+    for T, d in views:
+        before = set(map(tuple, ks.keys().tolist()))
+        ks.add_depth(d, K, T, vs, r)
+        new = [k for k in ks.keys().tolist() if tuple(k) not in before]
+        order = np.concatenate([order, np.array(new, np.int32).reshape(-1, 3)])
+    return order
+
+
+@pytest.mark.parametrize("which", ["tiny_room", "room_scale"])
+def test_activate_depth_bit_exact(sdg, which):
+    if which == "tiny_room":
+        sc, vs, r, W, H, nv, cap = synth.scene_tiny_room(0), 0.04, 3, 64, 48, 4, 4096
+    else:
+        sc, vs, r, W, H, nv, cap = synth.scene_room(0), 0.01, 4, 640, 480, 3, 200000
+    poses = synth.random_poses(sc, nv, seed=3)
+    K = synth.intrinsics(W, H)
+    views = [(T, synth.depth_map(sc, T, W, H, K)) for T in poses]
+    G = sdg.Grid(vs, cap)
+    total = sum(G.activate_depth(d.cuda(), K, T, r) for T, d in views)
+    want = _expected_batches(views, K, vs, r)
+    assert total == len(want) == G.num_blocks
+    np.testing.assert_array_equal(G.keys().cpu().numpy(), want)
+
+
+def test_lookup_present_and_absent(sdg):
+    sc = synth.scene_tiny_room(0)
+    keys = synth.band_blocks(sc, 0.04, 3)
+    G = sdg.Grid(0.04, 2048)
+    G.activate_keys(torch.as_tensor(keys, device="cuda"))
+    gk = G.keys()
+    idx = G.lookup(gk).cpu().numpy()
+    np.testing.assert_array_equal(idx, np.arange(len(keys)))
+    rng = np.random.default_rng(1)
+    absent = rng.integers(-(1 << 20), 1 << 20, size=(1_000_000, 3)).astype(np.int32)
+    O = oracle.Grid(0.04, 0.02).set(gk.cpu().numpy(), np.zeros((len(keys), 512)), np.zeros((len(keys), 512, 3)))
+    want = O.lookup(absent)
+    got = G.lookup(torch.as_tensor(absent, device="cuda")).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    assert (got == -1).mean() > 0.999
+
+
+def test_capacity_error_leaves_grid_unchanged(sdg):
+    G = sdg.Grid(0.01, 100)
+    rng = np.random.default_rng(2)
+    small = torch.as_tensor(rng.uniform(0, 0.05, size=(50, 3)).astype(np.float32), device="cuda")
+    n0 = G.activate_points(small, 0)
+    k0 = G.keys().cpu().numpy()
+    big = torch.as_tensor(rng.uniform(-5, 5, size=(5000, 3)).astype(np.float32), device="cuda")
+    with pytest.raises(sdg.SdgError) as e:
+        G.activate_points(big, 2)
+    assert e.value.code == sdg._abi.ERR_CAPACITY
+    assert G.num_blocks == n0
+    np.testing.assert_array_equal(G.keys().cpu().numpy(), k0)
+    # the de-duplication set was emptied: a fitting batch still activates exactly its new keys
+    more = torch.as_tensor(np.array([[1.0, 1.0, 1.0]], np.float32), device="cuda")
+    assert G.activate_points(more, 0) == 1
+    assert G.num_blocks == n0 + 1
+
+
+def test_activate_keys_duplicates_and_present(sdg):
+    G = sdg.Grid(0.01, 64)
+    k = torch.tensor([[0, 0, 0], [1, 0, 0], [0, 0, 0], [-3, 2, 1]], dtype=torch.int32, device="cuda")
+    assert G.activate_keys(k) == 3
+    assert G.activate_keys(k) == 0
+    np.testing.assert_array_equal(G.keys().cpu().numpy(), [[0, 0, 0], [1, 0, 0], [-3, 2, 1]])
+    bad = torch.tensor([[1 << 20, 0, 0]], dtype=torch.int32, device="cuda")
+    with pytest.raises(sdg.SdgError):
+        G.activate_keys(bad)
+    assert G.num_blocks == 3
+
+
+def test_empty_activation(sdg):
+    G = sdg.Grid(0.01, 16)
+    assert G.activate_points(torch.zeros((0, 3), device="cuda"), 3) == 0
+    assert G.num_blocks == 0
+
+
+def test_save_load_roundtrip(sdg, tmp_path):
+    from tests.gpu_util import tiny_room
+    sc, G, O, stored, vals = tiny_room()
+    G.step = 7
+    p = str(tmp_path / "g.sdg")
+    G.save(p)
+    H = sdg.Grid.load(p, max_blocks=G.max_blocks)
+    assert H.num_blocks == G.num_blocks and H.step == 7
+    np.testing.assert_array_equal(H.keys().cpu().numpy(), G.keys().cpu().numpy())
+    A = sdg._abi
+    N = G.num_blocks
+    assert torch.equal(H.channel(A.GROUP_GEO)[:N], G.channel(A.GROUP_GEO)[:N])
+    np.testing.assert_array_equal(H.lookup(G.keys()).cpu().numpy(), np.arange(N))
