@@ -11,6 +11,7 @@ _abi.lib()  # fail loudly at import when the CUDA library is missing
 from .grid import Grid, render_opts  # noqa: E402
 from .render import (DifferentiableRenderer, RenderContext, backward, loss_l1, render,  # noqa: E402
                      train_step_rays)
+from .serve import Server  # noqa: E402
 
 __all__ = ["Grid", "render_opts", "render", "backward", "loss_l1", "train_step_rays", "DifferentiableRenderer",
-           "RenderContext", "SdgError"]
+           "RenderContext", "SdgError", "Server"]

@@ -1,0 +1,107 @@
+"""Serving loop: continuous batching across scenes and resolutions; each result must equal the same request
+rendered alone (bit-for-bit: rays are computed independently of their batch mates) and match the oracle."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.gpu_util import make_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sdg():
+    import paper_2305_13220_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    out = []
+    for seed, dtype in ((0, "bf16"), (1, "bf16")):
+        sc = synth.scene_room(seed, size=(2.0 + seed, 2.0, 2.0), n_objects=2)
+        keys = synth.band_blocks(sc, 0.04, 3)
+        G, O, stored, vals = make_pair(sc, keys, 0.04, 3, 0.02, dtype)
+        out.append((sc, G, O))
+    return out
+
+
+def _req(sc, W, H, seed):
+    T = synth.random_poses(sc, 1, seed=seed)[0]
+    return T, synth.intrinsics(W, H)
+
+
+def test_mix_equals_alone_and_oracle(sdg, scenes):
+    srv = sdg.Server(hbm_budget_bytes=64 << 20, max_slots=6, n_streams=3, chunk_rays=1024, max_batch_rays=8192)
+    ids = [srv.add_scene(G) for _, G, _ in scenes]
+    reqs = []
+    rng = np.random.default_rng(0)
+    for i in range(12):
+        s = int(rng.integers(0, 2))
+        W, H = [(40, 30), (80, 60), (64, 48)][i % 3]
+        T, K = _req(scenes[s][0], W, H, seed=i)
+        reqs.append((s, W, H, T, K, 64 if i % 2 else 128, 100 + i))
+    # alone: one at a time
+    alone = []
+    for s, W, H, T, K, N, seed in reqs:
+        t = srv.submit(ids[s], H, W, K, T, n_samples=N, seed=seed)
+        r = srv.wait(t, 60000)
+        alone.append(srv.result_tensors(r))
+        srv.release(t)
+    # mixed: all at once
+    tickets = [srv.submit(ids[s], H, W, K, T, n_samples=N, seed=seed) for s, W, H, T, K, N, seed in reqs]
+    for t, ref in zip(tickets, alone):
+        r = srv.wait(t, 60000)
+        got = srv.result_tensors(r)
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b)
+        assert r.t_done_ms >= r.t_admit_ms >= r.t_submit_ms
+        srv.release(t)
+    st = srv.stats()
+    assert st.completed == 24 and st.bytes_in_use == 0 and st.peak_bytes_in_use <= 64 << 20
+    # oracle parity for two of the requests
+    for i in (0, 7):
+        s, W, H, T, K, N, seed = reqs[i]
+        rays = oracle.view_rays(H, W, K, T)
+        ref = scenes[s][2].render(rays, N, seed=seed)
+        nd = ~ref["degenerate"]
+        assert nd.mean() > 0.95
+        rgb, depth, opac = alone[i]
+        assert np.abs(rgb.double().cpu().numpy() - ref["rgb"])[nd].max() < 1e-4
+        assert np.abs(depth.double().cpu().numpy() - ref["depth"])[nd].max() < 1e-4
+    srv.close()
+
+
+def test_admission_by_memory_and_errors(sdg, scenes):
+    one = 80 * 60 * 5 * 4
+    srv = sdg.Server(hbm_budget_bytes=one + 4096, max_slots=8, n_streams=2, chunk_rays=512, max_batch_rays=4096)
+    sid = srv.add_scene(scenes[0][1])
+    T, K = _req(scenes[0][0], 80, 60, seed=3)
+    ts = [srv.submit(sid, 60, 80, K, T, n_samples=64, seed=i) for i in range(5)]
+    for t in ts:
+        r = srv.wait(t, 60000)
+        assert r.status == 0
+        srv.release(t)
+    st = srv.stats()
+    assert st.peak_bytes_in_use <= one + 4096 and st.completed == 5
+    with pytest.raises(sdg.SdgError) as e:
+        srv.submit(sid, 600, 800, K, T)
+    assert e.value.code == sdg._abi.ERR_CAPACITY
+    with pytest.raises(sdg.SdgError):
+        srv.submit(99, 10, 10, K, T)
+    # cancel a queued request and time out on a wait of 0 ms
+    t1 = srv.submit(sid, 60, 80, K, T, n_samples=256)
+    t2 = srv.submit(sid, 60, 80, K, T, n_samples=256)
+    srv.release(t2)
+    with pytest.raises(sdg.SdgError):
+        srv.poll(t2)
+    try:
+        srv.wait(t1, 0)
+    except sdg.SdgError as err:
+        assert err.code == sdg._abi.ERR_TIMEOUT
+    assert srv.wait(t1, 60000).status == 0
+    srv.close()
