@@ -1,0 +1,449 @@
+"""Benchmark: room-scale FP32 training step of the sparse-dense SDF renderer on one B300 (or N replicas).
+
+Workload (synthetic stand-in for the paper's ScanNet rooms): a 6x6x3 m room with 10 seeded boxes / cylinders,
+1 cm voxels in 8^3 blocks, blocks activated from 50 analytic 640x480 depth maps with a 4-voxel band; FP32 SDF,
+RGB and fusion weight per voxel.  One step = 2^18 rays x 128 stratified samples through the fused
+forward + L1 colour/depth loss + backward kernel, the loss reduction, and an Adam update of every voxel.
+
+Prints one JSON line (see the keys below).  `--impl reference` times the CPU FP64 oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd rays/s and samples/s on sparse-dense SDF grid; HBM GB/s; p50/p99 ms"
+VS, BAND, N_VIEWS, W, H = 0.01, 4, 50, 640, 480
+N_SAMPLES = 128
+BETA = 0.5 * VS
+LAMBDA_D = 0.1
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--rays", type=int, default=1 << 18)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
+    p.add_argument("--views", type=int, default=N_VIEWS)
+    return p.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Workload construction
+# ----------------------------------------------------------------------------------------------------------
+def build_workload(sdg, torch, device, n_views, rays_per_step, n_batches=4, seed=0):
+    import synth
+    sc = synth.scene_room(seed)
+    poses = synth.random_poses(sc, n_views, seed=seed)
+    K = synth.intrinsics(W, H)
+    t0 = time.time()
+    depths = [synth.depth_map(sc, T, W, H, K, device=device) for T in poses]
+    torch.cuda.synchronize()
+    t_depth = time.time() - t0
+    G = sdg.Grid(VS, 160_000, beta=BETA)
+    # activation: timed separately (all 50 maps), CUDA events on the grid's stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for T, d in zip(poses, depths):
+        G.activate_depth(d, K, T, BAND)
+    ev1.record()
+    torch.cuda.synchronize()
+    act_ms = ev0.elapsed_time(ev1)
+    nb = G.num_blocks
+    keys = G.keys().cpu().numpy()
+    vals = synth.fill_grid(sc, keys, VS, BAND, device=device)
+    A = sdg._abi
+    geo = G.channel(A.GROUP_GEO)
+    geo[:nb, :, 0] = vals["sdf"].to(torch.float32)
+    geo[:nb, :, 1:4] = vals["rgb"].to(torch.float32)
+    G.channel(A.GROUP_WEIGHT)[:nb, :, 0] = 1.0
+    del vals
+    batches = []
+    for b in range(n_batches):
+        tb = synth.training_batch(sc, poses, W, H, K, rays_per_step, seed=1000 * seed + b, device=device)
+        batches.append({k: v.contiguous() for k, v in tb.items()})
+    torch.cuda.synchronize()
+    return {"scene": sc, "poses": poses, "K": K, "grid": G, "keys": keys, "batches": batches, "act_ms": act_ms,
+            "depth_s": t_depth}
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ----------------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "power_w_max": max(power) if power else None, "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------------------------
+# CPU oracle leg (baseline and algorithmic byte counts)
+# ----------------------------------------------------------------------------------------------------------
+def oracle_grid(wl, torch, sdg):
+    import oracle
+    G = wl["grid"]
+    A = sdg._abi
+    nb = G.num_blocks
+    geo = G.channel(A.GROUP_GEO)[:nb].double().cpu().numpy()
+    return oracle.Grid(VS, BETA).set(wl["keys"], geo[..., 0], geo[..., 1:4])
+
+
+def cpu_leg(O, batch, seconds, N=N_SAMPLES):
+    """Times the oracle's forward + loss + backward on successive 256-ray chunks of the batch until `seconds`
+    of CPU time are spent; returns rays/s and the sample description."""
+    import oracle
+    rays = batch["rays"].cpu().numpy()
+    t_rgb = batch["rgb"].double().cpu().numpy()
+    t_d = batch["depth"].double().cpu().numpy()
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds and done < len(rays):
+        sl = slice(done, min(done + 256, len(rays)))
+        out = O.render(rays[sl], N, seed=0, ray_id0=done)
+        _, g = oracle.loss(out["rgb"], out["depth"], t_rgb[sl], t_d[sl], LAMBDA_D)
+        O.backward(rays[sl], N, g["rgb"], g["depth"], seed=0, ray_id0=done)
+        done = sl.stop
+    el = time.perf_counter() - t0
+    return done / el, done, el
+
+
+def bytes_per_ray(O, batch, n=1024, N=N_SAMPLES):
+    """Algorithmic bytes per ray of the fused training kernel, from the oracle's count of the distinct voxels
+    and blocks each ray's stencils touch: voxels x (16 B read + 16 B grad read + 16 B grad write),
+    blocks x 40 B (16-B hash slot + 24 B of neighbour table on average... counted as 40 B), ray 32 B,
+    targets 16 B, loss 4 B."""
+    rays = batch["rays"][:n].cpu().numpy()
+    vx, bl = O.count_touched(rays, N, seed=0)
+    per_ray = vx * 48.0 + bl * 40.0 + 32 + 16 + 4
+    return float(per_ray.mean()), float(vx.mean()), float(bl.mean())
+
+
+def read_traffic(kernel: str):
+    """DRAM bytes per launch recorded from an ncu capture in profiles/<kernel>_traffic.txt, else None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for ln in open(p):
+        if ln.startswith("traffic_bytes_per_launch:"):
+            try:
+                return float(ln.split(":", 1)[1])
+            except ValueError:
+                return None
+    return None
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Serving measurement (p50 / p99 latency)
+# ----------------------------------------------------------------------------------------------------------
+def serve_leg(sdg, torch, wl, n_requests=200, seed=0):
+    import synth
+    srv = sdg.Server(hbm_budget_bytes=2 << 30, max_slots=32, n_streams=4, chunk_rays=4096, max_batch_rays=1 << 18)
+    sid = srv.add_scene(wl["grid"])
+    rng = np.random.default_rng(seed)
+    res = [(160, 120), (320, 240), (640, 480), (1280, 960)]
+    sc = wl["scene"]
+    poses = synth.random_poses(sc, 16, seed=77)
+    # warm-up
+    t = srv.submit(sid, 120, 160, synth.intrinsics(160, 120), poses[0], n_samples=N_SAMPLES)
+    srv.wait(t, 120000)
+    srv.release(t)
+    # open loop at a rate of about 80% of a quick capacity estimate
+    t0 = time.perf_counter()
+    tk = [srv.submit(sid, 480, 640, synth.intrinsics(640, 480), poses[i % 16], n_samples=N_SAMPLES, seed=i)
+          for i in range(8)]
+    for t in tk:
+        srv.wait(t, 120000)
+        srv.release(t)
+    cap_rays_s = 8 * 640 * 480 / (time.perf_counter() - t0)
+    mean_rays = np.mean([w * h for w, h in res])
+    rate = 0.8 * cap_rays_s / mean_rays
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    tickets = []
+    start = time.perf_counter()
+    for i in range(n_requests):
+        while time.perf_counter() - start < arrivals[i]:
+            time.sleep(0.0002)
+        w, h = res[int(rng.integers(0, 4))]
+        tickets.append((srv.submit(sid, h, w, synth.intrinsics(w, h), poses[i % 16], n_samples=N_SAMPLES, seed=i),
+                        w * h))
+    lat, rays = [], 0
+    for t, n in tickets:
+        r = srv.wait(t, 300000)
+        lat.append(r.t_done_ms - r.t_submit_ms)
+        rays += n
+        srv.release(t)
+    elapsed = time.perf_counter() - start
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": n_requests, "rate_req_s": round(rate, 2), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "rays_per_s": round(rays / elapsed, 1),
+            "resolutions": "uniform over 160x120, 320x240, 640x480, 1280x960", "samples_per_ray": N_SAMPLES,
+            "arrivals": "Poisson at 0.8x measured saturated capacity"}
+
+
+# ----------------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    import paper_2305_13220_b300 as sdg
+    device = f"cuda:{local}"
+    wl = build_workload(sdg, torch, device, args.views, args.rays, seed=rank)
+    G = wl["grid"]
+    n = args.rays
+    stream = torch.cuda.current_stream()
+    loss_sum = torch.zeros(1, device=device)
+
+    def step(b):
+        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
+                            lambda_depth=LAMBDA_D, loss_sum=loss_sum)
+        G.adam_step(lr=1e-3)
+
+    stepno = [0]
+    for i in range(args.warmup):
+        stepno[0] = i
+        step(wl["batches"][i % len(wl["batches"])])
+    torch.cuda.synchronize()
+    # phase timing: events between the fused kernel (+ loss sum) and the optimiser
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(K):
+        b = wl["batches"][i % len(wl["batches"])]
+        stepno[0] = 1000 + i
+        evs[i][0].record(stream)
+        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
+                            lambda_depth=LAMBDA_D, loss_sum=loss_sum)
+        evs[i][1].record(stream)
+        G.adam_step(lr=1e-3)
+        evs[i][2].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    train_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    adam_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    ms_step = total_ms / K
+    value = world * n / (ms_step / 1e3)
+
+    # end to end through the public API: pinned host inputs copied in, loss read back, every step
+    hb = [{k: v.cpu().pin_memory() for k, v in b.items() if k in ("rays", "rgb", "depth")} for b in wl["batches"]]
+    dev_in = {k: torch.empty_like(v) for k, v in wl["batches"][0].items() if k in ("rays", "rgb", "depth")}
+    host_loss = torch.empty(1, pin_memory=True)
+    h2d = sum(v.numel() * v.element_size() for v in hb[0].values())
+    for i in range(2):
+        for k in dev_in:
+            dev_in[k].copy_(hb[i % len(hb)][k], non_blocking=True)
+        step(dev_in)
+        host_loss.copy_(loss_sum, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(K):
+        for k in dev_in:
+            dev_in[k].copy_(hb[i % len(hb)][k], non_blocking=True)
+        step(dev_in)
+        host_loss.copy_(loss_sum, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / K
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = t.item()
+
+    res = None
+    if rank == 0:
+        nb = G.num_blocks
+        params = nb * 512 * 4
+        adam_bytes = params * 32
+        line = {"metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "room-scale FP32 training step (6x6x3 m room, 10 boxes/cylinders, 1 cm "
+                                       "voxels, 8^3 blocks, 4-voxel band from 50 640x480 depth maps; 2^18 rays "
+                                       "x 128 stratified samples, L1 colour + 0.1 L1 depth, Adam on every voxel)",
+                           "rays_per_step": n, "samples_per_ray": N_SAMPLES, "n_blocks": nb,
+                           "voxels": nb * 512, "params": params,
+                           "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "l2": "inputs larger than L2: each step streams the whole grid and Adam state "
+                                 f"({adam_bytes / 1e9:.1f} GB) through HBM"},
+                "samples_per_s": round(value * N_SAMPLES, 1),
+                "phases": {"train_kernel_ms": round(train_ms, 4), "adam_ms": round(adam_ms, 4),
+                           "activation_ms_50_maps": round(wl["act_ms"], 3)},
+                "clocks": clk, "gpu_launches": 3 * K,
+                "e2e": {"value": round(world * n / (e2e_ms / 1e3), 1), "unit": "rays/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}}
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
+        peak_src = "measured" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else "fallback"
+        adam_gbs = adam_bytes / (adam_ms / 1e3) / 1e9
+        O = None
+        bpr = None
+        if not args.no_cpu_baseline:
+            O = oracle_grid(wl, torch, sdg)
+            bpr, vx, bl = bytes_per_ray(O, wl["batches"][0])
+            rate, done, el = cpu_leg(O, wl["batches"][0], args.cpu_seconds)
+            line["cpu_baseline"] = {"value": round(rate, 2), "unit": "rays/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"{done} rays of the first batch (fwd + L1 loss + bwd, FP64, "
+                                              f"single thread, {el:.1f} s)"}
+        train_gbs = (bpr * n / (train_ms / 1e3) / 1e9) if bpr else None
+        kern = {"adam": (adam_ms, adam_gbs, adam_bytes, "k_opt_f32"),
+                "train": (train_ms, train_gbs, bpr * n if bpr else None, "k_render_train")}
+        dom = "adam" if adam_ms >= train_ms or train_gbs is None else "train"
+        ms_d, gbs_d, bytes_d, kname = kern[dom]
+        line["roofline"] = {"kernel": kname, "bound": "hbm", "achieved": round(gbs_d, 1), "peak": peak,
+                            "unit": "GB/s", "frac": round(gbs_d / peak, 4), "traffic": read_traffic(kname),
+                            "peak_source": peak_src, "algorithmic_bytes_per_launch": bytes_d}
+        other = "train" if dom == "adam" else "adam"
+        if kern[other][1] is not None:
+            line["roofline_other"] = {"kernel": kern[other][3], "achieved": round(kern[other][1], 1),
+                                      "frac": round(kern[other][1] / peak, 4), "unit": "GB/s",
+                                      "algorithmic_bytes_per_launch": kern[other][2]}
+        if bpr:
+            line["train_kernel_bytes_per_ray"] = {"value": round(bpr, 1), "distinct_voxels": round(vx, 1),
+                                                  "distinct_blocks": round(bl, 2), "rays_counted": 1024}
+        if not args.no_serve:
+            line["serve"] = serve_leg(sdg, torch, wl)
+        res = line
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return res
+
+
+def run_reference(args):
+    """Reference arm: the CPU FP64 oracle, as it stands, on the same workload (rank 0 only)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import torch
+    import synth
+    import oracle
+    sc = synth.scene_room(0)
+    poses = synth.random_poses(sc, args.views, seed=0)
+    K = synth.intrinsics(W, H)
+    ks = oracle.KeySet()
+    for T in poses:
+        ks.add_depth(synth.depth_map(sc, T, W, H, K), K, T, VS, BAND)
+    keys = ks.keys()
+    vals = synth.fill_grid(sc, keys, VS, BAND)
+    O = oracle.Grid(VS, BETA).set(keys, vals["sdf"].to(torch.float32).double().numpy(),
+                                  vals["rgb"].to(torch.float32).double().numpy())
+    del vals
+    batch = synth.training_batch(sc, poses, W, H, K, 4096, seed=0)
+    rates = []
+    per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        r, done, el = cpu_leg(O, batch, per_step)
+        if i >= args.warmup:
+            rates.append(r)
+    v = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * 2 ** 18 / v, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "room-scale FP32 training step (same scene, rays and samples as the GPU arm)",
+                       "rays_per_step": 1 << 18, "samples_per_ray": N_SAMPLES, "n_blocks": int(len(keys))},
+            "cpu_baseline": {"value": round(v, 2), "unit": "rays/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step about {per_step:.0f} s of 256-ray chunks of a 4096-ray batch"},
+            "e2e": {"value": round(v, 2), "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -268,13 +268,15 @@ int sdg_train_step_rays(sdg_grid g, const float* rays_dev, int64_t n, const floa
  * theta -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
  * step <= 0 uses (and increments) the grid's own step counter. */
 typedef struct {
-    float lr;    /* 1e-3 */
-    float beta1; /* 0.9 */
-    float beta2; /* 0.999 (RMSProp: alpha, 0.99) */
-    float eps;   /* 1e-8 */
+    double lr;    /* 1e-3 */
+    double beta1; /* 0.9 */
+    double beta2; /* 0.999 (RMSProp: alpha, 0.99) */
+    double eps;   /* 1e-8 */
     int32_t step;
     int32_t algo; /* SDG_OPT_ADAM or SDG_OPT_RMSPROP */
 } sdg_adam_opts;
+/* (Hyper-parameters are doubles so that 1 - beta is exact to FP32 rounding;
+ * the update itself runs in FP32.) */
 
 int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a);
 

@@ -39,7 +39,7 @@ class LossOpts(C.Structure):
 
 
 class AdamOpts(C.Structure):
-    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
                 ("step", C.c_int32), ("algo", C.c_int32)]
 
 

@@ -13,18 +13,19 @@ namespace {
 
 struct OptParams {
     float lr, b1, b2, eps;
-    float c1, c2;  // Adam bias corrections 1 - b^step
+    float omb1, omb2;  // 1 - b1, 1 - b2 (rounded from double)
+    float c1, c2;      // Adam bias corrections 1 - b^step
 };
 
 template <int ALGO>
 __device__ __forceinline__ float update(float th, float g, float& m, float& v, const OptParams& p) {
     if (ALGO == SDG_OPT_ADAM) {
-        m = fmaf(p.b1, m, (1.f - p.b1) * g);
-        v = fmaf(p.b2, v, (1.f - p.b2) * g * g);
+        m = fmaf(p.b1, m, p.omb1 * g);
+        v = fmaf(p.b2, v, p.omb2 * g * g);
         const float mh = m / p.c1, vh = v / p.c2;
         return th - p.lr * mh / (sqrtf(vh) + p.eps);
     } else {  // RMSProp, alpha = b2
-        v = fmaf(p.b2, v, (1.f - p.b2) * g * g);
+        v = fmaf(p.b2, v, p.omb2 * g * g);
         return th - p.lr * g / (sqrtf(v) + p.eps);
     }
 }
@@ -108,8 +109,8 @@ int run(sdg_grid g, const OptParams& p) {
 }  // namespace
 
 extern "C" int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a) {
-    if (!g || !a || !(a->lr >= 0.f) || !(a->beta1 >= 0.f && a->beta1 < 1.f) || !(a->beta2 >= 0.f && a->beta2 < 1.f) ||
-        !(a->eps > 0.f) || (a->algo != SDG_OPT_ADAM && a->algo != SDG_OPT_RMSPROP))
+    if (!g || !a || !(a->lr >= 0.0) || !(a->beta1 >= 0.0 && a->beta1 < 1.0) || !(a->beta2 >= 0.0 && a->beta2 < 1.0) ||
+        !(a->eps > 0.0) || (a->algo != SDG_OPT_ADAM && a->algo != SDG_OPT_RMSPROP))
         return fail(SDG_ERR_ARG, "sdg_adam_step: invalid options");
     int rc = use_device(g);
     if (rc) return rc;
@@ -117,11 +118,13 @@ extern "C" int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a) {
     g->step = step;
     if (g->n_blocks == 0) return SDG_OK;
     OptParams p;
-    p.lr = a->lr;
-    p.b1 = a->beta1;
-    p.b2 = a->beta2;
-    p.eps = a->eps;
-    p.c1 = (float)(1.0 - std::pow((double)a->beta1, step));
-    p.c2 = (float)(1.0 - std::pow((double)a->beta2, step));
+    p.lr = (float)a->lr;
+    p.b1 = (float)a->beta1;
+    p.b2 = (float)a->beta2;
+    p.eps = (float)a->eps;
+    p.omb1 = (float)(1.0 - a->beta1);
+    p.omb2 = (float)(1.0 - a->beta2);
+    p.c1 = (float)(1.0 - std::pow(a->beta1, step));
+    p.c2 = (float)(1.0 - std::pow(a->beta2, step));
     return a->algo == SDG_OPT_ADAM ? run<SDG_OPT_ADAM>(g, p) : run<SDG_OPT_RMSPROP>(g, p);
 }

@@ -42,8 +42,10 @@ def test_f32_optimiser_matches_oracle(sdg, algo):
     assert torch.all(grad[:N] == 0)
     assert G.step == 3
     if algo == "adam":
-        np.testing.assert_allclose(m[:N].double().cpu().numpy().reshape(-1), mo, rtol=1e-5, atol=1e-12)
-    np.testing.assert_allclose(v[:N].double().cpu().numpy().reshape(-1), vo, rtol=1e-5, atol=1e-14)
+        # m sums gradients of both signs: cancellation makes its relative error unbounded, so the
+        # bound is a few FP32 ulps of the largest gradient fed in (0.1 * |N(0,1)| ~ 0.5)
+        np.testing.assert_allclose(m[:N].double().cpu().numpy().reshape(-1), mo, rtol=1e-5, atol=1e-8)
+    np.testing.assert_allclose(v[:N].double().cpu().numpy().reshape(-1), vo, rtol=1e-5, atol=1e-12)
 
 
 def test_bf16_channels_round_to_nearest_even(sdg):

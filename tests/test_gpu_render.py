@@ -69,7 +69,7 @@ def test_forward_sample_counts(sdg, room, N):
 
 def test_rays_missing_the_grid_and_empty_batches(sdg, room):
     sc, G, O, _, _ = room
-    r = np.array([[10, 10, 10, 0, 1, 0, 0, 100], [1, 1, 1, 0.0, 0, 0, 1, 0.01],   # misses; too short to reach
+    r = np.array([[10, 10, 10, 0, 1, 0, 0, 100], [-5, 1, 1, 0.0, 1, 0, 0, 0.01],  # misses; too short to reach
                   [1, 1, 1, 5.0, 1, 0, 0, 4.0]], np.float32)                           # tnear > tfar
     out = sdg.render(G, torch.as_tensor(r, device="cuda"), 64, bg=(0.3, 0.2, 0.1))
     np.testing.assert_allclose(out["rgb"].cpu().numpy(), np.tile([0.3, 0.2, 0.1], (3, 1)), atol=1e-7)
