@@ -6,8 +6,8 @@
 //   * admits queued requests (FIFO) while request slots and the device-memory
 //     budget allow (outputs are carved from one pre-allocated pool),
 //   * cuts admitted requests into chunks of chunk_rays pixels and packs
-//     chunks of different requests, resolutions and scenes into batches of at
-//     most max_batch_rays rays,
+//     chunks of different requests, resolutions and scenes (with samples per
+//     ray in the same class) into batches of at most max_batch_rays rays,
 //   * launches each batch on the next of n_streams streams (at most two
 //     batches in flight per stream), so batches overlap on the device while
 //     new requests join the following batch as soon as they are admitted,
@@ -253,9 +253,14 @@ struct sdg_server_s {
             Batch* b = free_batch();
             if (!b) break;
             int nch = 0, maxN = 1;
+            // One batch = one sample-slot class (Q = ceil(N/32) rounded as the kernels are built), so that
+            // every request runs the same kernel instantiation alone or in any mix: its rays' arithmetic,
+            // and hence its result, do not depend on its batch mates.
+            const int qclass = pick_q(reqs[active.front()].q.n_samples);
             // oldest admitted requests first; a request contributes chunks until the batch is full
             for (size_t i = 0; i < active.size() && nch < max_chunks; ++i) {
                 Req& r = reqs[active[i]];
+                if (pick_q(r.q.n_samples) != qclass) continue;
                 bool used = false;
                 while (r.next_pix < r.npix && nch < max_chunks) {
                     ChunkDesc& c = b->h_chunks[nch++];
