@@ -255,6 +255,28 @@ int sdg_train_step_rays(sdg_grid g, const float* rays_dev, int64_t n, const floa
                         const float* t_depth_dev, const float* t_sem_dev, const sdg_render_opts* opts,
                         const sdg_loss_opts* lo, float* loss_dev, float* loss_sum_dev);
 
+/* Allocation-free variant of sdg_train_step_rays (the paper has no
+ * counterpart; this is a deployment aid).  Some callers cannot let the
+ * library allocate device memory: processes whose whole device-memory budget
+ * is owned by another allocator, and latency-critical loops that cannot
+ * afford cudaMalloc/cudaFree, which synchronise the device.
+ * sdg_train_step_rays allocates a per-ray loss buffer the first time only the
+ * summed loss is requested; this entry point instead keeps that scratch in a
+ * fixed array built into the library (4 MiB, held on every GPU that loads
+ * the library until the process exits) and calls no allocating routine.
+ * Same arguments and results as sdg_train_step_rays without loss_dev: the
+ * gradients accumulate into the grid and loss_sum_dev [1] (may be NULL)
+ * receives the summed loss.  n may be at most 1048576 rays; larger n returns
+ * SDG_ERR_CAPACITY before any work is enqueued.  The first call on each
+ * device looks up the array's device address (a one-time set-up); make that
+ * first call before any stream capture.  Every call on a device shares the
+ * one array and overwrites its first n entries before reading them, so calls
+ * whose work overlaps on the GPU (other streams or host threads) race: order
+ * them on one stream or serialise them. */
+int sdg_train_step_rays_noalloc(sdg_grid g, const float* rays_dev, int64_t n, const float* t_rgb_dev,
+                                const float* t_depth_dev, const float* t_sem_dev, const sdg_render_opts* opts,
+                                const sdg_loss_opts* lo, float* loss_sum_dev);
+
 /* ----------------------------------------------------------------------- */
 /* Optimiser                                                                */
 /* ----------------------------------------------------------------------- */

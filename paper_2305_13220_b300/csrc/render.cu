@@ -1,6 +1,7 @@
 // Rendering entry points: forward, backward (recompute or stored samples),
 // rendering losses and the fused training pass.  Paper: arXiv 2305.13220,
 // Sec. 3.5.1 (Eq. 12-15), Sec. 3.5.4 and the supplement's hyper-parameters.
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -242,6 +243,70 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
     if (loss_sum) {
         k_sum<<<1, 1024, 0, g->stream>>>(per_ray, n, loss_sum);
         SDG_LAUNCH_CHECK("loss sum");
+    }
+    return SDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free fused training pass: the per-ray loss scratch is a fixed
+// array in the library image instead of a cudaMalloc'd buffer.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t kNoAllocMaxRays = 1 << 20;  // 4 MiB of FP32 per-ray loss terms
+static __device__ __align__(256) float g_noalloc_loss[kNoAllocMaxRays];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {};  // device address of g_noalloc_loss, per device ordinal
+
+// Resolves (once per device, with that device current) the device address of
+// the scratch array; host code must not pass the symbol itself to a kernel.
+int noalloc_scratch(int device, float** out) {
+    if (device < 0 || device >= kNoAllocMaxDevices) return fail(SDG_ERR_ARG, "no-alloc scratch: bad device ordinal");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        float* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_loss);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return SDG_OK;
+}
+}  // namespace
+
+extern "C" int sdg_train_step_rays_noalloc(sdg_grid g, const float* rays, int64_t n, const float* trgb,
+                                           const float* tdepth, const float* tsem, const sdg_render_opts* o,
+                                           const sdg_loss_opts* lo, float* loss_sum) {
+    if (!g || !lo || n < 0 || (n > 0 && (!rays || !trgb || !tdepth)))
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays_noalloc: null argument");
+    if (n > kNoAllocMaxRays)
+        return fail(SDG_ERR_CAPACITY, "sdg_train_step_rays_noalloc: n = " + std::to_string(n) +
+                                          " rays exceeds the fixed scratch capacity of 1048576 rays");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (n > 0 && !aligned16(rays))
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays_noalloc: rays must be 16-byte aligned");
+    if ((rc = use_device(g))) return rc;
+    float* scratch = nullptr;
+    if ((rc = noalloc_scratch(g->device, &scratch))) return rc;
+    if (n == 0) {
+        if (loss_sum) SDG_CUDA_TRY(cudaMemsetAsync(loss_sum, 0, sizeof(float), g->stream));
+        return SDG_OK;
+    }
+    PassArgs a = base_args(o, n);
+    a.t_rgb = trgb;
+    a.t_depth = tdepth;
+    a.t_sem = g->desc.n_sem ? tsem : nullptr;
+    a.lam_d = lo->lambda_depth;
+    a.lam_s = lo->lambda_sem;
+    a.inv_n = 1.0f / (float)n;
+    a.loss = loss_sum ? scratch : nullptr;  // every ray writes its entry before the sum reads it
+    rc = launch_pass<PASS_TRAIN>(g, rays, o->ray_id0, a);
+    if (rc) return rc;
+    if (loss_sum) {
+        k_sum<<<1, 1024, 0, g->stream>>>(scratch, n, loss_sum);
+        SDG_LAUNCH_CHECK("no-alloc loss sum");
     }
     return SDG_OK;
 }
