@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     p.add_argument("--views", type=int, default=N_VIEWS)
+    p.add_argument("--max-blocks", type=int, default=80_000, help="grid capacity (room: 53,855 active blocks)")
     return p.parse_args()
 
 
@@ -60,7 +61,7 @@ def dist_setup(args):
 # ----------------------------------------------------------------------------------------------------------
 # Workload construction
 # ----------------------------------------------------------------------------------------------------------
-def build_workload(sdg, torch, device, n_views, rays_per_step, n_batches=4, seed=0):
+def build_workload(sdg, torch, device, n_views, rays_per_step, n_batches=4, seed=0, max_blocks=80_000):
     import synth
     sc = synth.scene_room(seed)
     poses = synth.random_poses(sc, n_views, seed=seed)
@@ -69,7 +70,7 @@ def build_workload(sdg, torch, device, n_views, rays_per_step, n_batches=4, seed
     depths = [synth.depth_map(sc, T, W, H, K, device=device) for T in poses]
     torch.cuda.synchronize()
     t_depth = time.time() - t0
-    G = sdg.Grid(VS, 160_000, beta=BETA)
+    G = sdg.Grid(VS, max_blocks, beta=BETA)
     # activation: timed separately (all 50 maps), CUDA events on the grid's stream
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
@@ -261,7 +262,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_2305_13220_b300 as sdg
     device = f"cuda:{local}"
-    wl = build_workload(sdg, torch, device, args.views, args.rays, seed=rank)
+    wl = build_workload(sdg, torch, device, args.views, args.rays, seed=rank, max_blocks=args.max_blocks)
     G = wl["grid"]
     n = args.rays
     stream = torch.cuda.current_stream()
