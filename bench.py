@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     p.add_argument("--views", type=int, default=N_VIEWS)
     p.add_argument("--max-blocks", type=int, default=80_000, help="grid capacity (room: 53,855 active blocks)")
+    p.add_argument("--order", default="pixel", choices=["pixel", "drawn"],
+                   help="ray order inside a batch: grouped by view and pixel (a per-image loader) or as drawn")
     return p.parse_args()
 
 
@@ -61,7 +63,8 @@ def dist_setup(args):
 # ----------------------------------------------------------------------------------------------------------
 # Workload construction
 # ----------------------------------------------------------------------------------------------------------
-def build_workload(sdg, torch, device, n_views, rays_per_step, n_batches=4, seed=0, max_blocks=80_000):
+def build_workload(sdg, torch, device, n_views, rays_per_step, n_batches=4, seed=0, max_blocks=80_000,
+                   order="pixel"):
     import synth
     sc = synth.scene_room(seed)
     poses = synth.random_poses(sc, n_views, seed=seed)
@@ -90,7 +93,8 @@ def build_workload(sdg, torch, device, n_views, rays_per_step, n_batches=4, seed
     del vals
     batches = []
     for b in range(n_batches):
-        tb = synth.training_batch(sc, poses, W, H, K, rays_per_step, seed=1000 * seed + b, device=device)
+        tb = synth.training_batch(sc, poses, W, H, K, rays_per_step, seed=1000 * seed + b, device=device,
+                                  order=order)
         batches.append({k: v.contiguous() for k, v in tb.items()})
     torch.cuda.synchronize()
     return {"scene": sc, "poses": poses, "K": K, "grid": G, "keys": keys, "batches": batches, "act_ms": act_ms,
@@ -167,9 +171,10 @@ def cpu_leg(O, batch, seconds, N=N_SAMPLES):
     """Times the oracle's forward + loss + backward on successive 256-ray chunks of the batch until `seconds`
     of CPU time are spent; returns rays/s and the sample description."""
     import oracle
-    rays = batch["rays"].cpu().numpy()
-    t_rgb = batch["rgb"].double().cpu().numpy()
-    t_d = batch["depth"].double().cpu().numpy()
+    perm = np.random.default_rng(0).permutation(batch["rays"].shape[0])   # a sample spread over all views
+    rays = batch["rays"].cpu().numpy()[perm]
+    t_rgb = batch["rgb"].double().cpu().numpy()[perm]
+    t_d = batch["depth"].double().cpu().numpy()[perm]
     done, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds and done < len(rays):
         sl = slice(done, min(done + 256, len(rays)))
@@ -186,7 +191,8 @@ def bytes_per_ray(O, batch, n=1024, N=N_SAMPLES):
     and blocks each ray's stencils touch: voxels x (16 B read + 16 B grad read + 16 B grad write),
     blocks x 40 B (16-B hash slot + 24 B of neighbour table on average... counted as 40 B), ray 32 B,
     targets 16 B, loss 4 B."""
-    rays = batch["rays"][:n].cpu().numpy()
+    idx = np.linspace(0, batch["rays"].shape[0] - 1, n).astype(np.int64)   # spread over all views of the batch
+    rays = batch["rays"][idx].cpu().numpy()
     vx, bl = O.count_touched(rays, N, seed=0)
     per_ray = vx * 48.0 + bl * 40.0 + 32 + 16 + 4
     return float(per_ray.mean()), float(vx.mean()), float(bl.mean())
@@ -262,7 +268,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_2305_13220_b300 as sdg
     device = f"cuda:{local}"
-    wl = build_workload(sdg, torch, device, args.views, args.rays, seed=rank, max_blocks=args.max_blocks)
+    wl = build_workload(sdg, torch, device, args.views, args.rays, seed=rank, max_blocks=args.max_blocks,
+                        order=args.order)
     G = wl["grid"]
     n = args.rays
     stream = torch.cuda.current_stream()

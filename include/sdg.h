@@ -206,8 +206,9 @@ typedef struct {
 /* Forward render of n rays (rays_dev [n][8]).  When ctx is non-NULL, a
  * context for sdg_render_backward is returned; it refers to rays_dev, which
  * must stay unchanged until the backward has run.  In SDG_MODE_STORE the
- * context holds 5 + n_sem floats per sample (device memory allocated on the
- * grid's stream, freed by sdg_ctx_release).  Errors: SDG_ERR_ARG, SDG_ERR_OOM,
+ * context holds 6 words per sample slot (t, sdf, colour, block index;
+ * 32*ceil(N/32) slots per ray, device memory allocated on the grid's stream,
+ * freed by sdg_ctx_release); the backward then re-reads no voxel values.  Errors: SDG_ERR_ARG, SDG_ERR_OOM,
  * SDG_ERR_CUDA. */
 int sdg_render_forward(sdg_grid g, const float* rays_dev, int64_t n, const sdg_render_opts* opts,
                        const sdg_render_out* out, sdg_ctx* ctx);

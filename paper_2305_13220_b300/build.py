@@ -31,16 +31,20 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, jobs: int = 0) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose_ptxas: bool = False, jobs: int = 0, out: str = None,
+          extra_flags=()) -> str:
+    """Compiles every source and links libsdg.so (or `out`); extra_flags are added to each compile."""
+    lib = out or LIB
+    if out is None and not force and not _stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    objdir = os.path.join(HERE, "_build")
+    objdir = os.path.join(HERE, "_build" if out is None else "_build_" + os.path.basename(out))
     os.makedirs(objdir, exist_ok=True)
     common = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
               "--expt-relaxed-constexpr"]
     if verbose_ptxas:
         common += ["-Xptxas", "-v"]
+    common += list(extra_flags)
     objs = []
     procs = []
     for src in sources():
@@ -51,10 +55,10 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int = 0) -> st
     bad = [s for s, p in procs if p.wait() != 0]
     if bad:
         raise RuntimeError(f"nvcc failed for {bad}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -127,7 +127,7 @@ extern "C" int sdg_render_forward(sdg_grid g, const float* rays, int64_t n, cons
     float *rec = nullptr, *rec_S = nullptr;
     const bool store = o->mode == SDG_MODE_STORE && ctx;
     if (store && n > 0) {
-        SDG_CUDA_TRY(cudaMallocAsync((void**)&rec, sizeof(float) * 5 * (size_t)n * 32 * Q, g->stream));
+        SDG_CUDA_TRY(cudaMallocAsync((void**)&rec, sizeof(float) * kRecChannels * (size_t)n * 32 * Q, g->stream));
         cudaError_t e = cudaMallocAsync((void**)&rec_S, sizeof(float) * (size_t)n, g->stream);
         if (e != cudaSuccess) {
             cudaFreeAsync(rec, g->stream);

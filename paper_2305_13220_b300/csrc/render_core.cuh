@@ -3,20 +3,25 @@
 // compositing and its backward.  Paper: arXiv 2305.13220, Sec. 3.5.1
 // (Eq. 12-15) and Sec. 3.5.2 (Eq. 17, trilinear interpolation).
 //
-// Work decomposition (one warp = one ray):
+// Work decomposition (one warp = one ray), chosen so that control flow stays
+// uniform across the warp:
 //  * traversal: the ray's clipped range [t0, t1] is cut into 32 equal pieces;
-//    lane j walks the block cells of piece j (a block-level Amanatides-Woo
-//    walk against the occupancy bitmap) and sums the allocated length S_j.
-//    A sequential shuffle prefix gives each lane its skip-space interval
-//    [P_j, P_{j+1}) (monotone, so the lanes partition [0, S) exactly).
-//  * sampling: lane j walks its piece again and writes t_k for the samples
-//    whose s_k falls in its interval into the warp's shared-memory slots.
-//  * sample work: lane l owns the Q consecutive samples l*Q .. l*Q+Q-1, so
-//    consecutive samples of a lane usually share a voxel cell: the cell's 8
-//    corners (one 16-byte load each in the FP32 layout) are fetched once
-//    per cell, and in the backward the gradient of a run of same-cell
-//    samples is summed in registers and sent with one vector atomic per
-//    corner.  Transmittance is a warp scan over the lanes' optical depths.
+//    lane j walks the block cells of piece j once (a block-level
+//    Amanatides-Woo walk against the occupancy bitmap) and records each
+//    allocated cell it crosses -- t range, block index, block key -- in
+//    shared memory (up to kSegs per piece; a piece with more is re-walked
+//    exactly when one of its samples is placed).  A sequential shuffle prefix
+//    of the pieces' allocated lengths gives the skip-space offsets P_j.
+//  * sampling: lane l owns samples l*Q .. l*Q+Q-1.  It draws s_k itself,
+//    finds its piece by binary search over P and its cell in that piece's
+//    list, so every lane runs the same instructions.
+//  * fetch: every sample loads its 8 corner voxels unconditionally (one
+//    16-byte load each in the FP32 layout; consecutive samples of a lane hit
+//    the same L1 lines), so there is no divergent cell-change branch.
+//  * compositing: transmittance is a warp scan of the lanes' optical depths;
+//    the backward keeps per-sample state in registers, takes the suffix sum
+//    as a reverse warp scan, and sums each run of same-cell samples of a lane
+//    in registers before one vector atomic per corner.
 #pragma once
 
 #include "common.cuh"
@@ -25,8 +30,12 @@ namespace sdg {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWarpsPerBlock = 8;
+constexpr int kSegs = 8;  // allocated cells recorded per lane piece
 
 enum PassMode { PASS_FWD = 0, PASS_FWD_STORE = 1, PASS_BWD = 2, PASS_BWD_STORE = 3, PASS_TRAIN = 4 };
+
+// Store-mode record channels per sample: t, sdf (NaN if invalid), r, g, b, block index (int bits).
+constexpr int kRecChannels = 6;
 
 struct PassArgs {
     int N;  // samples per ray
@@ -35,7 +44,7 @@ struct PassArgs {
     float bg[3];
     int64_t n;  // rays in this launch
     float *out_rgb, *out_depth, *out_opac, *out_sem;
-    float* rec;    // store mode: [5][n][32*Q] (t, sdf or NaN if invalid, r, g, b)
+    float* rec;    // store mode: [kRecChannels][n][32*Q]
     float* rec_S;  // store mode: [n]
     const float *g_rgb, *g_depth, *g_opac, *g_sem;
     const float *t_rgb, *t_depth, *t_sem;
@@ -48,6 +57,17 @@ struct RayJob {
     float tn, tf;
     uint32_t ray_id;
     int64_t idx;  // row of this ray in per-ray arrays
+};
+
+// Per-warp shared memory: the allocated cells of each lane piece (m-major so a
+// lane's writes of one slot are bank-conflict free) and the piece prefixes.
+struct WarpSmem {
+    float tin[kSegs][32];
+    float len[kSegs][32];
+    int blk[kSegs][32];
+    unsigned long long key[kSegs][32];
+    float P[33];
+    int cnt[32];
 };
 
 // ---------------------------------------------------------------------------
@@ -101,8 +121,8 @@ __device__ __forceinline__ bool occupied(const GridDev& g, int cx, int cy, int c
     return (__ldg(g.bitmap + (bit >> 5)) >> (bit & 31)) & 1u;
 }
 
-// Calls f(a, b) for every allocated stretch [a, b) of the ray inside [ta, tb),
-// one call per allocated block cell, in order of increasing t.
+// Calls f(a, b, key) for every allocated block cell the ray crosses inside
+// [ta, tb), in order of increasing t, with [a, b) its stretch of the ray.
 template <class F>
 __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, const float3& d, const float3& invd,
                                            float ta, float tb, F&& f) {
@@ -125,7 +145,8 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
         float tz = sz ? ((float)(g.bmin[2] + cz + (sz > 0)) * g.L - o.z) * invd.z : INF;
         float te = fminf(tx, fminf(ty, tz));
         float b = fminf(te, tb);
-        if (b > tcur && occupied(g, cx, cy, cz)) f(tcur, b);
+        if (b > tcur && occupied(g, cx, cy, cz))
+            f(tcur, b, sdg_pack_key(g.bmin[0] + cx, g.bmin[1] + cy, g.bmin[2] + cz));
         if (!(te < tb)) break;
         if (tx == te) cx += sx;
         if (ty == te) cy += sy;
@@ -137,22 +158,44 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
     }
 }
 
-// Traversal + sample placement.  Writes t_k and s_k (k < N) to ts/ss and
-// s_N = S; returns S (0 when the ray sees no allocated block).
-__device__ __forceinline__ float place_samples(const GridDev& g, const PassArgs& a, const RayJob& j, float* ts,
-                                               float* ss, int lane, SampleGen& gen) {
+struct Pieces {
+    float t0, dt, S;
+    float3 invd;
+};
+
+__device__ __forceinline__ float piece_start(const Pieces& pc, int j) { return fmaf((float)j, pc.dt, pc.t0); }
+__device__ __forceinline__ float piece_end(const Pieces& pc, float t1, int j) {
+    return j == 31 ? t1 : fmaf((float)(j + 1), pc.dt, pc.t0);
+}
+
+// One traversal walk per lane: records the lane piece's allocated cells and
+// returns S, the ray's total allocated length (0 if it sees no block).
+__device__ __forceinline__ float walk_pieces(const GridDev& g, const RayJob& j, WarpSmem& sm, int lane, Pieces& pc,
+                                             float& t1_out) {
     float t0 = j.tn, t1 = j.tf;
     float S_j = 0.f;
-    const float3 invd = make_float3(1.0f / j.d.x, 1.0f / j.d.y, 1.0f / j.d.z);
-    float ta = 0.f, tb = 0.f;
+    int cnt = 0;
+    pc.invd = make_float3(1.0f / j.d.x, 1.0f / j.d.y, 1.0f / j.d.z);
+    pc.t0 = 0.f;
+    pc.dt = 0.f;
     const bool hit = clip_to_grid(g, j.o, j.d, t0, t1);
     if (hit) {
-        const float dt = (t1 - t0) * (1.0f / 32.0f);
-        ta = fmaf((float)lane, dt, t0);
-        tb = lane == 31 ? t1 : fmaf((float)(lane + 1), dt, t0);
-        walk_cells(g, j.o, j.d, invd, ta, tb, [&](float x0, float x1) { S_j += x1 - x0; });
+        pc.t0 = t0;
+        pc.dt = (t1 - t0) * (1.0f / 32.0f);
+        const float ta = piece_start(pc, lane), tb = piece_end(pc, t1, lane);
+        walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, uint64_t key) {
+            if (cnt < kSegs) {
+                sm.tin[cnt][lane] = x0;
+                sm.len[cnt][lane] = x1 - x0;
+                sm.blk[cnt][lane] = sdg_table_find(g.table, g.mask, key);
+                sm.key[cnt][lane] = key;
+            }
+            ++cnt;
+            S_j += x1 - x0;
+        });
     }
-    // sequential prefix: P_{j+1} = fl(P_j + S_j) exactly, so the intervals tile [0, S)
+    t1_out = t1;
+    // sequential prefix: P_{j+1} = fl(P_j + S_j) exactly, so the pieces tile [0, S) monotonically
     float P = 0.f;
 #pragma unroll
     for (int i = 0; i < 31; ++i) {
@@ -160,75 +203,77 @@ __device__ __forceinline__ float place_samples(const GridDev& g, const PassArgs&
         if (i < lane) P += v;
     }
     const float S = __shfl_sync(kFull, P + S_j, 31);
-    float hi = __shfl_down_sync(kFull, P, 1);
-    if (lane == 31) hi = S;
-    gen.s_over_n = S / (float)a.N;
-    gen.s_max = __int_as_float(__float_as_int(S) - 1);  // largest float below S (S > 0)
-    if (!(S > 0.f)) return 0.f;
-    const int N = a.N;
-    if (hi > P) {
-        int k = max(0, (int)(P / gen.s_over_n) - 1);
-        while (k < N && gen.s(k) < P) ++k;
-        float scur = P, pa = 0.f, ps = 0.f, plen = 0.f;
-        bool have = false;
-        auto flush = [&](float bound) {
-            while (k < N) {
-                float sk = gen.s(k);
-                if (!(sk < bound && sk < hi)) break;
-                ts[k] = pa + fminf(fmaxf(sk - ps, 0.f), plen);
-                ss[k] = sk;
-                ++k;
-            }
-        };
-        walk_cells(g, j.o, j.d, invd, ta, tb, [&](float x0, float x1) {
-            if (have) flush(ps + plen);
-            pa = x0;
-            ps = scur;
-            plen = x1 - x0;
-            scur += plen;
-            have = true;
-        });
-        if (have) flush(hi);
-    }
-    if (lane == 0) ss[N] = S;
+    sm.P[lane] = P;
+    sm.cnt[lane] = cnt;
+    if (lane == 0) sm.P[32] = S;
     __syncwarp();
+    pc.S = S;
     return S;
+}
+
+// t, block index and block key of skip-space position s (0 <= s < S).
+__device__ __forceinline__ float locate(const GridDev& g, const RayJob& j, const WarpSmem& sm, const Pieces& pc,
+                                        float t1, float s, int& blk, uint64_t& key) {
+    int jp = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (sm.P[jp + step] <= s) jp += step;
+    float local = s - sm.P[jp];
+    const int cnt = sm.cnt[jp];
+    if (cnt <= kSegs) {
+        int m = 0;
+        for (; m < cnt - 1; ++m) {
+            const float l = sm.len[m][jp];
+            if (local < l) break;
+            local -= l;
+        }
+        blk = sm.blk[m][jp];
+        key = sm.key[m][jp];
+        return sm.tin[m][jp] + fminf(local, sm.len[m][jp]);
+    }
+    // the piece had more allocated cells than were recorded: walk it again
+    float ta = piece_start(pc, jp), tb = piece_end(pc, t1, jp);
+    float t = ta, best_a = ta, best_len = 0.f;
+    uint64_t best_key = SDG_EMPTY_KEY;
+    bool found = false;
+    walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, uint64_t k) {
+        if (found) return;
+        best_a = x0;
+        best_len = x1 - x0;
+        best_key = k;
+        if (local < best_len) {
+            found = true;
+            return;
+        }
+        local -= best_len;
+    });
+    t = best_a + fminf(local, best_len);
+    key = best_key;
+    blk = best_key == SDG_EMPTY_KEY ? -1 : sdg_table_find(g.table, g.mask, best_key);
+    return t;
 }
 
 // ---------------------------------------------------------------------------
 // Voxel stencil of a cell (Eq. 17): the 8 grid points around x
 // ---------------------------------------------------------------------------
-struct BlockCache {
-    uint64_t key;
-    int32_t blk;
-};
+// Cell packed as lx | ly << 3 | lz << 6 (local coordinates of its base corner).
+__device__ __forceinline__ int corner_nb(int m, int4 n0, int4 n1) {
+    // neighbour block for overflow mask m (bit 0 = +x, bit 1 = +y, bit 2 = +z)
+    const int lo = (m & 1) ? ((m & 2) ? n0.w : n0.y) : ((m & 2) ? n0.z : n0.x);
+    const int hi = (m & 1) ? ((m & 2) ? n1.w : n1.y) : ((m & 2) ? n1.z : n1.x);
+    return (m & 4) ? hi : lo;
+}
 
-// Resolves the 8 corner voxel addresses of the cell whose base grid point is
-// (cx, cy, cz).  False if any corner's block is not allocated.
-__device__ __forceinline__ bool cell_addresses(const GridDev& g, int cx, int cy, int cz, BlockCache& bc, int addr[8]) {
-    const uint64_t key = sdg_pack_key(cx >> 3, cy >> 3, cz >> 3);
-    if (key != bc.key) {
-        bc.key = key;
-        bc.blk = sdg_table_find(g.table, g.mask, key);
-    }
-    const int b = bc.blk;
-    if (b < 0) return false;
-    const int lx = cx & 7, ly = cy & 7, lz = cz & 7;
+// Addresses of the 8 corners of cell `lcell` of block `blk`; false if a corner's block is absent.
+__device__ __forceinline__ bool corner_addresses(const GridDev& g, int blk, int lcell, int addr[8]) {
+    const int lx = lcell & 7, ly = (lcell >> 3) & 7, lz = lcell >> 6;
     const int ovf = (lx == 7) | ((ly == 7) << 1) | ((lz == 7) << 2);
-    int nb[8];
-    if (ovf) {
-        int4 n0 = __ldg(g.nbr + 2 * b), n1 = __ldg(g.nbr + 2 * b + 1);
-        nb[0] = n0.x; nb[1] = n0.y; nb[2] = n0.z; nb[3] = n0.w;
-        nb[4] = n1.x; nb[5] = n1.y; nb[6] = n1.z; nb[7] = n1.w;
-    } else {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) nb[m] = b;
-    }
+    const int4 n0 = __ldg(g.nbr + 2 * blk), n1 = __ldg(g.nbr + 2 * blk + 1);
     bool ok = true;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
-        const int be = nb[e & ovf];
+        const int be = corner_nb(e & ovf, n0, n1);
         ok = ok && be >= 0;
         addr[e] = be * 512 + (((lz + ez) & 7) << 6) + (((ly + ey) & 7) << 3) + ((lx + ex) & 7);
     }
@@ -257,7 +302,6 @@ __device__ __forceinline__ void trilinear_weights(float fx, float fy, float fz, 
     w[4] = gx * gy * fz; w[5] = fx * gy * fz; w[6] = gx * fy * fz; w[7] = fx * fy * fz;
 }
 
-// sum over 4 semantic channels c0..c0+3 of one corner, weighted
 __device__ __forceinline__ void sem_load4(const GridDev& g, int addr, int c0, float v[4]) {
     uint2 u = __ldg(reinterpret_cast<const uint2*>(g.sem + (int64_t)addr * g.n_sem + c0));
     v[0] = sdg_bf16_lo(u.x); v[1] = sdg_bf16_hi(u.x); v[2] = sdg_bf16_lo(u.y); v[3] = sdg_bf16_hi(u.y);
@@ -300,8 +344,8 @@ __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x <
 // The per-ray program
 // ---------------------------------------------------------------------------
 template <int MODE, bool BF16, bool SEM, int Q>
-__device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a, const RayJob& j, float* ts,
-                                            float* ss, int lane) {
+__device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a, const RayJob& j, WarpSmem& sm,
+                                            int lane) {
     constexpr bool kStoreIn = MODE == PASS_BWD_STORE;
     constexpr bool kStoreOut = MODE == PASS_FWD_STORE;
     constexpr bool kBwd = MODE == PASS_BWD || MODE == PASS_BWD_STORE || MODE == PASS_TRAIN;
@@ -315,101 +359,109 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     gen.seed_h = pcg_hash(a.seed);
     gen.ray_id = j.ray_id;
     gen.strat = a.strat;
+    Pieces pc;
+    float t1 = 0.f;
     float S;
     if constexpr (kStoreIn) {
         S = a.rec_S[j.idx];
-        gen.s_over_n = S / (float)N;
-        gen.s_max = __int_as_float(__float_as_int(S) - 1);
     } else {
-        S = place_samples(g, a, j, ts, ss, lane, gen);
+        S = walk_pieces(g, j, sm, lane, pc, t1);
     }
     if constexpr (kStoreOut) {
         if (lane == 0) a.rec_S[j.idx] = S;
     }
     const bool any = S > 0.f;
+    gen.s_over_n = S / (float)N;
+    gen.s_max = __int_as_float(__float_as_int(S) - 1);  // largest float below S (S > 0)
 
-    // ---------------- phase A: evaluate this lane's samples ----------------
+    // ---------------- phase A: place and evaluate this lane's samples ----------------
+    float s_[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int k = lane * Q + i;
+        s_[i] = (any && k < N) ? gen.s(k) : 0.f;
+    }
+    const float s_after = __shfl_down_sync(kFull, s_[0], 1);  // first sample of the next lane
+
     float t_[Q], dl_[Q], d_[Q], cr_[Q], cg_[Q], cb_[Q], tau_[Q], dsig_[Q], fx_[Q], fy_[Q], fz_[Q];
-    int cx_[Q], cy_[Q], cz_[Q];
+    int blk_[Q], lc_[Q];
     unsigned vmask = 0;
-    BlockCache bc{SDG_EMPTY_KEY, -1};
-    {
-        int ccx = INT32_MIN, ccy = 0, ccz = 0;  // cell whose corners are loaded
-        bool cvalid = false;
-        int addr[8];
-        float cs[8], crr[8], cgg[8], cbb[8];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int k = lane * Q + i;
-            t_[i] = 0.f; dl_[i] = 0.f; d_[i] = 0.f; cr_[i] = cg_[i] = cb_[i] = 0.f; tau_[i] = 0.f; dsig_[i] = 0.f;
-            fx_[i] = fy_[i] = fz_[i] = 0.f; cx_[i] = cy_[i] = cz_[i] = 0;
-            if (!any || k >= N) continue;
-            float sk, sn;
-            bool stored_valid = true;
-            if constexpr (kStoreIn) {
-                const float* rec = a.rec + j.idx * RS + i * 32 + lane;
-                const int64_t CS = a.n * RS;
-                t_[i] = rec[0];
-                d_[i] = rec[CS];
-                cr_[i] = rec[2 * CS];
-                cg_[i] = rec[3 * CS];
-                cb_[i] = rec[4 * CS];
-                stored_valid = !isnan(d_[i]);
-                sk = gen.s(k);
-                sn = k + 1 < N ? gen.s(k + 1) : S;
-            } else {
-                t_[i] = ts[k];
-                sk = ss[k];
-                sn = ss[k + 1];
-            }
-            dl_[i] = sn - sk;
-            const float px = fmaf(t_[i], j.d.x, j.o.x) * g.inv_vs;
-            const float py = fmaf(t_[i], j.d.y, j.o.y) * g.inv_vs;
-            const float pz = fmaf(t_[i], j.d.z, j.o.z) * g.inv_vs;
-            const float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
-            cx_[i] = (int)flx; cy_[i] = (int)fly; cz_[i] = (int)flz;
-            fx_[i] = px - flx; fy_[i] = py - fly; fz_[i] = pz - flz;
-            bool valid;
-            if constexpr (kStoreIn) {
-                valid = stored_valid;
-            } else {
-                if (cx_[i] != ccx || cy_[i] != ccy || cz_[i] != ccz) {
-                    ccx = cx_[i]; ccy = cy_[i]; ccz = cz_[i];
-                    cvalid = cell_addresses(g, ccx, ccy, ccz, bc, addr);
-                    if (cvalid) load_corners<BF16>(g, addr, cs, crr, cgg, cbb);
-                }
-                valid = cvalid;
-                if (valid) {
-                    float w[8];
-                    trilinear_weights(fx_[i], fy_[i], fz_[i], w);
-                    float dd = 0.f, r = 0.f, gg = 0.f, bb = 0.f;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        dd = fmaf(w[e], cs[e], dd);
-                        r = fmaf(w[e], crr[e], r);
-                        gg = fmaf(w[e], cgg[e], gg);
-                        bb = fmaf(w[e], cbb[e], bb);
-                    }
-                    d_[i] = dd; cr_[i] = r; cg_[i] = gg; cb_[i] = bb;
-                }
-            }
+    for (int i = 0; i < Q; ++i) {
+        const int k = lane * Q + i;
+        t_[i] = 0.f; dl_[i] = 0.f; d_[i] = 0.f; cr_[i] = cg_[i] = cb_[i] = 0.f; tau_[i] = 0.f; dsig_[i] = 0.f;
+        fx_[i] = fy_[i] = fz_[i] = 0.f; blk_[i] = -1; lc_[i] = 0;
+        if (!any || k >= N) continue;
+        float sn;
+        if (k + 1 >= N) sn = S;
+        else if (i + 1 < Q) sn = s_[i + 1 < Q ? i + 1 : i];
+        else sn = s_after;
+        dl_[i] = sn - s_[i];
+        int blk = -1;
+        uint64_t key = SDG_EMPTY_KEY;
+        bool stored_valid = true;
+        if constexpr (kStoreIn) {
+            const float* rec = a.rec + j.idx * RS + i * 32 + lane;
+            const int64_t CS = a.n * RS;
+            t_[i] = rec[0];
+            d_[i] = rec[CS];
+            cr_[i] = rec[2 * CS];
+            cg_[i] = rec[3 * CS];
+            cb_[i] = rec[4 * CS];
+            blk = __float_as_int(rec[5 * CS]);
+            stored_valid = !isnan(d_[i]);
+        } else {
+            t_[i] = locate(g, j, sm, pc, t1, s_[i], blk, key);
+        }
+        const float px = fmaf(t_[i], j.d.x, j.o.x) * g.inv_vs;
+        const float py = fmaf(t_[i], j.d.y, j.o.y) * g.inv_vs;
+        const float pz = fmaf(t_[i], j.d.z, j.o.z) * g.inv_vs;
+        const float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
+        const int cx = (int)flx, cy = (int)fly, cz = (int)flz;
+        fx_[i] = px - flx; fy_[i] = py - fly; fz_[i] = pz - flz;
+        lc_[i] = (cx & 7) | ((cy & 7) << 3) | ((cz & 7) << 6);
+        bool valid;
+        if constexpr (kStoreIn) {
+            valid = stored_valid;
+        } else {
+            // the sample's own block: the traversal cell's, unless rounding put it across a block face
+            const uint64_t own = sdg_pack_key(cx >> 3, cy >> 3, cz >> 3);
+            if (own != key) blk = sdg_table_find(g.table, g.mask, own);
+            int addr[8];
+            valid = blk >= 0 && corner_addresses(g, blk, lc_[i], addr);
             if (valid) {
-                vmask |= 1u << i;
-                // sigma = Psi_beta(-d) / beta, the Laplace CDF transform (Sec. 3.5.1)
-                const float e = __expf(-fabsf(d_[i]) * g.inv_beta);
-                const float sig = d_[i] >= 0.f ? 0.5f * g.inv_beta * e : g.inv_beta * (1.f - 0.5f * e);
-                tau_[i] = sig * dl_[i];
-                dsig_[i] = -0.5f * g.inv_beta * g.inv_beta * e * dl_[i];  // delta * dsigma/dd
+                float cs[8], crr[8], cgg[8], cbb[8], w[8];
+                load_corners<BF16>(g, addr, cs, crr, cgg, cbb);
+                trilinear_weights(fx_[i], fy_[i], fz_[i], w);
+                float dd = 0.f, r = 0.f, gg = 0.f, bb = 0.f;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    dd = fmaf(w[e], cs[e], dd);
+                    r = fmaf(w[e], crr[e], r);
+                    gg = fmaf(w[e], cgg[e], gg);
+                    bb = fmaf(w[e], cbb[e], bb);
+                }
+                d_[i] = dd; cr_[i] = r; cg_[i] = gg; cb_[i] = bb;
             }
-            if constexpr (kStoreOut) {
-                float* rec = a.rec + j.idx * RS + i * 32 + lane;
-                const int64_t CS = a.n * RS;
-                rec[0] = t_[i];
-                rec[CS] = valid ? d_[i] : __int_as_float(0x7fc00000);
-                rec[2 * CS] = cr_[i];
-                rec[3 * CS] = cg_[i];
-                rec[4 * CS] = cb_[i];
-            }
+        }
+        blk_[i] = blk;
+        if (valid) {
+            vmask |= 1u << i;
+            // sigma = Psi_beta(-d) / beta, the Laplace CDF transform (Sec. 3.5.1)
+            const float e = __expf(-fabsf(d_[i]) * g.inv_beta);
+            const float sig = d_[i] >= 0.f ? 0.5f * g.inv_beta * e : g.inv_beta * (1.f - 0.5f * e);
+            tau_[i] = sig * dl_[i];
+            dsig_[i] = -0.5f * g.inv_beta * g.inv_beta * e * dl_[i];  // delta * dsigma/dd
+        }
+        if constexpr (kStoreOut) {
+            float* rec = a.rec + j.idx * RS + i * 32 + lane;
+            const int64_t CS = a.n * RS;
+            rec[0] = t_[i];
+            rec[CS] = valid ? d_[i] : __int_as_float(0x7fc00000);
+            rec[2 * CS] = cr_[i];
+            rec[3 * CS] = cg_[i];
+            rec[4 * CS] = cb_[i];
+            rec[5 * CS] = __int_as_float(blk);
         }
     }
 
@@ -433,15 +485,21 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         }
     }
 
-    // semantic logits: per run of same-cell samples, corner weights W_e = sum_i w_i r_e(f_i)
+    // runs: consecutive valid samples of a lane in the same cell share their 8 corners
+    auto same_cell = [&](int i0, int i1) { return blk_[i0] == blk_[i1] && lc_[i0] == lc_[i1]; };
+    auto run_start = [&](int i) {
+        return ((vmask >> i) & 1u) && (i == 0 || !((vmask >> (i - 1)) & 1u) || !same_cell(i - 1, i));
+    };
+    auto run_end = [&](int i) {
+        return ((vmask >> i) & 1u) && (i == Q - 1 || !((vmask >> (i + 1)) & 1u) || !same_cell(i, i + 1));
+    };
+
+    // semantic logits: per run, corner weights W_e = sum_i w_i r_e(f_i)
     float sem_acc[SEMCAP > 0 ? SEMCAP : 1];
     if constexpr (SEM) {
 #pragma unroll
         for (int c = 0; c < SEMCAP; ++c) sem_acc[c] = 0.f;
     }
-    // run iteration helper: same cell and valid
-    auto same_cell = [&](int i0, int i1) { return cx_[i0] == cx_[i1] && cy_[i0] == cy_[i1] && cz_[i0] == cz_[i1]; };
-
     if constexpr (SEM && (kFwdOut || MODE == PASS_TRAIN)) {
         if (any) {
             float W[8];
@@ -449,12 +507,10 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const bool v = (vmask >> i) & 1u;
-                const bool start = v && (i == 0 || !((vmask >> (i - 1)) & 1u) || !same_cell(i - 1, i));
-                const bool end = v && (i == Q - 1 || !((vmask >> (i + 1)) & 1u) || !same_cell(i, i + 1));
-                if (start) {
+                if (run_start(i)) {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) W[e] = 0.f;
-                    cell_addresses(g, cx_[i], cy_[i], cz_[i], bc, addr);
+                    corner_addresses(g, blk_[i], lc_[i], addr);
                 }
                 if (v) {
                     float r[8];
@@ -462,7 +518,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 #pragma unroll
                     for (int e = 0; e < 8; ++e) W[e] = fmaf(w_[i], r[e], W[e]);
                 }
-                if (end) {
+                if (run_end(i)) {
 #pragma unroll
                     for (int c4 = 0; c4 < SEMCAP / 4; ++c4) {
                         if (4 * c4 < ns) {
@@ -571,10 +627,8 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             float dot[8];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const bool v = (vmask >> i) & 1u;
-                const bool start = v && (i == 0 || !((vmask >> (i - 1)) & 1u) || !same_cell(i - 1, i));
-                if (start) {
-                    cell_addresses(g, cx_[i], cy_[i], cz_[i], bc, addr);
+                if (run_start(i)) {
+                    corner_addresses(g, blk_[i], lc_[i], addr);
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         dot[e] = 0.f;
@@ -588,7 +642,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                             }
                     }
                 }
-                if (v) {
+                if ((vmask >> i) & 1u) {
                     float r[8];
                     trilinear_weights(fx_[i], fy_[i], fz_[i], r);
                     float acc = 0.f;
@@ -621,12 +675,10 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const bool v = (vmask >> i) & 1u;
-            const bool start = v && (i == 0 || !((vmask >> (i - 1)) & 1u) || !same_cell(i - 1, i));
-            const bool end = v && (i == Q - 1 || !((vmask >> (i + 1)) & 1u) || !same_cell(i, i + 1));
-            if (start) {
+            if (run_start(i)) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) aS[e] = aR[e] = aG[e] = aB[e] = aW[e] = 0.f;
-                cell_addresses(g, cx_[i], cy_[i], cz_[i], bc, addr);
+                corner_addresses(g, blk_[i], lc_[i], addr);
             }
             if (v) {
                 float r[8];
@@ -641,7 +693,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                     if constexpr (SEM) aW[e] = fmaf(r[e], w_[i], aW[e]);
                 }
             }
-            if (end) {
+            if (run_end(i)) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     if constexpr (!BF16) {

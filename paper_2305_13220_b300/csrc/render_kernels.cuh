@@ -4,12 +4,16 @@
 
 #include "render_core.cuh"
 
+#ifndef SDG_RENDER_MIN_BLOCKS
+#define SDG_RENDER_MIN_BLOCKS 1
+#endif
+
 namespace sdg {
 
 template <int MODE, bool BF16, bool SEM, int Q>
-__global__ void __launch_bounds__(256) k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0,
+__global__ void __launch_bounds__(256, SDG_RENDER_MIN_BLOCKS) k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0,
                                                 PassArgs a) {
-    __shared__ float smem[kWarpsPerBlock][64 * Q + 1];
+    __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (r >= a.n) return;  // warp-uniform
@@ -22,7 +26,7 @@ __global__ void __launch_bounds__(256) k_render(GridDev g, const float* __restri
     j.tf = r1.w;
     j.ray_id = ray_id0 + (uint32_t)r;
     j.idx = r;
-    ray_program<MODE, BF16, SEM, Q>(g, a, j, smem[warp], smem[warp] + 32 * Q, lane);
+    ray_program<MODE, BF16, SEM, Q>(g, a, j, smem[warp], lane);
 }
 
 template <int MODE, bool BF16, bool SEM>

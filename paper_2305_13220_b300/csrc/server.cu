@@ -47,7 +47,7 @@ struct ChunkDesc {
 template <bool BF16, int Q>
 __global__ void __launch_bounds__(256) k_serve(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks,
                                                int chunk_rays) {
-    __shared__ float smem[kWarpsPerBlock][64 * Q + 1];
+    __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     const int c = (int)(w / chunk_rays);
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_serve(const GridDev* __restrict__ scene
     a.out_rgb = ch.rgb;
     a.out_depth = ch.depth;
     a.out_opac = ch.opac;
-    ray_program<PASS_FWD, BF16, false, Q>(scenes[ch.scene], a, j, smem[warp], smem[warp] + 32 * Q, lane);
+    ray_program<PASS_FWD, BF16, false, Q>(scenes[ch.scene], a, j, smem[warp], lane);
 }
 
 double now_ms() {

@@ -424,15 +424,22 @@ def view_rays(Twc: np.ndarray, W: int, H: int, K, device="cpu", tnear=0.05, tfar
 
 
 def training_batch(scene: Scene, poses: np.ndarray, W: int, H: int, K, n_rays: int, seed: int = 0,
-                   device="cpu", n_sem: int = 0, tnear=0.05, tfar=1.0e3):
+                   device="cpu", n_sem: int = 0, tnear=0.05, tfar=1.0e3, order: str = "drawn"):
     """n_rays rays drawn uniformly (seeded) over the pixels of the given views, with analytic targets.
 
+    order="drawn" keeps the draw order; order="pixel" lists the same rays grouped by view and sorted by pixel
+    index, as a loader that draws rays per image would hand them over (same set of rays, other order).
     Returns dict: rays (n,8) f32, rgb (n,3) f32 = colour at the first hit, depth (n,) f32 = hit distance
     along the unit ray, and, if n_sem, sem (n, n_sem) f32 = 4*onehot(hit label mod n_sem)."""
     g = torch.Generator(device="cpu")
     g.manual_seed(40000 + seed)
     view = torch.randint(0, poses.shape[0], (n_rays,), generator=g)
     pix = torch.randint(0, W * H, (n_rays,), generator=g)
+    if order == "pixel":
+        perm = torch.argsort(view * (W * H) + pix, stable=True)
+        view, pix = view[perm], pix[perm]
+    elif order != "drawn":
+        raise ValueError(order)
     u = (pix % W).to(F64)
     v = (pix // W).to(F64)
     fx, fy, cx, cy = K
