@@ -43,9 +43,30 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     p.add_argument("--views", type=int, default=N_VIEWS)
     p.add_argument("--max-blocks", type=int, default=80_000, help="grid capacity (room: 53,855 active blocks)")
+    p.add_argument("--config", default="room", choices=["room", "room_bf16_sem", "serve", "apartment"],
+                   help="room: the headline training step; the others are the precision, serving and apartment "
+                        "workloads (one JSON line each)")
+    p.add_argument("--requests", type=int, default=2000, help="serve: requests per arrival rate")
     p.add_argument("--order", default="pixel", choices=["pixel", "drawn"],
                    help="ray order inside a batch: grouped by view and pixel (a per-image loader) or as drawn")
     return p.parse_args()
+
+
+def reduce_max(x: float, device=None) -> float:
+    """Max of x over all ranks (identity without torch.distributed); the timing rule takes the slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = device if (device is not None and dist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rays_per_s(world: int, rays_per_rank: int, ms_per_step_max: float) -> float:
+    """Whole-job throughput: the rays all ranks processed in one step over the slowest rank's step time."""
+    return world * rays_per_rank / (ms_per_step_max / 1e3)
 
 
 def dist_setup(args):
@@ -308,15 +329,11 @@ def run_ours(args):
     end.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total_ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = reduce_max(start.elapsed_time(end), device)
     train_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     adam_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
     ms_step = total_ms / K
-    value = world * n / (ms_step / 1e3)
+    value = aggregate_rays_per_s(world, n, ms_step)
 
     # end to end through the public API: pinned host inputs copied in, loss read back, every step
     hb = [{k: v.cpu().pin_memory() for k, v in b.items() if k in ("rays", "rgb", "depth")} for b in wl["batches"]]
@@ -338,11 +355,7 @@ def run_ours(args):
         host_loss.copy_(loss_sum, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / K
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = t.item()
+    e2e_ms = reduce_max(e0.elapsed_time(e1) / K, device)
 
     res = None
     if rank == 0:
@@ -364,7 +377,7 @@ def run_ours(args):
                 "phases": {"train_kernel_ms": round(train_ms, 4), "adam_ms": round(adam_ms, 4),
                            "activation_ms_50_maps": round(wl["act_ms"], 3)},
                 "clocks": clk, "gpu_launches": 3 * K,
-                "e2e": {"value": round(world * n / (e2e_ms / 1e3), 1), "unit": "rays/s",
+                "e2e": {"value": round(aggregate_rays_per_s(world, n, e2e_ms), 1), "unit": "rays/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}}
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
@@ -403,6 +416,255 @@ def run_ours(args):
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return res
+
+
+# ----------------------------------------------------------------------------------------------------------
+# Other workloads: precision variant, serving, apartment
+# ----------------------------------------------------------------------------------------------------------
+def _timed_steps(torch, step, batches, K, W_):
+    for i in range(W_):
+        step(batches[i % len(batches)], i)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for i in range(K):
+        step(batches[i % len(batches)], 1000 + i)
+    s1.record()
+    torch.cuda.synchronize()
+    return s0.elapsed_time(s1) / K
+
+
+def _activate_views(sdg, torch, G, sc, poses, K, device, band):
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    import synth
+    ms = 0.0
+    for T in poses:
+        d = synth.depth_map(sc, T, W, H, K, device=device)
+        t0.record()
+        G.activate_depth(d, K, T, band)
+        t1.record()
+        torch.cuda.synchronize()
+        ms += t0.elapsed_time(t1)
+    return ms
+
+
+def _fill(sdg, torch, G, sc, vs, band, device, n_sem=0):
+    import synth
+    A = sdg._abi
+    keys = G.keys().cpu().numpy()
+    nb = len(keys)
+    vals = synth.fill_grid(sc, keys, vs, band, n_sem=n_sem, device=device)
+    if G.rgb_dtype == "f32":
+        geo = G.channel(A.GROUP_GEO)
+        geo[:nb, :, 0] = vals["sdf"].to(torch.float32)
+        geo[:nb, :, 1:4] = vals["rgb"].to(torch.float32)
+    else:
+        G.channel(A.GROUP_SDF)[:nb, :, 0] = vals["sdf"].to(torch.float32)
+        ch = G.channel(A.GROUP_RGB)
+        ch[:nb, :, 0:3] = vals["rgb"].to(torch.bfloat16)
+        ch[:nb, :, 3] = 0
+    if n_sem:
+        G.channel(A.GROUP_SEM)[:nb] = vals["sem"].to(torch.bfloat16)
+    return keys, vals
+
+
+def _line(value, unit, K, W_, ms, config, **extra):
+    d = {"metric": METRIC, "value": round(value, 1), "unit": unit, "n_gpus": 1, "steps": K, "warmup": W_,
+         "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+         "dtype": "f32", "data": "synthetic", "config": config}
+    d.update(extra)
+    return d
+
+
+def run_precision(args):
+    """Room-scale step with BF16 colour and 20 BF16 semantic logits; per-output errors vs the FP64 oracle."""
+    import torch
+    import oracle
+    import paper_2305_13220_b300 as sdg
+    import synth
+    device = "cuda:0"
+    sc = synth.scene_room(0)
+    poses = synth.random_poses(sc, args.views, seed=0)
+    K = synth.intrinsics(W, H)
+    G = sdg.Grid(VS, args.max_blocks, beta=BETA, rgb_dtype="bf16", n_sem=20)
+    _activate_views(sdg, torch, G, sc, poses, K, device, BAND)
+    keys, vals = _fill(sdg, torch, G, sc, VS, BAND, device, n_sem=20)
+    batches = [synth.training_batch(sc, poses, W, H, K, args.rays, seed=b, device=device, n_sem=20,
+                                    order=args.order) for b in range(4)]
+
+    def step(b, i):
+        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i)
+        G.adam_step(lr=1e-3)
+
+    ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
+    # error table on 4096 rays spread over the views: GPU (BF16 storage) vs the FP64 oracle on the unrounded
+    # generator values, and vs the oracle on the stored (rounded) values (the parity check)
+    A = sdg._abi
+    nb = len(keys)
+    G.zero_grad()
+    sub = batches[0]["rays"][torch.linspace(0, args.rays - 1, 4096, device=device).long()].contiguous()
+    out = sdg.render(G, sub, N_SAMPLES, seed=0, want_ctx=True)
+    n = sub.shape[0]
+    gen = torch.Generator(device=device).manual_seed(0)
+    seeds = [torch.randn(sh, generator=gen, device=device) * 1e-3 for sh in ((n, 3), (n,), (n,), (n, 20))]
+    sdg.backward(out["ctx"], *seeds)
+    torch.cuda.synchronize()
+    stored = {"sdf": G.channel(A.GROUP_SDF)[:nb, :, 0].double().cpu().numpy(),
+              "rgb": G.channel(A.GROUP_RGB)[:nb, :, 0:3].double().cpu().numpy(),
+              "sem": G.channel(A.GROUP_SEM)[:nb].double().cpu().numpy()}
+    full = {"sdf": vals["sdf"].to(torch.float32).double().cpu().numpy(), "rgb": vals["rgb"].cpu().numpy(),
+            "sem": vals["sem"].cpu().numpy()}
+    del vals
+    got = {k: out[k].double().cpu().numpy() for k in ("rgb", "depth", "opac", "sem")}
+    ggot = {"sdf": G.channel(A.GROUP_SDF, A.KIND_GRAD)[:nb, :, 0].double().cpu().numpy(),
+            "rgb": G.channel(A.GROUP_RGB, A.KIND_GRAD)[:nb, :, 0:3].double().cpu().numpy(),
+            "sem": G.channel(A.GROUP_SEM, A.KIND_GRAD)[:nb].double().cpu().numpy()}
+    rays_np = sub.cpu().numpy()
+    sd = [s.double().cpu().numpy() for s in seeds]
+    table = {}
+    for name, src in (("vs_fp64_unrounded", full), ("vs_fp64_same_bf16_values", stored)):
+        O = oracle.Grid(VS, BETA, 20).set(keys, src["sdf"], src["rgb"], src["sem"])
+        ref = O.render(rays_np, N_SAMPLES, seed=0)
+        nd = ~ref["degenerate"]
+        row = {k: float(np.abs(got[k] - ref[k])[nd].max()) for k in ("rgb", "depth", "opac", "sem")}
+        gref = O.backward(rays_np, N_SAMPLES, sd[0], sd[1], sd[2], sd[3], seed=0)
+        for k in ("sdf", "rgb", "sem"):
+            row["grad_" + k + "_rel"] = float(np.abs(ggot[k] - gref[k]).max() / max(np.abs(gref[k]).max(), 1e-30))
+        row["degenerate_rays"] = int((~nd).sum())
+        table[name] = row
+        del O
+    line = _line(args.rays / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
+                 {"workload": "precision variant of the room step: BF16 colour + 20 BF16 semantic logits, FP32 "
+                              "SDF / transmittance / accumulation", "rays_per_step": args.rays,
+                  "samples_per_ray": N_SAMPLES, "n_blocks": nb},
+                 dtype="f32+bf16", samples_per_s=round(args.rays * N_SAMPLES / (ms / 1e3), 1),
+                 errors_on_4096_rays=table, gpu_launches=5 * args.steps)
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """8 device-resident rooms (10k-200k blocks, 1-2 cm voxels, BF16 colour); Poisson arrivals at 0.5x, 0.8x and
+    1.0x of the measured saturated capacity; latency = submit -> result ready (host clock)."""
+    import torch
+    import paper_2305_13220_b300 as sdg
+    import synth
+    device = "cuda:0"
+    specs = [((4, 4, 3), 0.02), ((6, 5, 3), 0.02), ((5, 5, 3), 0.015), ((7, 6, 3), 0.015),
+             ((4, 3, 2.7), 0.01), ((6, 6, 3), 0.01), ((5, 4, 3), 0.01), ((8, 6, 3), 0.01)]
+    grids, scenes = [], []
+    for i, (size, vs) in enumerate(specs):
+        sc = synth.scene_room(100 + i, size=size, n_objects=6 + i)
+        poses = synth.random_poses(sc, 24, seed=i)
+        G = sdg.Grid(vs, 260_000, beta=0.5 * vs, rgb_dtype="bf16")
+        _activate_views(sdg, torch, G, sc, poses, synth.intrinsics(W, H), device, 3)
+        _fill(sdg, torch, G, sc, vs, 3, device)
+        grids.append(G)
+        scenes.append(sc)
+    srv = sdg.Server(hbm_budget_bytes=4 << 30, max_slots=32, n_streams=4, chunk_rays=4096, max_batch_rays=1 << 18)
+    ids = [srv.add_scene(G) for G in grids]
+    res = [(160, 120), (320, 240), (640, 480), (1280, 960)]
+    rng = np.random.default_rng(0)
+    poses = [synth.random_poses(sc, 8, seed=50) for sc in scenes]
+
+    def req(i):
+        s = int(rng.integers(0, 8))
+        w, h = res[int(rng.integers(0, 4))]
+        return ids[s], h, w, synth.intrinsics(w, h), poses[s][i % 8]
+
+    # saturated capacity: 64 mixed requests submitted at once
+    reqs = [req(i) for i in range(64)]
+    t = srv.submit(*reqs[0][:3], reqs[0][3], reqs[0][4], n_samples=N_SAMPLES)
+    srv.wait(t, 300000)
+    srv.release(t)
+    t0 = time.perf_counter()
+    tk = [(srv.submit(s, h, w, Kq, T, n_samples=N_SAMPLES, seed=i), h * w) for i, (s, h, w, Kq, T) in enumerate(reqs)]
+    rays = 0
+    for t, nr in tk:
+        srv.wait(t, 300000)
+        srv.release(t)
+        rays += nr
+    cap = rays / (time.perf_counter() - t0)
+    mean_rays = np.mean([w * h for w, h in res])
+    points = []
+    for frac in (0.5, 0.8, 1.0):
+        rate = frac * cap / mean_rays
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=args.requests))
+        tickets = []
+        start = time.perf_counter()
+        for i in range(args.requests):
+            while time.perf_counter() - start < arr[i]:
+                time.sleep(0.0001)
+            s, h, w, Kq, T = req(i)
+            tickets.append((srv.submit(s, h, w, Kq, T, n_samples=N_SAMPLES, seed=i), h * w))
+        lat, nr_tot = [], 0
+        for t, nr in tickets:
+            r = srv.wait(t, 600000)
+            lat.append(r.t_done_ms - r.t_submit_ms)
+            nr_tot += nr
+            srv.release(t)
+        el = time.perf_counter() - start
+        lat = np.array(lat)
+        points.append({"load": frac, "rate_req_s": round(rate, 2), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                       "p99_ms": round(float(np.percentile(lat, 99)), 3), "rays_per_s": round(nr_tot / el, 1),
+                       "requests": args.requests})
+    st = srv.stats()
+    srv.close()
+    nblocks = [G.num_blocks for G in grids]
+    line = _line(cap, "rays/s", len(points), 1, 1e3 * mean_rays / cap,
+                 {"workload": "serving: 8 device-resident rooms, BF16 colour, 128 samples per ray, requests of "
+                              "160x120 / 320x240 / 640x480 / 1280x960 with Poisson arrivals",
+                  "scene_blocks": nblocks},
+                 dtype="f32+bf16", saturated_rays_per_s=round(cap, 1), serve_points=points,
+                 peak_server_bytes=int(st.peak_bytes_in_use), gpu_launches=int(st.launches))
+    print(json.dumps(line), flush=True)
+
+
+def run_apartment(args):
+    """20x15x3 m apartment (6 rooms, 60 furniture primitives), 1 cm voxels: a full 1280x960 render at 192
+    samples per ray, and 2^20-ray training steps (fused pass + Adam)."""
+    import torch
+    import paper_2305_13220_b300 as sdg
+    import synth
+    device = "cuda:0"
+    sc = synth.scene_apartment(0)
+    poses = synth.random_poses(sc, 300, seed=0)
+    K = synth.intrinsics(W, H)
+    G = sdg.Grid(VS, 1_600_000, beta=BETA)
+    act_ms = _activate_views(sdg, torch, G, sc, poses, K, device, BAND)
+    keys, vals = _fill(sdg, torch, G, sc, VS, BAND, device)
+    del vals
+    nb = len(keys)
+    # full-frame render, 1280x960 at 192 samples
+    Kr = synth.intrinsics(1280, 960)
+    frame = synth.view_rays(poses[0], 1280, 960, Kr, device=device)
+    for _ in range(2):
+        sdg.render(G, frame, 192, seed=0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(5):
+        sdg.render(G, frame, 192, seed=i)
+    e1.record()
+    torch.cuda.synchronize()
+    render_ms = e0.elapsed_time(e1) / 5
+    batches = [synth.training_batch(sc, poses, W, H, K, 1 << 20, seed=b, device=device, order=args.order)
+               for b in range(2)]
+
+    def step(b, i):
+        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i)
+        G.adam_step(lr=1e-3)
+
+    ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
+    n = 1 << 20
+    line = _line(n / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
+                 {"workload": "apartment 20x15x3 m, 6 rooms, 60 furniture primitives, 1 cm voxels, 4-voxel band "
+                              "from 300 depth maps; 2^20-ray training steps at 128 samples + 1280x960 render at 192",
+                  "n_blocks": nb, "voxels": nb * 512, "rays_per_step": n},
+                 render_1280x960_n192={"ms": round(render_ms, 3), "rays_per_s": round(1280 * 960 / (render_ms / 1e3), 1),
+                                       "samples_per_s": round(1280 * 960 * 192 / (render_ms / 1e3), 1)},
+                 activation_ms_300_maps=round(act_ms, 2), gpu_launches=3 * args.steps)
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -449,6 +711,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "room_bf16_sem":
+        run_precision(args)
+    elif args.config == "serve":
+        run_serve(args)
+    elif args.config == "apartment":
+        run_apartment(args)
     else:
         run_ours(args)
 

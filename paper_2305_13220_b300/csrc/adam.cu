@@ -9,6 +9,10 @@
 
 using namespace sdg;
 
+// Streaming (evict-first) cache hints on the once-read, once-written optimiser streams.
+#define SDG_LD(p) __ldcs(p)
+#define SDG_ST(p, v) __stcs(p, v)
+
 namespace {
 
 struct OptParams {
@@ -37,15 +41,15 @@ __global__ void __launch_bounds__(256) k_opt_f32(float4* __restrict__ th, float4
                                                  OptParams p) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        float4 t = __ldcs(th + i), g = __ldcs(gr + i), mm = __ldcs(m + i), vv = __ldcs(v + i);
+        float4 t = SDG_LD(th + i), g = SDG_LD(gr + i), mm = SDG_LD(m + i), vv = SDG_LD(v + i);
         t.x = update<ALGO>(t.x, g.x, mm.x, vv.x, p);
         t.y = update<ALGO>(t.y, g.y, mm.y, vv.y, p);
         t.z = update<ALGO>(t.z, g.z, mm.z, vv.z, p);
         t.w = update<ALGO>(t.w, g.w, mm.w, vv.w, p);
-        __stcs(th + i, t);
-        __stcs(gr + i, z);
-        if (ALGO == SDG_OPT_ADAM) __stcs(m + i, mm);
-        __stcs(v + i, vv);
+        SDG_ST(th + i, t);
+        SDG_ST(gr + i, z);
+        if (ALGO == SDG_OPT_ADAM) SDG_ST(m + i, mm);
+        SDG_ST(v + i, vv);
     }
 }
 
@@ -64,8 +68,8 @@ __global__ void __launch_bounds__(256) k_opt_bf16(uint2* __restrict__ th, float4
                                                   int nlanes, OptParams p) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        uint2 t = __ldcs(th + i);
-        float4 g = __ldcs(gr + i), mm = __ldcs(m + i), vv = __ldcs(v + i);
+        uint2 t = SDG_LD(th + i);
+        float4 g = SDG_LD(gr + i), mm = SDG_LD(m + i), vv = SDG_LD(v + i);
         float a0 = bf_lo(t.x), a1 = bf_hi(t.x), a2 = bf_lo(t.y), a3 = bf_hi(t.y);
         a0 = update<ALGO>(a0, g.x, mm.x, vv.x, p);
         a1 = update<ALGO>(a1, g.y, mm.y, vv.y, p);
@@ -73,10 +77,10 @@ __global__ void __launch_bounds__(256) k_opt_bf16(uint2* __restrict__ th, float4
         if (nlanes == 4) a3 = update<ALGO>(a3, g.w, mm.w, vv.w, p);
         t.x = pack_bf2(a0, a1);
         t.y = pack_bf2(a2, a3);
-        __stcs(th + i, t);
-        __stcs(gr + i, z);
-        if (ALGO == SDG_OPT_ADAM) __stcs(m + i, mm);
-        __stcs(v + i, vv);
+        SDG_ST(th + i, t);
+        SDG_ST(gr + i, z);
+        if (ALGO == SDG_OPT_ADAM) SDG_ST(m + i, mm);
+        SDG_ST(v + i, vv);
     }
 }
 

@@ -669,38 +669,36 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     }
 
     // ---------------- scatter to voxels (runs of same-cell samples) ----------------
+    // Per run and corner e only aS_e = sum_i r_e(f_i) dd_i and aW_e = sum_i r_e(f_i) w_i are accumulated:
+    // the colour (and logit) gradients of a corner are the ray's seeds times aW_e.
     {
         int addr[8];
-        float aS[8], aR[8], aG[8], aB[8], aW[8];
+        float aS[8], aW[8];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const bool v = (vmask >> i) & 1u;
             if (run_start(i)) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) aS[e] = aR[e] = aG[e] = aB[e] = aW[e] = 0.f;
+                for (int e = 0; e < 8; ++e) aS[e] = aW[e] = 0.f;
                 corner_addresses(g, blk_[i], lc_[i], addr);
             }
             if (v) {
                 float r[8];
                 trilinear_weights(fx_[i], fy_[i], fz_[i], r);
-                const float wr = w_[i] * gC0, wg = w_[i] * gC1, wb = w_[i] * gC2;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     aS[e] = fmaf(r[e], dd_[i], aS[e]);
-                    aR[e] = fmaf(r[e], wr, aR[e]);
-                    aG[e] = fmaf(r[e], wg, aG[e]);
-                    aB[e] = fmaf(r[e], wb, aB[e]);
-                    if constexpr (SEM) aW[e] = fmaf(r[e], w_[i], aW[e]);
+                    aW[e] = fmaf(r[e], w_[i], aW[e]);
                 }
             }
             if (run_end(i)) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     if constexpr (!BF16) {
-                        red_add_v4(g.ggeo + addr[e], aS[e], aR[e], aG[e], aB[e]);
+                        red_add_v4(g.ggeo + addr[e], aS[e], gC0 * aW[e], gC1 * aW[e], gC2 * aW[e]);
                     } else {
                         atomicAdd(g.gsdf + addr[e], aS[e]);
-                        red_add_v4(g.grgb + addr[e], aR[e], aG[e], aB[e], 0.f);
+                        red_add_v4(g.grgb + addr[e], gC0 * aW[e], gC1 * aW[e], gC2 * aW[e], 0.f);
                     }
                     if (SEM && sem_grad) {
 #pragma unroll

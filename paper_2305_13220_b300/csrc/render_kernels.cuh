@@ -4,14 +4,22 @@
 
 #include "render_core.cuh"
 
-#ifndef SDG_RENDER_MIN_BLOCKS
-#define SDG_RENDER_MIN_BLOCKS 1
-#endif
-
 namespace sdg {
 
+// Resident 256-thread blocks per SM requested from the register allocator: three (80 registers) where the
+// program fits with no or a few bytes of spill (measured on the room training step: 1.69 -> 1.49 ms), fewer
+// for the larger per-lane sample counts and the semantic variants, which need more registers.
+template <int MODE, bool SEM, int Q>
+constexpr int render_min_blocks() {
+#ifdef SDG_RENDER_MIN_BLOCKS
+    return SDG_RENDER_MIN_BLOCKS;
+#else
+    return SEM ? (Q >= 6 ? 1 : 2) : (Q >= 6 ? 2 : 3);
+#endif
+}
+
 template <int MODE, bool BF16, bool SEM, int Q>
-__global__ void __launch_bounds__(256, SDG_RENDER_MIN_BLOCKS) k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0,
+__global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>())) k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0,
                                                 PassArgs a) {
     __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
