@@ -259,23 +259,12 @@ def serve_leg(sdg, torch, wl, n_requests=200, seed=0):
     mean_rays = np.mean([w * h for w, h in res])
     rate = 0.8 * cap_rays_s / mean_rays
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
-    tickets = []
+    sizes = [res[int(rng.integers(0, 4))] for _ in range(n_requests)]
     start = time.perf_counter()
-    for i in range(n_requests):
-        while time.perf_counter() - start < arrivals[i]:
-            time.sleep(0.0002)
-        w, h = res[int(rng.integers(0, 4))]
-        tickets.append((srv.submit(sid, h, w, synth.intrinsics(w, h), poses[i % 16], n_samples=N_SAMPLES, seed=i),
-                        w * h))
-    lat, rays = [], 0
-    for t, n in tickets:
-        r = srv.wait(t, 300000)
-        lat.append(r.t_done_ms - r.t_submit_ms)
-        rays += n
-        srv.release(t)
+    lat, rays = _open_loop(srv, n_requests, arrivals,
+                           lambda i: (sid, sizes[i][1], sizes[i][0], synth.intrinsics(*sizes[i]), poses[i % 16]), start)
     elapsed = time.perf_counter() - start
     srv.close()
-    lat = np.array(lat)
     return {"requests": n_requests, "rate_req_s": round(rate, 2), "p50_ms": round(float(np.percentile(lat, 50)), 3),
             "p99_ms": round(float(np.percentile(lat, 99)), 3), "rays_per_s": round(rays / elapsed, 1),
             "resolutions": "uniform over 160x120, 320x240, 640x480, 1280x960", "samples_per_ray": N_SAMPLES,
@@ -335,24 +324,43 @@ def run_ours(args):
     ms_step = total_ms / K
     value = aggregate_rays_per_s(world, n, ms_step)
 
-    # end to end through the public API: pinned host inputs copied in, loss read back, every step
+    # end to end through the public API: every step's rays and targets are copied from pinned host memory and its
+    # loss is read back, inside the timed region.  Two device input buffers: while step k computes on the
+    # grid's stream, step k+1's inputs upload on a copy stream (events order the two).
     hb = [{k: v.cpu().pin_memory() for k, v in b.items() if k in ("rays", "rgb", "depth")} for b in wl["batches"]]
-    dev_in = {k: torch.empty_like(v) for k, v in wl["batches"][0].items() if k in ("rays", "rgb", "depth")}
+    dev_in = [{k: torch.empty_like(v) for k, v in wl["batches"][0].items() if k in ("rays", "rgb", "depth")}
+              for _ in range(2)]
     host_loss = torch.empty(1, pin_memory=True)
     h2d = sum(v.numel() * v.element_size() for v in hb[0].values())
-    for i in range(2):
-        for k in dev_in:
-            dev_in[k].copy_(hb[i % len(hb)][k], non_blocking=True)
-        step(dev_in)
-        host_loss.copy_(loss_sum, non_blocking=True)
+    copy_stream = torch.cuda.Stream()
+    uploaded = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+
+    def upload(i, slot):
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(consumed[slot])
+            for k in dev_in[slot]:
+                dev_in[slot][k].copy_(hb[i % len(hb)][k], non_blocking=True)
+            uploaded[slot].record(copy_stream)
+
+    def e2e_steps(count):
+        for s_ in range(2):
+            consumed[s_].record(stream)
+        upload(0, 0)
+        for i in range(count):
+            slot = i % 2
+            if i + 1 < count:
+                upload(i + 1, 1 - slot)
+            stream.wait_event(uploaded[slot])
+            step(dev_in[slot])
+            consumed[slot].record(stream)
+            host_loss.copy_(loss_sum, non_blocking=True)
+
+    e2e_steps(2)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i in range(K):
-        for k in dev_in:
-            dev_in[k].copy_(hb[i % len(hb)][k], non_blocking=True)
-        step(dev_in)
-        host_loss.copy_(loss_sum, non_blocking=True)
+    e2e_steps(K)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = reduce_max(e0.elapsed_time(e1) / K, device)
@@ -477,6 +485,36 @@ def _line(value, unit, K, W_, ms, config, **extra):
     return d
 
 
+def _open_loop(srv, n_requests, arrivals, make_req, start, n_samples=N_SAMPLES):
+    """Submits request i at time arrivals[i] (open loop) while a consumer thread waits for results in order and
+    releases them, as a client that reads its frames would.  Returns (latencies ms, rays rendered)."""
+    import queue
+    q = queue.Queue()
+    lat, tot = [], [0]
+
+    def consume():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            t, nr = item
+            r = srv.wait(t, 600000)
+            lat.append(r.t_done_ms - r.t_submit_ms)
+            tot[0] += nr
+            srv.release(t)
+
+    th = threading.Thread(target=consume, daemon=True)
+    th.start()
+    for i in range(n_requests):
+        while time.perf_counter() - start < arrivals[i]:
+            time.sleep(0.0001)
+        s, h, w, Kq, T = make_req(i)
+        q.put((srv.submit(s, h, w, Kq, T, n_samples=n_samples, seed=i), h * w))
+    q.put(None)
+    th.join()
+    return np.array(lat), tot[0]
+
+
 def run_precision(args):
     """Room-scale step with BF16 colour and 20 BF16 semantic logits; per-output errors vs the FP64 oracle."""
     import torch
@@ -493,13 +531,9 @@ def run_precision(args):
     batches = [synth.training_batch(sc, poses, W, H, K, args.rays, seed=b, device=device, n_sem=20,
                                     order=args.order) for b in range(4)]
 
-    def step(b, i):
-        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i)
-        G.adam_step(lr=1e-3)
-
-    ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
-    # error table on 4096 rays spread over the views: GPU (BF16 storage) vs the FP64 oracle on the unrounded
-    # generator values, and vs the oracle on the stored (rounded) values (the parity check)
+    # error table (before any training step changes the grid) on 4096 rays spread over the views: GPU (BF16
+    # storage) vs the FP64 oracle on the unrounded generator values, and vs the oracle on the stored (rounded)
+    # values (the parity check)
     A = sdg._abi
     nb = len(keys)
     G.zero_grad()
@@ -534,6 +568,12 @@ def run_precision(args):
         row["degenerate_rays"] = int((~nd).sum())
         table[name] = row
         del O
+
+    def step(b, i):
+        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i)
+        G.adam_step(lr=1e-3)
+
+    ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
     line = _line(args.rays / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
                  {"workload": "precision variant of the room step: BF16 colour + 20 BF16 semantic logits, FP32 "
                               "SDF / transmittance / accumulation", "rays_per_step": args.rays,
@@ -590,21 +630,9 @@ def run_serve(args):
     for frac in (0.5, 0.8, 1.0):
         rate = frac * cap / mean_rays
         arr = np.cumsum(rng.exponential(1.0 / rate, size=args.requests))
-        tickets = []
         start = time.perf_counter()
-        for i in range(args.requests):
-            while time.perf_counter() - start < arr[i]:
-                time.sleep(0.0001)
-            s, h, w, Kq, T = req(i)
-            tickets.append((srv.submit(s, h, w, Kq, T, n_samples=N_SAMPLES, seed=i), h * w))
-        lat, nr_tot = [], 0
-        for t, nr in tickets:
-            r = srv.wait(t, 600000)
-            lat.append(r.t_done_ms - r.t_submit_ms)
-            nr_tot += nr
-            srv.release(t)
+        lat, nr_tot = _open_loop(srv, args.requests, arr, lambda i: req(i), start)
         el = time.perf_counter() - start
-        lat = np.array(lat)
         points.append({"load": frac, "rate_req_s": round(rate, 2), "p50_ms": round(float(np.percentile(lat, 50)), 3),
                        "p99_ms": round(float(np.percentile(lat, 99)), 3), "rays_per_s": round(nr_tot / el, 1),
                        "requests": args.requests})

@@ -369,6 +369,12 @@ int sdg_server_get_stats(sdg_server s, sdg_server_stats* st);
 /* Waits for in-flight work, stops the scheduler, frees everything. */
 int sdg_server_destroy(sdg_server s);
 
+/* Test support (no counterpart in the paper): from now on, the n-th device
+ * allocation made by grid creation, activation or loading fails as if the
+ * device were out of memory (n = 0: the next one; n < 0: switch off).  Used
+ * to check that every such failure returns SDG_ERR_OOM and leaks nothing. */
+int sdg_debug_fail_alloc_after(int64_t n);
+
 /* Thread-local message of the calling thread's last error ("" if none). */
 const char* sdg_last_error(void);
 

@@ -102,6 +102,7 @@ SIGNATURES = {
     "sdg_server_release": [_p, C.c_uint64],
     "sdg_server_get_stats": [_p, _P(ServerStats)],
     "sdg_server_destroy": [_p],
+    "sdg_debug_fail_alloc_after": [_i64],
 }
 
 _lib = None

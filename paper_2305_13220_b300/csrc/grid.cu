@@ -1,6 +1,7 @@
 // Grid life cycle, block activation (Sec. 3.4.1, Eq. 7-8), hash lookups, the
 // neighbour table and occupancy bitmap derived from the hash map, and
 // checkpointing.  Paper: arXiv 2305.13220.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -26,7 +27,27 @@ int use_device(sdg_grid g) {
     return SDG_OK;
 }
 
+// Host-side fault injection for tests: the n-th device allocation made by grid creation or activation from
+// now on fails with cudaErrorMemoryAllocation (n < 0: off).
+static std::atomic<long long> g_fail_alloc_countdown{-1};
+
+cudaError_t device_malloc(void** p, size_t bytes) {
+    long long c = g_fail_alloc_countdown.load();
+    if (c >= 0) {
+        if (g_fail_alloc_countdown.fetch_sub(1) == 0) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 }  // namespace sdg
+
+extern "C" int sdg_debug_fail_alloc_after(int64_t n) {
+    sdg::g_fail_alloc_countdown.store(n < 0 ? -1 : n);
+    return SDG_OK;
+}
 
 using namespace sdg;
 
@@ -301,7 +322,7 @@ int dalloc(T** p, size_t count, cudaStream_t s) {
         *p = nullptr;
         return SDG_OK;
     }
-    SDG_CUDA_TRY(cudaMalloc((void**)p, count * sizeof(T)));
+    SDG_CUDA_TRY(device_malloc((void**)p, count * sizeof(T)));
     SDG_CUDA_TRY(cudaMemsetAsync(*p, 0, count * sizeof(T), s));
     return SDG_OK;
 }
@@ -334,6 +355,17 @@ int sort_keys(sdg_grid g, int64_t n) {
     return SDG_OK;
 }
 
+// Makes the occupancy bitmap hold at least `words` words (the old contents are not kept).
+int reserve_bitmap(sdg_grid g, int64_t words) {
+    if (words <= g->bitmap_words_cap) return SDG_OK;
+    uint32_t* nb = nullptr;
+    SDG_CUDA_TRY(device_malloc((void**)&nb, words * sizeof(uint32_t)));
+    if (g->bitmap) cudaFree(g->bitmap);
+    g->bitmap = nb;
+    g->bitmap_words_cap = words;
+    return SDG_OK;
+}
+
 // Recomputes the AABB (from all keys), the occupancy bitmap and the neighbour table.
 int rebuild_derived(sdg_grid g) {
     const int64_t N = g->n_blocks;
@@ -357,13 +389,8 @@ int rebuild_derived(sdg_grid g) {
         bits *= g->bdim[a];
     }
     int64_t words = (bits + 31) / 32;
-    if (words > g->bitmap_words_cap) {
-        if (g->bitmap) cudaFree(g->bitmap);
-        g->bitmap = nullptr;
-        g->bitmap_words_cap = 0;
-        SDG_CUDA_TRY(cudaMalloc((void**)&g->bitmap, words * sizeof(uint32_t)));
-        g->bitmap_words_cap = words;
-    }
+    int rc = reserve_bitmap(g, words);
+    if (rc) return rc;
     g->bitmap_words = words;
     SDG_CUDA_TRY(cudaMemsetAsync(g->bitmap, 0, words * sizeof(uint32_t), g->stream));
     k_bitmap<<<grid_blocks(N), kThreads, 0, g->stream>>>(g->keys, N, g->bmin[0], g->bmin[1], g->bmin[2], g->bdim[0],
@@ -423,6 +450,9 @@ int finish_activation(sdg_grid g, int64_t* n_new) {
     for (int a = 0; a < 3; ++a) bits *= (int64_t)g->h_minmax[3 + a] - g->h_minmax[a] + 1;
     if (bits > kMaxBitmapBits)
         return fail(SDG_ERR_CAPACITY, "activation: block bounding box exceeds 2^34 blocks; grid unchanged");
+    // every allocation happens before the first insertion, so a failure leaves the grid unchanged
+    rc = reserve_bitmap(g, (bits + 31) / 32);
+    if (rc) return rc;
     k_insert<<<grid_blocks(cnt), kThreads, 0, g->stream>>>(g->sort_buf, (int64_t)cnt, g->n_blocks, g->table, g->mask,
                                                             g->keys, g->counters);
     SDG_LAUNCH_CHECK("insert");
@@ -465,8 +495,8 @@ extern "C" int sdg_grid_create(const sdg_grid_desc* d, sdg_grid* out) {
         SDG_CUDA_TRY(cudaSetDevice(g->device));
         cudaStream_t s = g->stream;
         const size_t V = (size_t)g->max_blocks * 512;
-        SDG_CUDA_TRY(cudaMalloc((void**)&g->table, (size_t)g->cap * sizeof(ulonglong2)));
-        SDG_CUDA_TRY(cudaMalloc((void**)&g->tmp_table, (size_t)g->cap * sizeof(ulonglong2)));
+        SDG_CUDA_TRY(device_malloc((void**)&g->table, (size_t)g->cap * sizeof(ulonglong2)));
+        SDG_CUDA_TRY(device_malloc((void**)&g->tmp_table, (size_t)g->cap * sizeof(ulonglong2)));
         SDG_CUDA_TRY(cudaMemsetAsync(g->table, 0xFF, (size_t)g->cap * sizeof(ulonglong2), s));
         SDG_CUDA_TRY(cudaMemsetAsync(g->tmp_table, 0xFF, (size_t)g->cap * sizeof(ulonglong2), s));
         int r;
