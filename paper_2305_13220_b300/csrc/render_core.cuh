@@ -79,17 +79,17 @@ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
     uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
     return (word >> 22u) ^ word;
 }
-__device__ __forceinline__ float sample_u(uint32_t seed_h, uint32_t ray_id, int k) {
-    uint32_t h = pcg_hash((uint32_t)k + pcg_hash(ray_id + seed_h));
-    return (float)(h >> 8) * 5.9604644775390625e-8f;
+// ray_h = pcg_hash(ray_id + pcg_hash(seed)) is per ray; u_k = pcg_hash(k + ray_h) >> 8, times 2^-24.
+__device__ __forceinline__ float sample_u(uint32_t ray_h, int k) {
+    return (float)(pcg_hash((uint32_t)k + ray_h) >> 8) * 5.9604644775390625e-8f;
 }
 
 struct SampleGen {
     float s_over_n, s_max;
-    uint32_t seed_h, ray_id;
+    uint32_t ray_h;
     int strat;
     __device__ __forceinline__ float s(int k) const {
-        float u = strat ? sample_u(seed_h, ray_id, k) : 0.5f;
+        float u = strat ? sample_u(ray_h, k) : 0.5f;
         return fminf(((float)k + u) * s_over_n, s_max);
     }
 };
@@ -256,28 +256,34 @@ __device__ __forceinline__ float locate(const GridDev& g, const RayJob& j, const
 // ---------------------------------------------------------------------------
 // Voxel stencil of a cell (Eq. 17): the 8 grid points around x
 // ---------------------------------------------------------------------------
-// Cell packed as lx | ly << 3 | lz << 6 (local coordinates of its base corner).
-__device__ __forceinline__ int corner_nb(int m, int4 n0, int4 n1) {
-    // neighbour block for overflow mask m (bit 0 = +x, bit 1 = +y, bit 2 = +z)
-    const int lo = (m & 1) ? ((m & 2) ? n0.w : n0.y) : ((m & 2) ? n0.z : n0.x);
-    const int hi = (m & 1) ? ((m & 2) ? n1.w : n1.y) : ((m & 2) ? n1.z : n1.x);
-    return (m & 4) ? hi : lo;
-}
-
-// Addresses of the 8 corners of cell `lcell` of block `blk`; false if a corner's block is absent.
+// Cell packed as lx | ly << 3 | lz << 6 (local coordinates of its base corner).  Its 8 corners are the
+// voxels (lx + ex, ly + ey, lz + ez), e = ex | ey << 1 | ez << 2; a corner whose coordinate wraps past 7 on an
+// axis lives in the neighbour block on that side, read from the block's neighbour row
+// {self, +x, +y, +xy | +z, +xz, +yz, +xyz}.  Writes their voxel addresses; false if a corner's block is absent.
 __device__ __forceinline__ bool corner_addresses(const GridDev& g, int blk, int lcell, int addr[8]) {
     const int lx = lcell & 7, ly = (lcell >> 3) & 7, lz = lcell >> 6;
-    const int ovf = (lx == 7) | ((ly == 7) << 1) | ((lz == 7) << 2);
+    const bool ox = lx == 7, oy = ly == 7, oz = lz == 7;
     const int4 n0 = __ldg(g.nbr + 2 * blk), n1 = __ldg(g.nbr + 2 * blk + 1);
-    bool ok = true;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
-        const int be = corner_nb(e & ovf, n0, n1);
-        ok = ok && be >= 0;
-        addr[e] = be * 512 + (((lz + ez) & 7) << 6) + (((ly + ey) & 7) << 3) + ((lx + ex) & 7);
-    }
-    return ok;
+    const int b1 = ox ? n0.y : blk;
+    const int b2 = oy ? n0.z : blk;
+    const int b3 = ox ? (oy ? n0.w : n0.y) : b2;
+    const int b4 = oz ? n1.x : blk;
+    const int b5 = ox ? (oz ? n1.y : n0.y) : b4;
+    const int b6 = oy ? (oz ? n1.z : n0.z) : b4;
+    const int b7 = ox ? (oy ? (oz ? n1.w : n0.w) : (oz ? n1.y : n0.y)) : b6;
+    const int x0 = lx, x1 = (lx + 1) & 7;
+    const int y0 = ly << 3, y1 = ((ly + 1) & 7) << 3;
+    const int z0 = lz << 6, z1 = ((lz + 1) & 7) << 6;
+    const int q00 = x0 + y0, q10 = x1 + y0, q01 = x0 + y1, q11 = x1 + y1;
+    addr[0] = blk * 512 + q00 + z0;
+    addr[1] = b1 * 512 + q10 + z0;
+    addr[2] = b2 * 512 + q01 + z0;
+    addr[3] = b3 * 512 + q11 + z0;
+    addr[4] = b4 * 512 + q00 + z1;
+    addr[5] = b5 * 512 + q10 + z1;
+    addr[6] = b6 * 512 + q01 + z1;
+    addr[7] = b7 * 512 + q11 + z1;
+    return (b1 | b2 | b3 | b4 | b5 | b6 | b7) >= 0;
 }
 
 template <bool BF16>
@@ -356,8 +362,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     const int64_t RS = 32 * Q;  // record stride per ray
 
     SampleGen gen;
-    gen.seed_h = pcg_hash(a.seed);
-    gen.ray_id = j.ray_id;
+    gen.ray_h = pcg_hash(j.ray_id + pcg_hash(a.seed));
     gen.strat = a.strat;
     Pieces pc;
     float t1 = 0.f;
