@@ -442,6 +442,20 @@ def _timed_steps(torch, step, batches, K, W_):
     return s0.elapsed_time(s1) / K
 
 
+def _phase_times(torch, sdg, G, batches, K, train):
+    """Mean CUDA-event times of the fused training pass and of the optimiser step."""
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for i in range(K):
+        ev[i][0].record()
+        train(batches[i % len(batches)], 2000 + i)
+        ev[i][1].record()
+        G.adam_step(lr=1e-3)
+        ev[i][2].record()
+    torch.cuda.synchronize()
+    return {"train_kernel_ms": round(float(np.mean([e[0].elapsed_time(e[1]) for e in ev])), 4),
+            "adam_ms": round(float(np.mean([e[1].elapsed_time(e[2]) for e in ev])), 4)}
+
+
 def _activate_views(sdg, torch, G, sc, poses, K, device, band):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -574,11 +588,13 @@ def run_precision(args):
         G.adam_step(lr=1e-3)
 
     ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
+    phases = _phase_times(torch, sdg, G, batches, args.steps, lambda b, i: sdg.train_step_rays(
+        G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i))
     line = _line(args.rays / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
                  {"workload": "precision variant of the room step: BF16 colour + 20 BF16 semantic logits, FP32 "
                               "SDF / transmittance / accumulation", "rays_per_step": args.rays,
                   "samples_per_ray": N_SAMPLES, "n_blocks": nb},
-                 dtype="f32+bf16", samples_per_s=round(args.rays * N_SAMPLES / (ms / 1e3), 1),
+                 dtype="f32+bf16", samples_per_s=round(args.rays * N_SAMPLES / (ms / 1e3), 1), phases=phases,
                  errors_on_4096_rays=table, gpu_launches=5 * args.steps)
     print(json.dumps(line), flush=True)
 
@@ -684,6 +700,8 @@ def run_apartment(args):
         G.adam_step(lr=1e-3)
 
     ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
+    phases = _phase_times(torch, sdg, G, batches, args.steps, lambda b, i: sdg.train_step_rays(
+        G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i))
     n = 1 << 20
     line = _line(n / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
                  {"workload": "apartment 20x15x3 m, 6 rooms, 60 furniture primitives, 1 cm voxels, 4-voxel band "
@@ -691,7 +709,7 @@ def run_apartment(args):
                   "n_blocks": nb, "voxels": nb * 512, "rays_per_step": n},
                  render_1280x960_n192={"ms": round(render_ms, 3), "rays_per_s": round(1280 * 960 / (render_ms / 1e3), 1),
                                        "samples_per_s": round(1280 * 960 * 192 / (render_ms / 1e3), 1)},
-                 activation_ms_300_maps=round(act_ms, 2), gpu_launches=3 * args.steps)
+                 activation_ms_300_maps=round(act_ms, 2), phases=phases, gpu_launches=3 * args.steps)
     print(json.dumps(line), flush=True)
 
 

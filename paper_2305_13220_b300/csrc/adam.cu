@@ -17,20 +17,23 @@ namespace {
 
 struct OptParams {
     float lr, b1, b2, eps;
-    float omb1, omb2;  // 1 - b1, 1 - b2 (rounded from double)
-    float c1, c2;      // Adam bias corrections 1 - b^step
+    float omb1, omb2;   // 1 - b1, 1 - b2 (rounded from double)
+    float step_size;    // lr / (1 - b1^step)
+    float inv_sqrt_c2;  // 1 / sqrt(1 - b2^step)
 };
 
+// theta -= lr (m / c1) / (sqrt(v / c2) + eps), written as step_size * m / (sqrt(v) / sqrt(c2) + eps) with the
+// bias corrections folded on the host: one square root and one division per parameter.
 template <int ALGO>
 __device__ __forceinline__ float update(float th, float g, float& m, float& v, const OptParams& p) {
     if (ALGO == SDG_OPT_ADAM) {
         m = fmaf(p.b1, m, p.omb1 * g);
         v = fmaf(p.b2, v, p.omb2 * g * g);
-        const float mh = m / p.c1, vh = v / p.c2;
-        return th - p.lr * mh / (sqrtf(vh) + p.eps);
+        const float denom = fmaf(sqrtf(v), p.inv_sqrt_c2, p.eps);
+        return th - __fdividef(p.step_size * m, denom);
     } else {  // RMSProp, alpha = b2
         v = fmaf(p.b2, v, p.omb2 * g * g);
-        return th - p.lr * g / (sqrtf(v) + p.eps);
+        return th - __fdividef(p.lr * g, sqrtf(v) + p.eps);
     }
 }
 
@@ -128,7 +131,7 @@ extern "C" int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a) {
     p.eps = (float)a->eps;
     p.omb1 = (float)(1.0 - a->beta1);
     p.omb2 = (float)(1.0 - a->beta2);
-    p.c1 = (float)(1.0 - std::pow(a->beta1, step));
-    p.c2 = (float)(1.0 - std::pow(a->beta2, step));
+    p.step_size = (float)(a->lr / (1.0 - std::pow(a->beta1, step)));
+    p.inv_sqrt_c2 = (float)(1.0 / std::sqrt(1.0 - std::pow(a->beta2, step)));
     return a->algo == SDG_OPT_ADAM ? run<SDG_OPT_ADAM>(g, p) : run<SDG_OPT_RMSPROP>(g, p);
 }
