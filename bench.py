@@ -49,7 +49,15 @@ def parse():
     p.add_argument("--requests", type=int, default=2000, help="serve: requests per arrival rate")
     p.add_argument("--order", default="pixel", choices=["pixel", "drawn"],
                    help="ray order inside a batch: grouped by view and pixel (a per-image loader) or as drawn")
+    p.add_argument("--ray-order", default="auto", choices=["auto", "given", "surface"],
+                   help="processing order of the fused pass (train_step_rays ray_order): auto puts batches of "
+                        ">= 65536 rays in surface order on the GPU inside the step")
     return p.parse_args()
+
+
+def _order_launches(args, n: int) -> int:
+    """Kernels the surface ordering adds to a training step (bucket keys, bucket scan, scatter)."""
+    return 3 if args.ray_order == "surface" or (args.ray_order == "auto" and n >= 65536) else 0
 
 
 def reduce_max(x: float, device=None) -> float:
@@ -287,7 +295,7 @@ def run_ours(args):
 
     def step(b):
         sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
-                            lambda_depth=LAMBDA_D, loss_sum=loss_sum)
+                            lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
         G.adam_step(lr=1e-3)
 
     stepno = [0]
@@ -311,7 +319,7 @@ def run_ours(args):
         stepno[0] = 1000 + i
         evs[i][0].record(stream)
         sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
-                            lambda_depth=LAMBDA_D, loss_sum=loss_sum)
+                            lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
         evs[i][1].record(stream)
         G.adam_step(lr=1e-3)
         evs[i][2].record(stream)
@@ -377,6 +385,8 @@ def run_ours(args):
                                        "voxels, 8^3 blocks, 4-voxel band from 50 640x480 depth maps; 2^18 rays "
                                        "x 128 stratified samples, L1 colour + 0.1 L1 depth, Adam on every voxel)",
                            "rays_per_step": n, "samples_per_ray": N_SAMPLES, "n_blocks": nb,
+                           "ray_order": args.ray_order + (" (surface order, sorted on the GPU inside the step)"
+                                                          if _order_launches(args, n) else ""),
                            "voxels": nb * 512, "params": params,
                            "parallelism": f"replicas{world}" if world > 1 else "single",
                            "l2": "inputs larger than L2: each step streams the whole grid and Adam state "
@@ -384,7 +394,7 @@ def run_ours(args):
                 "samples_per_s": round(value * N_SAMPLES, 1),
                 "phases": {"train_kernel_ms": round(train_ms, 4), "adam_ms": round(adam_ms, 4),
                            "activation_ms_50_maps": round(wl["act_ms"], 3)},
-                "clocks": clk, "gpu_launches": 3 * K,
+                "clocks": clk, "gpu_launches": (3 + _order_launches(args, n)) * K,
                 "e2e": {"value": round(aggregate_rays_per_s(world, n, e2e_ms), 1), "unit": "rays/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}}
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
@@ -584,18 +594,19 @@ def run_precision(args):
         del O
 
     def step(b, i):
-        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i)
+        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i,
+                            ray_order=args.ray_order)
         G.adam_step(lr=1e-3)
 
     ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
     phases = _phase_times(torch, sdg, G, batches, args.steps, lambda b, i: sdg.train_step_rays(
-        G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i))
+        G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i, ray_order=args.ray_order))
     line = _line(args.rays / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
                  {"workload": "precision variant of the room step: BF16 colour + 20 BF16 semantic logits, FP32 "
                               "SDF / transmittance / accumulation", "rays_per_step": args.rays,
                   "samples_per_ray": N_SAMPLES, "n_blocks": nb},
                  dtype="f32+bf16", samples_per_s=round(args.rays * N_SAMPLES / (ms / 1e3), 1), phases=phases,
-                 errors_on_4096_rays=table, gpu_launches=5 * args.steps)
+                 errors_on_4096_rays=table, gpu_launches=(5 + _order_launches(args, args.rays)) * args.steps)
     print(json.dumps(line), flush=True)
 
 
@@ -696,20 +707,23 @@ def run_apartment(args):
                for b in range(2)]
 
     def step(b, i):
-        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i)
+        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i,
+                            ray_order=args.ray_order)
         G.adam_step(lr=1e-3)
 
     ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
     phases = _phase_times(torch, sdg, G, batches, args.steps, lambda b, i: sdg.train_step_rays(
-        G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i))
+        G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i, ray_order=args.ray_order))
     n = 1 << 20
     line = _line(n / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
                  {"workload": "apartment 20x15x3 m, 6 rooms, 60 furniture primitives, 1 cm voxels, 4-voxel band "
                               "from 300 depth maps; 2^20-ray training steps at 128 samples + 1280x960 render at 192",
                   "n_blocks": nb, "voxels": nb * 512, "rays_per_step": n},
-                 render_1280x960_n192={"ms": round(render_ms, 3), "rays_per_s": round(1280 * 960 / (render_ms / 1e3), 1),
+                 render_1280x960_n192={"ms": round(render_ms, 3),
+                                       "rays_per_s": round(1280 * 960 / (render_ms / 1e3), 1),
                                        "samples_per_s": round(1280 * 960 * 192 / (render_ms / 1e3), 1)},
-                 activation_ms_300_maps=round(act_ms, 2), phases=phases, gpu_launches=3 * args.steps)
+                 activation_ms_300_maps=round(act_ms, 2), phases=phases,
+                 gpu_launches=(3 + _order_launches(args, 1 << 20)) * args.steps)
     print(json.dumps(line), flush=True)
 
 

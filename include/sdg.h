@@ -234,7 +234,26 @@ int sdg_ctx_release(sdg_ctx ctx);
 typedef struct {
     float lambda_depth; /* 0.1 */
     float lambda_sem;   /* 0.1 */
+    int32_t ray_order;  /* SDG_ORDER_*; used by sdg_train_step_rays only */
 } sdg_loss_opts;
+
+/* Order in which sdg_train_step_rays processes a batch's rays.  The result of
+ * each ray (its samples, its loss term, its gradient contributions) does not
+ * depend on the order; only the order of the floating-point gradient
+ * accumulation, which is unordered in every mode, and the speed do.
+ *   SDG_ORDER_AUTO    surface order for batches of at least 65536 rays,
+ *                     the given order below that;
+ *   SDG_ORDER_GIVEN   the rays' order in rays_dev;
+ *   SDG_ORDER_SURFACE rays grouped by the coarse cell (4x4x4 blocks, Morton
+ *                     order) that holds their target surface point
+ *                     o + t_depth d, so that rays updating the same voxels
+ *                     run together and their gradient updates meet in L2.
+ *                     Rays with a non-finite or non-positive target depth go
+ *                     last.  Needs a grid-owned scratch of 8 bytes per ray
+ *                     plus 128 KiB, grown on demand. */
+#define SDG_ORDER_AUTO 0
+#define SDG_ORDER_GIVEN 1
+#define SDG_ORDER_SURFACE 2
 
 /* Per-ray loss and gradient seeds for n rays:
  *   loss_i = sum_c |rgb - t_rgb| / (3n) + lambda_d |depth - t_depth| / n + lambda_s ||sem - t_sem||^2 / n
@@ -251,7 +270,8 @@ int sdg_loss_l1(sdg_grid g, int64_t n, const float* rgb_dev, const float* depth_
  * the gradients and writes the per-ray loss terms to loss_dev [n] (may be
  * NULL) and their sum to loss_sum_dev [1] (may be NULL; deterministic
  * reduction).  t_sem_dev may be NULL when the grid has no semantics or the
- * semantic term is not wanted.  opts->mode is ignored. */
+ * semantic term is not wanted.  opts->mode is ignored.  lo->ray_order picks
+ * the processing order (SDG_ORDER_*); an unknown value is SDG_ERR_ARG. */
 int sdg_train_step_rays(sdg_grid g, const float* rays_dev, int64_t n, const float* t_rgb_dev,
                         const float* t_depth_dev, const float* t_sem_dev, const sdg_render_opts* opts,
                         const sdg_loss_opts* lo, float* loss_dev, float* loss_sum_dev);
@@ -267,7 +287,8 @@ int sdg_train_step_rays(sdg_grid g, const float* rays_dev, int64_t n, const floa
  * the library until the process exits) and calls no allocating routine.
  * Same arguments and results as sdg_train_step_rays without loss_dev: the
  * gradients accumulate into the grid and loss_sum_dev [1] (may be NULL)
- * receives the summed loss.  n may be at most 1048576 rays; larger n returns
+ * receives the summed loss.  lo->ray_order is ignored: the rays run in the
+ * given order (surface ordering would need a further scratch).  n may be at most 1048576 rays; larger n returns
  * SDG_ERR_CAPACITY before any work is enqueued.  The first call on each
  * device looks up the array's device address (a one-time set-up); make that
  * first call before any stream capture.  Every call on a device shares the

@@ -12,6 +12,7 @@ F32, BF16 = 0, 1
 GROUP_GEO, GROUP_SDF, GROUP_RGB, GROUP_SEM, GROUP_WEIGHT = range(5)
 KIND_VALUE, KIND_GRAD, KIND_ADAM_M, KIND_ADAM_V = range(4)
 MODE_RECOMPUTE, MODE_STORE = 0, 1
+ORDER_AUTO, ORDER_GIVEN, ORDER_SURFACE = 0, 1, 2
 OPT_ADAM, OPT_RMSPROP = 0, 1
 
 ERROR_NAMES = {OK: "SDG_OK", ERR_ARG: "SDG_ERR_ARG", ERR_OOM: "SDG_ERR_OOM", ERR_CAPACITY: "SDG_ERR_CAPACITY",
@@ -35,7 +36,7 @@ class RenderOut(C.Structure):
 
 
 class LossOpts(C.Structure):
-    _fields_ = [("lambda_depth", C.c_float), ("lambda_sem", C.c_float)]
+    _fields_ = [("lambda_depth", C.c_float), ("lambda_sem", C.c_float), ("ray_order", C.c_int32)]
 
 
 class AdamOpts(C.Structure):

@@ -45,6 +45,10 @@ struct sdg_grid_s {
     int* h_minmax = nullptr;                   // pinned host [6]
     float* loss_buf = nullptr;                 // per-ray loss scratch of the fused training pass
     int64_t loss_cap = 0;
+    int* order_keys = nullptr;  // surface ordering of a training batch: per-ray bucket [order_cap]
+    int* order_perm = nullptr;  // processing order [order_cap]
+    int* order_hist = nullptr;  // bucket counts, then offsets [kOrderBuckets]
+    int64_t order_cap = 0;
 
     std::mutex mu;  // serialises host-side mutation (activation, load) of this grid
 
@@ -82,4 +86,12 @@ struct sdg_grid_s {
 namespace sdg {
 // Makes g's device current for the calling thread.
 int use_device(sdg_grid g);
+
+// Buckets of the surface ordering of a training batch (order.cu).
+constexpr int kOrderBuckets = 1 << 15;
+
+// Enqueues on g's stream the surface ordering of n training rays (SDG_ORDER_SURFACE) and sets *perm to the
+// grid-owned processing order (valid until the next call on this grid).  Sets *perm to NULL, with nothing
+// enqueued, when the grid holds no block.
+int order_rays_by_surface(sdg_grid g, const float* rays, const float* tdepth, int64_t n, const int** perm);
 }  // namespace sdg

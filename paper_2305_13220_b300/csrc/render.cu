@@ -26,6 +26,9 @@ int launch_q(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs&
 
 namespace {
 
+// Smallest batch that SDG_ORDER_AUTO puts in surface order.
+constexpr int64_t kAutoSurfaceOrderRays = 65536;
+
 int pick_q(int N) { return N <= 64 ? 2 : N <= 128 ? 4 : N <= 192 ? 6 : 8; }
 
 template <int MODE>
@@ -211,6 +214,8 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
     if (rc) return rc;
     if (n > 0 && !aligned16(rays)) return fail(SDG_ERR_ARG, "sdg_train_step_rays: rays must be 16-byte aligned");
     if (n > (int64_t)1 << 31) return fail(SDG_ERR_ARG, "sdg_train_step_rays: at most 2^31 rays per call");
+    if (lo->ray_order != SDG_ORDER_AUTO && lo->ray_order != SDG_ORDER_GIVEN && lo->ray_order != SDG_ORDER_SURFACE)
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays: unknown ray_order");
     if ((rc = use_device(g))) return rc;
     if (n == 0) {
         if (loss_sum) SDG_CUDA_TRY(cudaMemsetAsync(loss_sum, 0, sizeof(float), g->stream));
@@ -238,6 +243,9 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
     a.lam_s = lo->lambda_sem;
     a.inv_n = 1.0f / (float)n;
     a.loss = per_ray;
+    if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
+        if ((rc = order_rays_by_surface(g, rays, tdepth, n, &a.perm))) return rc;
+    }
     rc = launch_pass<PASS_TRAIN>(g, rays, o->ray_id0, a);
     if (rc) return rc;
     if (loss_sum) {

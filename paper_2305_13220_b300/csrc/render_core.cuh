@@ -50,6 +50,7 @@ struct PassArgs {
     const float *t_rgb, *t_depth, *t_sem;
     float lam_d, lam_s, inv_n;
     float* loss;
+    const int* perm;  // optional processing order: warp slot i runs ray perm[i] (NULL: ray i)
 };
 
 struct RayJob {

@@ -23,8 +23,9 @@ __global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>())) k_re
                                                 PassArgs a) {
     __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-    if (r >= a.n) return;  // warp-uniform
+    const int64_t slot = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (slot >= a.n) return;  // warp-uniform
+    const int64_t r = a.perm ? (int64_t)__ldg(a.perm + slot) : slot;
     const float4 r0 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r);
     const float4 r1 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r + 1);
     RayJob j;
