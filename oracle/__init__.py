@@ -97,6 +97,8 @@ def _declare(L):
         "orc_adam": (None, [_p, _p, _p, _p, _i64, _d, _d, _d, _d, C.c_int]),
         "orc_rmsprop": (None, [_p, _p, _p, _i64, _d, _d, _d]),
         "orc_view_rays": (None, [C.c_int, C.c_int, _p, _p, C.c_float, C.c_float, _p]),
+        "orc_fuse": (None, [_p, _i64, C.c_float, C.c_int, C.c_int, C.c_int, _p, _p, _p, C.c_int, _p, _p, C.c_float,
+                            _p, _p, _p, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -332,3 +334,36 @@ def view_rays(H, W, K, Twc, tnear=0.05, tfar=1.0e3):
     rays = np.empty((H * W, 8), np.float32)
     lib().orc_view_rays(H, W, Kd.ctypes.data, Td.ctypes.data, C.c_float(tnear), C.c_float(tfar), rays.ctypes.data)
     return rays
+
+
+def fuse(keys, voxel_size: float, depth, K, Twc, mu: float, rgb=None, sem=None):
+    """Volumetric fusion (Eq. 9-11): frames depth [F,H,W] (z-depth), optional rgb [F,H,W,3] and logits
+    [F,H,W,ns], intrinsics K [4] or [F,4] (fx, fy, cx, cy), camera-to-world Twc [3,4] or [F,3,4].  Returns
+    float64 sdf [N,512], rgb [N,512,3], sem [N,512,ns] (normalised) and weight [N,512] (association counts)."""
+    keys, kp = _arr(keys, np.int32)
+    depth = np.asarray(_np(depth, np.float32), dtype=np.float32)
+    if depth.ndim == 2:
+        depth = depth[None]
+    F, H, W = depth.shape
+    depth, dp = _arr(depth, np.float32)
+    K = np.broadcast_to(np.asarray(_np(K, np.float32), np.float32).reshape(-1, 4), (F, 4))
+    K, Kp = _arr(K, np.float32)
+    T = np.asarray(_np(Twc, np.float32), np.float32).reshape(-1, 12)
+    T = np.broadcast_to(T, (F, 12))
+    T, Tp = _arr(T, np.float32)
+    N = keys.shape[0]
+    ns = 0
+    rp = sp = None
+    if rgb is not None:
+        rgb, rp = _arr(_np(rgb, np.float32), np.float32)
+    if sem is not None:
+        sem, sp = _arr(_np(sem, np.float32), np.float32)
+        ns = sem.shape[-1]
+    out = {"sdf": np.zeros((N, 512)), "rgb": np.zeros((N, 512, 3)), "sem": np.zeros((N, 512, max(ns, 1))),
+           "weight": np.zeros((N, 512))}
+    lib().orc_fuse(kp, N, float(voxel_size), F, H, W, dp, rp, sp, ns, Kp, Tp, float(mu),
+                   out["sdf"].ctypes.data_as(_p), out["rgb"].ctypes.data_as(_p), out["sem"].ctypes.data_as(_p),
+                   out["weight"].ctypes.data_as(_p))
+    if not ns:
+        del out["sem"]
+    return out

@@ -597,6 +597,78 @@ void orc_rmsprop(double* theta, double* grad, double* v, int64_t n, double lr, d
     }
 }
 
+// ------------------------------ fusion -------------------------------------
+// Volumetric fusion of depth, colour and semantic frames into the allocated
+// voxels (Sec. 3.4.2, Eq. 9-11; the supplement's truncation psi).  Voxel v of
+// block b sits at x = (8b + l) * vs.  Its association with frame i (camera to
+// world R_i, t_i; pinhole fx, fy, cx, cy) is decided in FP32 with this order
+// and no fused multiply-add, so that any FP32 implementation of the same
+// order takes the same integer decisions:
+//   x_a = (float)(8 b_a + l_a) * vs                       per axis a
+//   e_a = x_a - t_a;  c_j = (R_0j e_0 + R_1j e_1) + R_2j e_2   (c = R^T (x - t))
+//   kept only if c_2 > 0;  pu = fx * (c_0 / c_2) + cx,  pv = fy * (c_1 / c_2) + cy
+//   pixel (floor(pu), floor(pv)) inside the image, its depth D finite and > 0
+//   o = D - c_2 (the SDF seen from view i, positive in front of the surface)
+//   kept only if o >= -mu (farther behind the observed surface is occlusion)
+//   psi = min(o, mu)
+// The least-squares problems of Eq. 9-11 have the averages over the kept
+// associations as solutions: theta_d = mean psi, theta_c = mean pixel colour,
+// s* = mean pixel logits and theta_s = s* / |s*|.  weight = number of kept
+// associations; a voxel with none keeps zeros.  Sums run in FP64.
+void orc_fuse(const int32_t* keys, int64_t N, float vs, int F, int H, int W, const float* depth, const float* rgb,
+              const float* sem, int n_sem, const float* K, const float* T, float mu, double* sdf, double* col,
+              double* logit, double* weight) {
+    for (int64_t b = 0; b < N; ++b)
+        for (int l = 0; l < 512; ++l) {
+            const int lc[3] = {l & 7, (l >> 3) & 7, l >> 6};
+            float x[3];
+            for (int a = 0; a < 3; ++a) x[a] = (float)(8 * keys[3 * b + a] + lc[a]) * vs;
+            double n = 0.0, sd = 0.0, sc[3] = {0.0, 0.0, 0.0};
+            std::vector<double> ss(n_sem > 0 ? n_sem : 1, 0.0);
+            for (int i = 0; i < F; ++i) {
+                const float* R = T + 12 * i;
+                const float* k = K + 4 * i;
+                float e[3];
+                for (int a = 0; a < 3; ++a) e[a] = x[a] - R[a * 4 + 3];
+                float c[3];
+                for (int j = 0; j < 3; ++j) {
+                    float p0 = R[0 * 4 + j] * e[0];
+                    float p1 = R[1 * 4 + j] * e[1];
+                    float p2 = R[2 * 4 + j] * e[2];
+                    c[j] = (p0 + p1) + p2;
+                }
+                if (!(c[2] > 0.0f)) continue;
+                float pu = k[0] * (c[0] / c[2]) + k[2];
+                float pv = k[1] * (c[1] / c[2]) + k[3];
+                float fu = std::floor(pu), fv = std::floor(pv);
+                if (!(fu >= 0.0f && fu < (float)W && fv >= 0.0f && fv < (float)H)) continue;
+                const int64_t pix = (int64_t)i * H * W + (int64_t)fv * W + (int64_t)fu;
+                float D = depth[pix];
+                if (!(std::isfinite(D) && D > 0.0f)) continue;
+                float o = D - c[2];
+                if (!(o >= -mu)) continue;
+                float psi = std::min(o, mu);
+                n += 1.0;
+                sd += (double)psi;
+                if (rgb)
+                    for (int q = 0; q < 3; ++q) sc[q] += (double)rgb[3 * pix + q];
+                if (sem)
+                    for (int q = 0; q < n_sem; ++q) ss[q] += (double)sem[(int64_t)n_sem * pix + q];
+            }
+            const int64_t vi = b * 512 + l;
+            weight[vi] = n;
+            sdf[vi] = n > 0 ? sd / n : 0.0;
+            for (int q = 0; q < 3; ++q) col[3 * vi + q] = n > 0 ? sc[q] / n : 0.0;
+            if (sem && n_sem > 0) {
+                double nn = 0.0;
+                for (int q = 0; q < n_sem; ++q) nn += (ss[q] / n) * (ss[q] / n);
+                nn = std::sqrt(nn);
+                for (int q = 0; q < n_sem; ++q)
+                    logit[(int64_t)n_sem * vi + q] = (n > 0 && nn > 0.0) ? (ss[q] / n) / nn : 0.0;
+            }
+        }
+}
+
 // Pinhole rays of one H x W view (serve requests): o = t, d = normalize(R * ((u+0.5-cx)/fx, (v+0.5-cy)/fy, 1)).
 void orc_view_rays(int H, int W, const double* K, const double* T, float tnear, float tfar, float* rays) {
     for (int v = 0; v < H; ++v)

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_activation as A
+from tests import test_oracle_fusion as Fu
 from tests import test_oracle_render as R
 
 MUTANTS = [
@@ -37,6 +38,19 @@ MUTANTS = [
      [R.test_traversal_matches_dense_classification]),
     ("dilation_off_by_one", "b1[a] = floordiv(v[a] + r, 8);", "b1[a] = floordiv(v[a] + r - 1, 8);",
      [lambda: A.test_activation_matches_voxel_cube_enumeration(3)]),
+    ("fusion_sdf_sign", "float o = D - c[2];", "float o = c[2] - D;", [Fu.test_plane_sdf_is_the_truncated_distance]),
+    ("fusion_transpose", "float p1 = R[1 * 4 + j] * e[1];", "float p1 = R[j * 4 + 1] * e[1];",
+     [Fu.test_plane_sdf_is_the_truncated_distance, Fu.test_two_views_agree_and_weights_count]),
+    ("fusion_no_truncation", "float psi = std::min(o, mu);", "float psi = o;",
+     [Fu.test_plane_sdf_is_the_truncated_distance]),
+    ("fusion_keeps_occluded", "if (!(o >= -mu)) continue;", "",
+     [Fu.test_plane_sdf_is_the_truncated_distance]),
+    ("fusion_no_translation", "e[a] = x[a] - R[a * 4 + 3];", "e[a] = x[a];",
+     [Fu.test_plane_sdf_is_the_truncated_distance]),
+    ("fusion_pixel_rounding", "float fu = std::floor(pu), fv = std::floor(pv);",
+     "float fu = std::floor(pu + 0.5f), fv = std::floor(pv + 0.5f);", [Fu.test_pixel_centre_convention]),
+    ("fusion_unnormalised_logits", "? (ss[q] / n) / nn : 0.0;", "? (ss[q] / n) : 0.0;",
+     [Fu.test_colour_is_the_mean_and_logits_are_normalised]),
 ]
 
 
