@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     p.add_argument("--views", type=int, default=N_VIEWS)
     p.add_argument("--max-blocks", type=int, default=80_000, help="grid capacity (room: 53,855 active blocks)")
-    p.add_argument("--config", default="room", choices=["room", "room_bf16_sem", "serve", "apartment"],
+    p.add_argument("--config", default="room", choices=["room", "room_bf16_sem", "serve", "apartment", "fusion"],
                    help="room: the headline training step; the others are the precision, serving and apartment "
                         "workloads (one JSON line each)")
     p.add_argument("--requests", type=int, default=2000, help="serve: requests per arrival rate")
@@ -767,6 +767,63 @@ def run_reference(args):
     return line
 
 
+def run_fusion(args):
+    """Volumetric fusion (Eq. 9-11) of the room's RGB-D views into the room grid: frames/s with all views in one
+    call and one view per call (an online loop), for an FP32 grid (depth + colour) and a BF16 grid with 20
+    logits (depth + colour + labels)."""
+    import torch
+    import paper_2305_13220_b300 as sdg
+    import synth
+    device = "cuda:0"
+    sc = synth.scene_room(0)
+    poses = synth.random_poses(sc, args.views, seed=0)
+    K = synth.intrinsics(W, H)
+    mu = BAND * VS
+    F = len(poses)
+    out = {}
+    for name, dtype, ns in (("depth_rgb_f32", "f32", 0), ("depth_rgb_sem20_bf16", "bf16", 20)):
+        G = sdg.Grid(VS, args.max_blocks, beta=BETA, rgb_dtype=dtype, n_sem=ns)
+        _activate_views(sdg, torch, G, sc, poses, K, device, BAND)
+        fr = [synth.rgbd_frame(sc, T, W, H, K, n_sem=ns, seed=i, device=device) for i, T in enumerate(poses)]
+        depth = torch.stack([f["depth"] for f in fr]).contiguous()
+        rgb = torch.stack([f["rgb"] for f in fr]).contiguous()
+        sem = torch.stack([f["sem"] for f in fr]).contiguous() if ns else None
+        del fr
+        Kt = torch.tensor(K, dtype=torch.float32)
+
+        def batch(_b, _i):
+            G.fuse(depth, Kt, poses, mu, rgb=rgb, sem=sem)
+
+        def online(_b, _i):
+            for i in range(F):
+                G.fuse(depth[i], Kt, poses[i], mu, rgb=rgb[i], sem=sem[i] if ns else None)
+
+        ms_batch = _timed_steps(torch, batch, [None], args.steps, args.warmup)
+        ms_online = _timed_steps(torch, online, [None], max(args.steps // 4, 2), 1)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        G.fuse_finalize()
+        t1.record()
+        torch.cuda.synchronize()
+        w = G.channel(sdg._abi.GROUP_WEIGHT)[:G.num_blocks, :, 0]
+        out[name] = {"frames_per_s_batched": round(F / (ms_batch / 1e3), 1), "ms_per_50_frames": round(ms_batch, 4),
+                     "frames_per_s_one_per_call": round(F / (ms_online / 1e3), 1),
+                     "finalize_ms": round(t0.elapsed_time(t1), 4), "n_blocks": G.num_blocks,
+                     "voxels_fused": int((w > 0).sum().item()),
+                     "mean_associations_per_fused_voxel": round(float(w[w > 0].mean().item()) / (args.warmup
+                                                                  + args.steps + max(args.steps // 4, 2) + 1), 2)}
+        del G, depth, rgb, sem
+        torch.cuda.empty_cache()
+    main_ = out["depth_rgb_f32"]
+    line = _line(main_["frames_per_s_batched"], "frames/s", args.steps, args.warmup, main_["ms_per_50_frames"],
+                 {"workload": f"volumetric fusion of {F} 640x480 RGB-D views (analytic depth and colour; 20 noisy "
+                              "one-hot logits for the semantic variant) into the room grid (1 cm voxels, 8^3 "
+                              f"blocks, 4-voxel band, mu = {mu} m)", "frames_per_call": F},
+                 fusion=out, gpu_launches=args.steps,
+                 paper_context="50 Hz depth + colour, 30 Hz with labels (RTX 3060, whole fusion step; context)")
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -777,6 +834,8 @@ def main():
         run_serve(args)
     elif args.config == "apartment":
         run_apartment(args)
+    elif args.config == "fusion":
+        run_fusion(args)
     else:
         run_ours(args)
 

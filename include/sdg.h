@@ -324,6 +324,50 @@ typedef struct {
 
 int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a);
 
+/* ---------------------------------------------------------------------------
+ * Volumetric fusion, Sec. 3.4.2 (Eq. 9-11) with the supplement's truncation
+ * psi(x, mu) = min(x, mu): initialises the voxels from RGB-D (+ logit) frames.
+ * Every voxel v of every allocated block b (world x = (8b + l) * voxel_size)
+ * is associated with each frame i whose pixel it projects into; the decision
+ * is taken in FP32 in this exact order (no fused multiply-add):
+ *   x_a = (float)(8 b_a + l_a) * voxel_size;  e_a = x_a - t_a
+ *   c_j = (R_0j e_0 + R_1j e_1) + R_2j e_2      (camera coordinates, c = R^T (x - t))
+ *   kept only if c_2 > 0;  pu = fx (c_0 / c_2) + cx,  pv = fy (c_1 / c_2) + cy
+ *   pixel (floor pu, floor pv) inside the image (pixel centres at +0.5, as in
+ *   activation); D = depth there finite and > 0;  o = D - c_2 (the SDF seen
+ *   from frame i, positive in front of the surface); kept only if o >= -mu
+ *   (farther behind the surface is occlusion);  psi = min(o, mu).
+ * The least-squares solutions of Eq. 9-11 are averages over the kept
+ * associations: SDF = mean psi, colour = mean pixel colour, logits
+ * s* = mean pixel logits and theta_s = s* / |s*| (Eq. 11).  They are kept as
+ * running means with the association count in the WEIGHT channel, so frames
+ * may be fused over any number of calls: theta' = (w theta + sum) / (w + n).
+ * Where the running means live until sdg_fuse_finalize:
+ *   SDF: the SDF value channel (FP32 in both layouts);
+ *   colour: the RGB value channel in the SDG_F32 layout; for SDG_BF16 the FP32
+ *     colour gradient channel, rounded into the BF16 value channel by
+ *     sdg_fuse_finalize;
+ *   logits: the FP32 semantic gradient channel; sdg_fuse_finalize writes
+ *     theta_s (rounded to BF16) into the semantic value channel.
+ * Fusion therefore precedes training: finalize (which zeroes those gradient
+ * channels) before the first training pass.  Colour and logits should be given
+ * on every call or on none, since the count is shared.
+ *   F frames of H x W pixels; depth_dev [F][H][W] float z-depth (m);
+ *   rgb_dev [F][H][W][3] float or NULL; sem_dev [F][H][W][n_sem] float logits
+ *   or NULL (SDG_ERR_ARG if the grid has no semantic channel);
+ *   K (host) [F][4] fx, fy, cx, cy (fx, fy > 0); Twc (host) [F][12] row-major
+ *   3x4 camera-to-world [R | t]; mu > 0 the truncation distance (m).
+ * Asynchronous on the grid's stream; the host arrays may be reused on return.
+ * Voxels with no kept association are not written. */
+int sdg_fuse_frames(sdg_grid g, int64_t F, int32_t H, int32_t W, const float* depth_dev, const float* rgb_dev,
+                    const float* sem_dev, const float* K, const float* Twc, float mu);
+
+/* Ends a fusion: for every voxel with a non-zero weight writes the BF16
+ * colour (SDG_BF16 layout) and theta_s = s* / |s*| (grids with logits) into
+ * the value channels, then zeroes the FP32 accumulators (colour and semantic
+ * gradient channels).  No-op for an SDG_F32 grid without logits. */
+int sdg_fuse_finalize(sdg_grid g);
+
 /* ----------------------------------------------------------------------- */
 /* Serving: continuous batching of render requests over several grids       */
 /* ----------------------------------------------------------------------- */

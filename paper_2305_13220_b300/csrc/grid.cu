@@ -331,7 +331,7 @@ void free_grid_buffers(sdg_grid g) {
     void* ptrs[] = {g->table, g->tmp_table, g->keys, g->nbr, g->bitmap, g->geo, g->ggeo, g->m_geo, g->v_geo,
                     g->sdf, g->gsdf, g->m_sdf, g->v_sdf, g->rgbh, g->grgb, g->m_rgb, g->v_rgb, g->sem, g->gsem,
                     g->m_sem, g->v_sem, g->weight, g->sort_buf, g->counters, g->minmax, g->loss_buf,
-                    g->order_keys, g->order_perm, g->order_hist};
+                    g->order_keys, g->order_perm, g->order_hist, g->fuse_cams};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->h_counters) cudaFreeHost(g->h_counters);

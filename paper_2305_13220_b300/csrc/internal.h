@@ -49,6 +49,8 @@ struct sdg_grid_s {
     int* order_perm = nullptr;  // processing order [order_cap]
     int* order_hist = nullptr;  // bucket counts, then offsets [kOrderBuckets]
     int64_t order_cap = 0;
+    void* fuse_cams = nullptr;  // per-frame cameras of a fusion call [fuse_cam_cap]
+    int64_t fuse_cam_cap = 0;
 
     std::mutex mu;  // serialises host-side mutation (activation, load) of this grid
 

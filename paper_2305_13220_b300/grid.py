@@ -101,6 +101,26 @@ class Grid:
                int(dilate_voxels), C.byref(n))
         return n.value
 
+    def fuse(self, depth: torch.Tensor, K, Twc, mu: float, rgb: Optional[torch.Tensor] = None,
+             sem: Optional[torch.Tensor] = None):
+        """Volumetric fusion (Eq. 9-11) of F frames: depth [F,H,W] or [H,W] (z-depth), optional rgb [F,H,W,3] and
+        logits [F,H,W,n_sem] on the grid's device; K [4] or [F,4]; Twc [3,4] or [F,3,4] camera-to-world.
+        Running means over calls; call fuse_finalize() once all frames are in (before training)."""
+        if depth.dim() == 2:
+            depth = depth[None]
+            rgb = rgb[None] if rgb is not None else None
+            sem = sem[None] if sem is not None else None
+        F, H, W = depth.shape
+        Kt = torch.as_tensor(K, dtype=torch.float32).reshape(-1, 4).expand(F, 4).contiguous()
+        Tt = torch.as_tensor(Twc, dtype=torch.float32).reshape(-1, 12).expand(F, 12).contiguous()
+        A.call("sdg_fuse_frames", self._h, F, H, W, _ptr(depth, torch.float32, "depth"),
+               _ptr(rgb, torch.float32, "rgb") if rgb is not None else None,
+               _ptr(sem, torch.float32, "sem") if sem is not None else None,
+               Kt.data_ptr(), Tt.data_ptr(), float(mu))
+
+    def fuse_finalize(self):
+        A.call("sdg_fuse_finalize", self._h)
+
     def activate_keys(self, keys: torch.Tensor) -> int:
         n = C.c_int64()
         A.call("sdg_grid_activate_keys", self._h, _ptr(keys, torch.int32, "keys"), keys.shape[0], C.byref(n))

@@ -403,6 +403,30 @@ def depth_map(scene: Scene, Twc: np.ndarray, W: int, H: int, K, device="cpu") ->
     return z.reshape(H, W).to(torch.float32)
 
 
+def rgbd_frame(scene: Scene, Twc: np.ndarray, W: int, H: int, K, n_sem: int = 0, seed: int = 0, device="cpu"):
+    """One analytic RGB-D(-logit) frame: z-depth (H, W), the colour at each pixel's first hit (H, W, 3) and, if
+    n_sem, logits 4*onehot(hit label mod n_sem) + N(0, 0.5^2) (H, W, n_sem), all float32.  Pixels whose ray
+    leaves the scene get depth inf and colour 0."""
+    R = torch.tensor(Twc[:, :3], dtype=F64, device=device)
+    t = torch.tensor(Twc[:, 3], dtype=F64, device=device)
+    dc = pixel_dirs_cam(W, H, K, device)
+    dw = dc @ R.T
+    o = t.expand_as(dw)
+    z = ray_hit(scene, o, dw)
+    hit = torch.isfinite(z)
+    x = o + torch.where(hit, z, torch.zeros_like(z))[:, None] * dw
+    rgb = torch.where(hit[:, None], scene_colour(scene, x), torch.zeros_like(x))
+    out = {"depth": z.reshape(H, W).to(torch.float32), "rgb": rgb.reshape(H, W, 3).to(torch.float32)}
+    if n_sem:
+        _, lab = scene_sdf(scene, x, with_label=True)
+        g = torch.Generator(device="cpu")
+        g.manual_seed(70000 + seed)
+        noise = torch.randn((H * W, n_sem), generator=g, dtype=F64).to(device) * 0.5
+        logits = 4.0 * torch.nn.functional.one_hot(lab % n_sem, n_sem).to(F64) + noise
+        out["sem"] = logits.reshape(H, W, n_sem).to(torch.float32)
+    return out
+
+
 def pack_rays(o: torch.Tensor, d: torch.Tensor, tnear: float = 0.05, tfar: float = 1.0e3) -> torch.Tensor:
     """Ray records (n, 8) float32: ox, oy, oz, tnear, dx, dy, dz, tfar."""
     n = o.shape[0]
