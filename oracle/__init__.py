@@ -88,6 +88,8 @@ def _declare(L):
         "orc_density": (_d, [_d, _d]),
         "orc_density_deriv": (_d, [_d, _d]),
         "orc_query": (None, [_p, _p, _i64, _p, _p, _p]),
+        "orc_query_grad": (None, [_p, _p, _i64, _p, _p, _p]),
+        "orc_eikonal": (_d, [_p, _p, _i64, _d, _p, _p]),
         "orc_render": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p]),
         "orc_trace": (C.c_int, [_p, _p, C.c_int, _u32, _u32, C.c_int, _p]),
         "orc_render_backward": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p,
@@ -218,6 +220,24 @@ class Grid:
         sdf, rgb, valid = np.empty(n), np.empty((n, 3)), np.empty(n, np.uint8)
         lib().orc_query(self._h, x.ctypes.data, n, sdf.ctypes.data, rgb.ctypes.data, valid.ctypes.data)
         return sdf, rgb, valid.astype(bool)
+
+    def query_grad(self, x):
+        """SDF and its closed-form gradient (Eq. 16-17) at points x (n,3): sdf (n), grad (n,3), valid (n)."""
+        x = _np(x, np.float64).reshape(-1, 3)
+        n = x.shape[0]
+        sdf, grad, valid = np.empty(n), np.empty((n, 3)), np.empty(n, np.uint8)
+        lib().orc_query_grad(self._h, x.ctypes.data, n, sdf.ctypes.data, grad.ctypes.data, valid.ctypes.data)
+        return sdf, grad, valid.astype(bool)
+
+    def eikonal(self, x, lam: float):
+        """Eikonal loss (lambda/n) sum (|grad f| - 1)^2 at points x (n,3); returns (loss, per-point terms,
+        dL/dtheta_d [N,512])."""
+        x = _np(x, np.float64).reshape(-1, 3)
+        n = x.shape[0]
+        g = np.zeros((self.n_blocks, 512))
+        terms = np.empty(n)
+        L = lib().orc_eikonal(self._h, x.ctypes.data, n, float(lam), g.ctypes.data, terms.ctypes.data)
+        return L, terms, g
 
     def render(self, rays, n_samples: int, seed: int = 0, ray_id0: int = 0, stratified: bool = True, bg=(0, 0, 0)):
         rays = _np(rays, np.float32).reshape(-1, 8)

@@ -449,6 +449,75 @@ void orc_query(void* gp, const double* x, int64_t n, double* sdf, double* rgb, u
     }
 }
 
+// Trilinear weight r(x, x_i) of stencil corner e and its gradient in x (Sec. 3.5.2): r is a product over the
+// axes of f_a (far corner) or 1 - f_a (near corner), f = x/vs - floor(x/vs); its derivative along axis a replaces
+// that axis's factor by +1/vs (far corner) or -1/vs (near corner).
+void corner_weight_grad(const Stencil& s, double vs, int e, double* r, double dr[3]) {
+    const int bit[3] = {e & 1, (e >> 1) & 1, (e >> 2) & 1};
+    double fac[3], dfac[3];
+    for (int a = 0; a < 3; ++a) {
+        fac[a] = bit[a] ? s.f[a] : 1.0 - s.f[a];
+        dfac[a] = (bit[a] ? 1.0 : -1.0) / vs;
+    }
+    *r = fac[0] * fac[1] * fac[2];
+    dr[0] = dfac[0] * fac[1] * fac[2];
+    dr[1] = fac[0] * dfac[1] * fac[2];
+    dr[2] = fac[0] * fac[1] * dfac[2];
+}
+
+// SDF and its gradient at points x (n,3) in one pass (Eq. 16-17):
+//   f(x) = sum_i r(x, x_i) theta_d(x_i),  grad_x f(x) = sum_i grad_x r(x, x_i) theta_d(x_i).
+// Invalid points (a grid point unallocated) get valid = 0 and zeros.
+void orc_query_grad(void* gp, const double* x, int64_t n, double* sdf, double* grad, uint8_t* valid) {
+    Grid* g = (Grid*)gp;
+    for (int64_t i = 0; i < n; ++i) {
+        Stencil s = stencil_at(*g, x + 3 * i);
+        valid[i] = s.valid;
+        double f = 0.0, gr[3] = {0.0, 0.0, 0.0};
+        if (s.valid)
+            for (int e = 0; e < 8; ++e) {
+                double r, dr[3];
+                corner_weight_grad(s, g->vs, e, &r, dr);
+                const double th = g->sdf[s.lin[e]];
+                f += r * th;
+                for (int a = 0; a < 3; ++a) gr[a] += dr[a] * th;
+            }
+        sdf[i] = f;
+        for (int a = 0; a < 3; ++a) grad[3 * i + a] = gr[a];
+    }
+}
+
+// Eikonal regularisation (Sec. 3.5.3): L = (lambda / n) * sum over the n points of (|grad f(x)| - 1)^2, invalid
+// points contributing 0.  Its gradient with respect to the stored SDF values,
+//   dL/dtheta_d(x_i) = (lambda / n) * 2 (|grad f| - 1) * (grad f / |grad f|) . grad_x r(x, x_i),
+// is added into g_sdf [N*512] (taken as 0 where |grad f| = 0).  Per-point terms go to terms (n) if given.
+double orc_eikonal(void* gp, const double* x, int64_t n, double lambda, double* g_sdf, double* terms) {
+    Grid* g = (Grid*)gp;
+    double L = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double f, gr[3];
+        uint8_t ok;
+        orc_query_grad(gp, x + 3 * i, 1, &f, gr, &ok);
+        double term = 0.0;
+        if (ok) {
+            const double norm = std::sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+            term = lambda / (double)n * (norm - 1.0) * (norm - 1.0);
+            if (norm > 0.0) {
+                const double c = lambda / (double)n * 2.0 * (norm - 1.0) / norm;
+                Stencil s = stencil_at(*g, x + 3 * i);
+                for (int e = 0; e < 8; ++e) {
+                    double r, dr[3];
+                    corner_weight_grad(s, g->vs, e, &r, dr);
+                    g_sdf[s.lin[e]] += c * (gr[0] * dr[0] + gr[1] * dr[1] + gr[2] * dr[2]);
+                }
+            }
+        }
+        if (terms) terms[i] = term;
+        L += term;
+    }
+    return L;
+}
+
 // Forward render of n rays (ray i uses hash id ray_id0 + i).  diag[i] = {S, n_valid, degenerate, T_N}.
 void orc_render(void* gp, const float* rays, int64_t n, int N, uint32_t seed, uint32_t ray_id0, int stratified,
                 const double* bg, double* rgb, double* depth, double* opac, double* sem, double* diag) {

@@ -192,24 +192,38 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 
 // Writes the fused colour (BF16 layout) and theta_s = s* / |s*| (Eq. 11) of every voxel with a kept
 // association into the BF16 value channels, then zeroes the FP32 accumulators (the gradient channels).
-__global__ void k_fuse_finalize(int64_t V, const float* __restrict__ weight, float4* racc, uint2* rgbh, float* sacc,
-                                __nv_bfloat16* sem, int ns) {
+// n_sem is a multiple of 4: logits move as 16-byte groups (FP32 accumulators) and 8-byte groups (BF16 values).
+template <int NS4>
+__global__ void k_fuse_finalize(int64_t V, const float* __restrict__ weight, float4* racc, uint2* rgbh,
+                                float4* sacc, uint2* sem, int ns4_rt) {
+    const int ns4 = NS4 > 0 ? NS4 : ns4_rt;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
-        const bool fused = weight[v] > 0.f;
+        const bool fused = __ldg(weight + v) > 0.f;
         if (racc) {
             const float4 r = racc[v];
             if (fused) rgbh[v] = make_uint2(pack_bf16x2(r.x, r.y), pack_bf16x2(r.z, 0.f));
-            racc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            __stcs(racc + v, make_float4(0.f, 0.f, 0.f, 0.f));
         }
         if (sacc) {
-            float* sp = sacc + (int64_t)ns * v;
+            constexpr int kCap = NS4 > 0 ? NS4 : 8;  // n_sem <= 32
+            float4* sp = sacc + (int64_t)ns4 * v;
+            float4 x[kCap];
             float nn = 0.f;
-            for (int q = 0; q < ns; ++q) nn += sp[q] * sp[q];
-            nn = sqrtf(nn);
-            if (fused)
-                for (int q = 0; q < ns; ++q)
-                    sem[(int64_t)ns * v + q] = __float2bfloat16_rn(nn > 0.f ? sp[q] / nn : 0.f);
-            for (int q = 0; q < ns; ++q) sp[q] = 0.f;
+#pragma unroll
+            for (int q = 0; q < kCap; ++q) {
+                x[q] = q < ns4 ? __ldcs(sp + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                nn += x[q].x * x[q].x + x[q].y * x[q].y + x[q].z * x[q].z + x[q].w * x[q].w;
+            }
+            const float inv = nn > 0.f ? 1.0f / sqrtf(nn) : 0.f;
+#pragma unroll
+            for (int q = 0; q < kCap; ++q) {
+                if (q < ns4) {
+                    if (fused)
+                        sem[(int64_t)ns4 * v + q] = make_uint2(pack_bf16x2(x[q].x * inv, x[q].y * inv),
+                                                               pack_bf16x2(x[q].z * inv, x[q].w * inv));
+                    __stcs(sp + q, make_float4(0.f, 0.f, 0.f, 0.f));
+                }
+            }
         }
     }
 }
@@ -297,8 +311,11 @@ extern "C" int sdg_fuse_finalize(sdg_grid g) {
     if ((!bf16 && ns == 0) || g->n_blocks == 0) return SDG_OK;
     const int64_t V = g->n_blocks * 512;
     const int blocks = (int)std::min<int64_t>((V + 255) / 256, 148 * 16);
-    k_fuse_finalize<<<blocks, 256, 0, g->stream>>>(V, g->weight, bf16 ? g->grgb : nullptr, g->rgbh,
-                                                   ns ? g->gsem : nullptr, g->sem, ns);
+    float4* racc = bf16 ? g->grgb : nullptr;
+    float4* sacc = ns ? reinterpret_cast<float4*>(g->gsem) : nullptr;
+    uint2* sem = reinterpret_cast<uint2*>(g->sem);
+    if (ns == 20) k_fuse_finalize<5><<<blocks, 256, 0, g->stream>>>(V, g->weight, racc, g->rgbh, sacc, sem, 5);
+    else k_fuse_finalize<0><<<blocks, 256, 0, g->stream>>>(V, g->weight, racc, g->rgbh, sacc, sem, ns / 4);
     SDG_LAUNCH_CHECK("fuse finalize");
     return SDG_OK;
 }

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_activation as A
+from tests import test_oracle_eikonal as Ek
 from tests import test_oracle_fusion as Fu
 from tests import test_oracle_render as R
 
@@ -51,6 +52,16 @@ MUTANTS = [
      "float fu = std::floor(pu + 0.5f), fv = std::floor(pv + 0.5f);", [Fu.test_pixel_centre_convention]),
     ("fusion_unnormalised_logits", "? (ss[q] / n) / nn : 0.0;", "? (ss[q] / n) : 0.0;",
      [Fu.test_colour_is_the_mean_and_logits_are_normalised]),
+    ("grad_no_inv_vs", "dfac[a] = (bit[a] ? 1.0 : -1.0) / vs;", "dfac[a] = (bit[a] ? 1.0 : -1.0);",
+     [Ek.test_linear_field_gradient_and_eikonal_closed_forms]),
+    ("grad_sign", "dfac[a] = (bit[a] ? 1.0 : -1.0) / vs;", "dfac[a] = (bit[a] ? -1.0 : 1.0) / vs;",
+     [Ek.test_linear_field_gradient_and_eikonal_closed_forms]),
+    ("grad_axis_swap", "dr[1] = fac[0] * dfac[1] * fac[2];", "dr[1] = fac[0] * fac[1] * dfac[2];",
+     [Ek.test_gradient_equals_central_differences_of_the_interpolant]),
+    ("eikonal_unnormalised", "* 2.0 * (norm - 1.0) / norm;", "* 2.0 * (norm - 1.0);",
+     [Ek.test_eikonal_gradient_equals_central_differences_of_the_loss]),
+    ("eikonal_no_factor_two", "* 2.0 * (norm - 1.0) / norm;", "* (norm - 1.0) / norm;",
+     [Ek.test_eikonal_gradient_equals_central_differences_of_the_loss]),
 ]
 
 
