@@ -490,7 +490,8 @@ void orc_query_grad(void* gp, const double* x, int64_t n, double* sdf, double* g
 // Eikonal regularisation (Sec. 3.5.3): L = (lambda / n) * sum over the n points of (|grad f(x)| - 1)^2, invalid
 // points contributing 0.  Its gradient with respect to the stored SDF values,
 //   dL/dtheta_d(x_i) = (lambda / n) * 2 (|grad f| - 1) * (grad f / |grad f|) . grad_x r(x, x_i),
-// is added into g_sdf [N*512] (taken as 0 where |grad f| = 0).  Per-point terms go to terms (n) if given.
+// is added into g_sdf [N*512].  Where |grad f| < 1e-4 (a flat, e.g. truncated, region) the direction of grad f is
+// undefined and the gradient is taken as 0.  Per-point terms go to terms (n) if given.
 double orc_eikonal(void* gp, const double* x, int64_t n, double lambda, double* g_sdf, double* terms) {
     Grid* g = (Grid*)gp;
     double L = 0.0;
@@ -502,7 +503,7 @@ double orc_eikonal(void* gp, const double* x, int64_t n, double lambda, double* 
         if (ok) {
             const double norm = std::sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
             term = lambda / (double)n * (norm - 1.0) * (norm - 1.0);
-            if (norm > 0.0) {
+            if (norm >= 1e-4) {
                 const double c = lambda / (double)n * 2.0 * (norm - 1.0) / norm;
                 Stencil s = stencil_at(*g, x + 3 * i);
                 for (int e = 0; e < 8; ++e) {

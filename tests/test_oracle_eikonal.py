@@ -51,6 +51,12 @@ def test_linear_field_gradient_and_eikonal_closed_forms():
         assert abs(L - lam * (scale - 1.0) ** 2) < 1e-12
         if scale == 1.0:
             assert np.abs(gs).max() < 1e-12
+    # a flat (truncated) region: |grad f| = 0, each point's term is lambda/n, and no gradient (its direction is
+    # undefined below |grad f| = 1e-4)
+    G0 = grid_with(np.full((len(keys), 512), 0.12), keys)
+    x = interior_points(100, rng, keys)
+    L, terms, gs = G0.eikonal(x, 0.1)
+    assert abs(L - 0.1) < 1e-12 and np.all(gs == 0)
     # points outside the allocated cube are invalid and contribute nothing
     far = np.array([[5.0, 5.0, 5.0], [-1.0, 0.2, 0.2]])
     _, _, ok = G.query_grad(far)
