@@ -43,7 +43,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     p.add_argument("--views", type=int, default=N_VIEWS)
     p.add_argument("--max-blocks", type=int, default=80_000, help="grid capacity (room: 53,855 active blocks)")
-    p.add_argument("--config", default="room", choices=["room", "room_bf16_sem", "serve", "apartment", "fusion"],
+    p.add_argument("--config", default="room", choices=["room", "room_bf16_sem", "serve", "apartment", "fusion",
+                                                              "query"],
                    help="room: the headline training step; the others are the precision, serving and apartment "
                         "workloads (one JSON line each)")
     p.add_argument("--requests", type=int, default=2000, help="serve: requests per arrival rate")
@@ -824,6 +825,66 @@ def run_fusion(args):
     print(json.dumps(line), flush=True)
 
 
+def run_query(args):
+    """The paper's query benchmark on the room grid: SDF and its gradient (one pass, Eq. 16-17) at the k^3 lattice
+    points of the block AABB, k = 16..512, and an Eikonal step (loss + gradient scatter) on 2^20 points drawn
+    uniformly in the allocated blocks."""
+    import torch
+    import paper_2305_13220_b300 as sdg
+    import synth
+    device = "cuda:0"
+    sc = synth.scene_room(0)
+    poses = synth.random_poses(sc, args.views, seed=0)
+    K = synth.intrinsics(W, H)
+    G = sdg.Grid(VS, args.max_blocks, beta=BETA)
+    _activate_views(sdg, torch, G, sc, poses, K, device, BAND)
+    keys, _ = _fill(sdg, torch, G, sc, VS, BAND, device)
+    kt = torch.as_tensor(keys, device=device, dtype=torch.float64)
+    lo = kt.min(0).values * 8 * VS
+    hi = (kt.max(0).values + 1) * 8 * VS
+    res = {}
+    for k in (16, 32, 64, 128, 256, 512):
+        t = (torch.arange(k, device=device, dtype=torch.float64) + 0.5) / k
+        zz, yy, xx = torch.meshgrid(t, t, t, indexing="ij")  # x fastest
+        xyz = (lo + (hi - lo) * torch.stack([xx, yy, zz], -1).reshape(-1, 3)).to(torch.float32).contiguous()
+        del zz, yy, xx
+        n = xyz.shape[0]
+        sdf = torch.empty(n, device=device)
+        grad = torch.empty((n, 3), device=device)
+
+        def q(_b, _i):
+            sdg._abi.call("sdg_query", G.handle, xyz.data_ptr(), n, sdf.data_ptr(), grad.data_ptr())
+
+        ms = _timed_steps(torch, q, [None], args.steps, args.warmup)
+        valid = int((~torch.isnan(sdf)).sum().item())
+        alg = n * (12 + 16) + valid * 8 * 4  # point in, SDF + gradient out, 8 corner SDF values per valid point
+        res[str(k)] = {"points": n, "ms": round(ms, 4), "points_per_s": round(n / (ms / 1e3), 1),
+                       "valid_points": valid, "alg_gb_s": round(alg / (ms / 1e3) / 1e9, 1)}
+        del xyz, sdf, grad
+    # Eikonal step on 2^20 points uniform in the allocated blocks
+    gen = torch.Generator(device=device)
+    gen.manual_seed(11)
+    m = 1 << 20
+    b = kt[torch.randint(0, len(keys), (m,), device=device, generator=gen)]
+    pts = ((b * 8 + torch.rand((m, 3), device=device, generator=gen, dtype=torch.float64) * 8) * VS)
+    pts = pts.to(torch.float32).contiguous()
+    total = torch.zeros(1, device=device)
+
+    def eik(_b, _i):
+        G.eikonal(pts, 0.1, loss_sum=total)
+
+    ms_eik = _timed_steps(torch, eik, [None], args.steps, args.warmup)
+    top = res["512"]
+    line = _line(top["points_per_s"], "points/s", args.steps, args.warmup, top["ms"],
+                 {"workload": "SDF + gradient query (one pass, Eq. 16-17) at the k^3 lattice points of the room grid's "
+                              "block AABB (53,855 blocks, 1 cm voxels), k = 16..512; value at k = 512",
+                  "points": top["points"]},
+                 query=res, eikonal_2p20_points={"ms": round(ms_eik, 4), "points_per_s": round(m / (ms_eik / 1e3), 1)},
+                 gpu_launches=args.steps,
+                 paper_context="the paper's figure (query time vs NGP-grid, k = 16..512) is not in the text")
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -836,6 +897,8 @@ def main():
         run_apartment(args)
     elif args.config == "fusion":
         run_fusion(args)
+    elif args.config == "query":
+        run_query(args)
     else:
         run_ours(args)
 

@@ -362,6 +362,30 @@ int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a);
 int sdg_fuse_frames(sdg_grid g, int64_t F, int32_t H, int32_t W, const float* depth_dev, const float* rgb_dev,
                     const float* sem_dev, const float* K, const float* Twc, float mu);
 
+/* ---------------------------------------------------------------------------
+ * SDF and its gradient at points, in one pass (Sec. 3.5.2, Eq. 16-17):
+ *   f(x) = sum_i r(x, x_i) theta_d(x_i),  grad f(x) = sum_i grad_x r(x, x_i) theta_d(x_i)
+ * over the 8 grid points x_i of the voxel cell holding x; r is the trilinear
+ * weight, whose derivative along an axis is +-1/voxel_size times the other two
+ * axes' factors.  The cell is floor(x * (1/voxel_size)) in FP32.
+ *   xyz_dev [n][3] float points; sdf_dev [n] and grad_dev [n][3] float outputs
+ *   (either may be NULL).  A point whose 8 grid points are not all allocated
+ *   (or outside the block-key range, or NaN) gets NaN.  Asynchronous. */
+int sdg_query(sdg_grid g, const float* xyz_dev, int64_t n, float* sdf_dev, float* grad_dev);
+
+/* Eikonal regulariser (Sec. 3.5.3) at n points:
+ *   L = (lambda / n) * sum_k (|grad f(x_k)| - 1)^2, invalid points contributing 0,
+ * and its gradient with respect to the stored SDF values,
+ *   dL/dtheta_d(x_i) = (lambda / n) 2 (|grad f| - 1) (grad f / |grad f|) . grad_x r(x, x_i)
+ * (0 where |grad f| < 1e-4: in a flat, e.g. truncated, region the direction
+ * of grad f is rounding noise), ADDED into the SDF gradient channel (the SDF lane of
+ * the FP32 gradient record, or the SDF gradient array of the BF16 layout) with
+ * atomics.  terms_dev [n] receives the per-point terms (may be NULL);
+ * loss_sum_dev [1] their sum (may be NULL; deterministic reduction).  The
+ * points are the caller's: surface samples, uniform samples in the allocated
+ * blocks, or both, as the paper combines them.  Asynchronous. */
+int sdg_eikonal(sdg_grid g, const float* xyz_dev, int64_t n, float lambda, float* terms_dev, float* loss_sum_dev);
+
 /* Ends a fusion: for every voxel with a non-zero weight writes the BF16
  * colour (SDG_BF16 layout) and theta_s = s* / |s*| (grids with logits) into
  * the value channels, then zeroes the FP32 accumulators (colour and semantic

@@ -93,6 +93,8 @@ SIGNATURES = {
     "sdg_render_backward": [_p, _p, _p, _p, _p],
     "sdg_ctx_release": [_p],
     "sdg_loss_l1": [_p, _i64, _p, _p, _p, _p, _p, _p, _P(LossOpts), _p, _p, _p, _p],
+    "sdg_query": [_p, _p, _i64, _p, _p],
+    "sdg_eikonal": [_p, _p, _i64, C.c_float, _p, _p],
     "sdg_fuse_frames": [_p, _i64, C.c_int32, C.c_int32, _p, _p, _p, _p, _p, C.c_float],
     "sdg_fuse_finalize": [_p],
     "sdg_train_step_rays": [_p, _p, _i64, _p, _p, _p, _P(RenderOpts), _P(LossOpts), _p, _p],

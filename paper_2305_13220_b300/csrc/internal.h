@@ -89,6 +89,9 @@ namespace sdg {
 // Makes g's device current for the calling thread.
 int use_device(sdg_grid g);
 
+// Grid-owned per-item loss scratch of at least n floats (grown on demand; valid until the next call on g).
+int loss_scratch(sdg_grid g, int64_t n, float** out);
+
 // Buckets of the surface ordering of a training batch (order.cu).
 constexpr int kOrderBuckets = 1 << 15;
 

@@ -5,6 +5,7 @@
 #include <new>
 
 #include "internal.h"
+#include "reduce.cuh"
 #include "render_core.cuh"
 
 using namespace sdg;
@@ -92,25 +93,28 @@ __global__ void k_loss_l1(int64_t n, int ns, const float* __restrict__ rgb, cons
     }
 }
 
-// Deterministic sum: fixed per-thread strided order, then a fixed tree.
-__global__ void __launch_bounds__(1024) k_sum(const float* __restrict__ x, int64_t n, float* out) {
-    __shared__ float s[1024];
-    float acc = 0.f;
-    for (int64_t i = threadIdx.x; i < n; i += 1024) acc += x[i];
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = 512; w > 0; w >>= 1) {
-        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[0] = s[0];
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------
+namespace sdg {
+int loss_scratch(sdg_grid g, int64_t n, float** out) {
+    if (g->loss_cap < n) {
+        if (g->loss_buf) {
+            SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));  // earlier work on the stream may still read it
+            cudaFree(g->loss_buf);
+        }
+        g->loss_buf = nullptr;
+        g->loss_cap = 0;
+        SDG_CUDA_TRY(cudaMalloc((void**)&g->loss_buf, sizeof(float) * n));
+        g->loss_cap = n;
+    }
+    *out = g->loss_buf;
+    return SDG_OK;
+}
+}  // namespace sdg
+
 extern "C" int sdg_render_forward(sdg_grid g, const float* rays, int64_t n, const sdg_render_opts* o,
                                   const sdg_render_out* out, sdg_ctx* ctx) {
     if (ctx) *ctx = nullptr;
@@ -223,17 +227,7 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
     }
     float* per_ray = loss;
     if (!per_ray && loss_sum) {
-        if (g->loss_cap < n) {  // grid-owned per-ray loss scratch, grown on demand
-            if (g->loss_buf) {
-                SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
-                cudaFree(g->loss_buf);
-            }
-            g->loss_buf = nullptr;
-            g->loss_cap = 0;
-            SDG_CUDA_TRY(cudaMalloc((void**)&g->loss_buf, sizeof(float) * n));
-            g->loss_cap = n;
-        }
-        per_ray = g->loss_buf;
+        if ((rc = loss_scratch(g, n, &per_ray))) return rc;
     }
     PassArgs a = base_args(o, n);
     a.t_rgb = trgb;

@@ -121,6 +121,22 @@ class Grid:
     def fuse_finalize(self):
         A.call("sdg_fuse_finalize", self._h)
 
+    def query(self, xyz: torch.Tensor, want_sdf: bool = True, want_grad: bool = True):
+        """SDF (n) and closed-form gradient (n, 3) at points xyz (n, 3) float32 in one pass (Eq. 16-17); NaN
+        where a grid point of the cell is not allocated."""
+        n = xyz.shape[0]
+        sdf = torch.empty(n, device=xyz.device) if want_sdf else None
+        grad = torch.empty((n, 3), device=xyz.device) if want_grad else None
+        A.call("sdg_query", self._h, _ptr(xyz, torch.float32, "xyz"), n, _ptr(sdf), _ptr(grad))
+        return sdf, grad
+
+    def eikonal(self, xyz: torch.Tensor, lam: float = 0.1, terms: Optional[torch.Tensor] = None,
+                loss_sum: Optional[torch.Tensor] = None):
+        """Eikonal loss (lam/n) sum (|grad f| - 1)^2 at points xyz (n, 3); its gradient is ADDED into the SDF
+        gradient channel.  Per-point terms to `terms` (n) and their sum to `loss_sum` (1) when given."""
+        A.call("sdg_eikonal", self._h, _ptr(xyz, torch.float32, "xyz"), xyz.shape[0], float(lam), _ptr(terms),
+               _ptr(loss_sum))
+
     def activate_keys(self, keys: torch.Tensor) -> int:
         n = C.c_int64()
         A.call("sdg_grid_activate_keys", self._h, _ptr(keys, torch.int32, "keys"), keys.shape[0], C.byref(n))
