@@ -93,7 +93,8 @@ def _declare(L):
         "orc_render": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p]),
         "orc_trace": (C.c_int, [_p, _p, C.c_int, _u32, _u32, C.c_int, _p]),
         "orc_render_backward": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p,
-                                       _p]),
+                                       _p, _p]),
+        "orc_depth_ssi": (_d, [_i64, _p, _p, _d, _p, _p]),
         "orc_count_touched": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p]),
         "orc_loss": (_d, [_i64, C.c_int, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p]),
         "orc_adam": (None, [_p, _p, _p, _p, _i64, _d, _d, _d, _d, C.c_int]),
@@ -275,7 +276,7 @@ class Grid:
         go = _np(g_opac, np.float64) if g_opac is not None else None
         gs = _np(g_sem, np.float64).reshape(n, self.n_sem) if (g_sem is not None and self.n_sem) else None
         N = self.n_blocks
-        grad = {"sdf": np.zeros((N, 512)), "rgb": np.zeros((N, 512, 3))}
+        grad = {"sdf": np.zeros((N, 512)), "rgb": np.zeros((N, 512, 3)), "beta_per_ray": np.zeros(n)}
         gsp = None
         if self.n_sem:
             grad["sem"] = np.zeros((N, 512, self.n_sem))
@@ -286,7 +287,9 @@ class Grid:
                                   gd.ctypes.data if gd is not None else None,
                                   go.ctypes.data if go is not None else None,
                                   gs.ctypes.data if gs is not None else None,
-                                  grad["sdf"].ctypes.data, grad["rgb"].ctypes.data, gsp)
+                                  grad["sdf"].ctypes.data, grad["rgb"].ctypes.data, gsp,
+                                  grad["beta_per_ray"].ctypes.data)
+        grad["beta"] = float(grad["beta_per_ray"].sum())
         return grad
 
     def count_touched(self, rays, n_samples: int, seed: int = 0, ray_id0: int = 0, stratified: bool = True):
@@ -387,3 +390,14 @@ def fuse(keys, voxel_size: float, depth, K, Twc, mu: float, rgb=None, sem=None):
     if not ns:
         del out["sem"]
     return out
+
+
+def depth_ssi(depth, t_depth, lam: float = 0.1):
+    """Scale/shift-invariant depth loss: (loss, dL/dD (n), (a, b)) with (a, b) the least-squares alignment of the
+    targets to the rendered depths."""
+    D = _np(depth, np.float64).reshape(-1)
+    t = _np(t_depth, np.float64).reshape(-1)
+    g = np.empty_like(D)
+    ab = np.empty(2)
+    L = lib().orc_depth_ssi(D.shape[0], D.ctypes.data, t.ctypes.data, float(lam), g.ctypes.data, ab.ctypes.data)
+    return L, g, (float(ab[0]), float(ab[1]))

@@ -120,6 +120,14 @@ double density(double d, double beta) { return laplace_cdf(-d, beta) / beta; }
 double density_deriv(double d, double beta) {  // d sigma / d d = -(1/beta) * pdf(-d)
     return -std::exp(-std::fabs(d) / beta) / (2.0 * beta * beta);
 }
+// d sigma / d beta, differentiating the two branches of sigma directly:
+//   d >= 0: sigma = exp(-d/beta) / (2 beta)        -> sigma (d - beta) / beta^2
+//   d <  0: sigma = (1 - exp(d/beta) / 2) / beta   -> -sigma / beta + d exp(d/beta) / (2 beta^3)
+double density_dbeta(double d, double beta) {
+    const double s = density(d, beta);
+    if (d >= 0.0) return s * (d - beta) / (beta * beta);
+    return -s / beta + d * std::exp(d / beta) / (2.0 * beta * beta * beta);
+}
 
 // ---------------------------------------------------------------------------
 // Counter-based uniform numbers for stratified sampling: the PCG integer hash
@@ -552,7 +560,9 @@ int orc_trace(void* gp, const float* ray, int N, uint32_t seed, uint32_t ray_id,
     return (int)R.smp.size();
 }
 
-// Backward: accumulates dL/dtheta (+=) for L = sum_i g_rgb_i.C_i + g_depth_i D_i + g_opac_i O_i + g_sem_i.Sem_i.
+// Backward: accumulates dL/dtheta (+=) for L = sum_i g_rgb_i.C_i + g_depth_i D_i + g_opac_i O_i + g_sem_i.Sem_i,
+// and, if grad_beta is given, dL/dbeta per ray (grad_beta[i] = sum_k dL/dtau_k delta_k dsigma_k/dbeta, the
+// Laplace scale beta as a parameter as in VolSDF).
 // Derivation of Eq. 15 w.r.t. tau_k = sigma_k delta_k (T_k = exp(-sum_{j<k} tau_j)):
 //   dL/dtau_k = T_{k+1} v_k - sum_{j>k} w_j v_j - T_N (g_rgb . bg),   v_k = g_rgb.c_k + g_depth t_k + g_opac + g_sem.s_k
 //   dL/dd_k   = delta_k sigma'(d_k) dL/dtau_k ;  dL/dc_k = w_k g_rgb ;  dL/ds_k = w_k g_sem
@@ -560,10 +570,11 @@ int orc_trace(void* gp, const float* ray, int N, uint32_t seed, uint32_t ray_id,
 void orc_render_backward(void* gp, const float* rays, int64_t n, int N, uint32_t seed, uint32_t ray_id0,
                          int stratified, const double* bg, const double* g_rgb, const double* g_depth,
                          const double* g_opac, const double* g_sem, double* grad_sdf, double* grad_rgb,
-                         double* grad_sem) {
+                         double* grad_sem, double* grad_beta) {
     Grid* g = (Grid*)gp;
     const int ns = g->n_sem;
     for (int64_t i = 0; i < n; ++i) {
+        if (grad_beta) grad_beta[i] = 0.0;
         RayResult R = render_ray(*g, rays + 8 * i, N, seed, ray_id0 + (uint32_t)i, stratified, bg);
         if (R.smp.empty()) continue;
         const double* gc = g_rgb + 3 * i;
@@ -586,6 +597,7 @@ void orc_render_backward(void* gp, const float* rays, int64_t n, int N, uint32_t
             suffix += s.w * v[k];
             if (!s.valid) continue;
             double dd = s.delta * density_deriv(s.d, g->beta) * dtau;
+            if (grad_beta) grad_beta[i] += s.delta * density_dbeta(s.d, g->beta) * dtau;
             for (int e = 0; e < 8; ++e) {
                 int64_t li = s.st.lin[e];
                 double r = s.st.r[e];
@@ -640,6 +652,40 @@ double orc_loss(int64_t n, int n_sem, const double* rgb, const double* depth, co
             g_sem[i * n_sem + c] = 2.0 * lam_s * es / n;
         }
     }
+    return L;
+}
+
+// Scale- and shift-invariant depth loss (Eq. 13, MiDaS-style alignment): (a, b) = argmin sum_i (a t_i + b - D_i)^2
+// over the batch (t = target depth, D = rendered depth), solved by the 2x2 normal equations; where the targets do
+// not vary the scale is undetermined and a = 1, b = mean(D - t).  L = (lambda / n) sum_i (D_i - a t_i - b)^2.
+// At the optimum dL/da = dL/db = 0, so dL/dD_i is the partial derivative 2 lambda (D_i - a t_i - b) / n
+// (written to g_depth).  Returns L; ab receives (a, b).
+double orc_depth_ssi(int64_t n, const double* D, const double* t, double lambda, double* g_depth, double* ab) {
+    double st = 0, sd = 0, stt = 0, std_ = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        st += t[i];
+        sd += D[i];
+        stt += t[i] * t[i];
+        std_ += t[i] * D[i];
+    }
+    const double nn = (double)n;
+    const double det = nn * stt - st * st;
+    double a, b;
+    if (n > 0 && det > 1e-12 * nn * stt) {
+        a = (nn * std_ - st * sd) / det;
+        b = (sd - a * st) / nn;
+    } else {
+        a = 1.0;
+        b = n > 0 ? (sd - st) / nn : 0.0;
+    }
+    double L = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double r = D[i] - a * t[i] - b;
+        L += lambda * r * r / nn;
+        g_depth[i] = 2.0 * lambda * r / nn;
+    }
+    ab[0] = a;
+    ab[1] = b;
     return L;
 }
 

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_activation as A
+from tests import test_oracle_beta_ssi as Bs
 from tests import test_oracle_eikonal as Ek
 from tests import test_oracle_fusion as Fu
 from tests import test_oracle_render as R
@@ -62,6 +63,14 @@ MUTANTS = [
      [Ek.test_eikonal_gradient_equals_central_differences_of_the_loss]),
     ("eikonal_no_factor_two", "* 2.0 * (norm - 1.0) / norm;", "* (norm - 1.0) / norm;",
      [Ek.test_eikonal_gradient_equals_central_differences_of_the_loss]),
+    ("dbeta_front_sign", "if (d >= 0.0) return s * (d - beta) / (beta * beta);",
+     "if (d >= 0.0) return s * (beta - d) / (beta * beta);",
+     [lambda: Bs.test_beta_gradient_matches_central_differences((0, 0, 0))]),
+    ("dbeta_behind_term", "return -s / beta + d * std::exp(d / beta) / (2.0 * beta * beta * beta);",
+     "return -s / beta;", [lambda: Bs.test_beta_gradient_matches_central_differences((0, 0, 0))]),
+    ("ssi_no_shift", "b = (sd - a * st) / nn;", "b = 0.0;", [Bs.test_ssi_loss_zero_for_affine_targets_and_invariant]),
+    ("ssi_grad_factor", "g_depth[i] = 2.0 * lambda * r / nn;", "g_depth[i] = lambda * r / nn;",
+     [Bs.test_ssi_gradient_matches_central_differences]),
 ]
 
 
