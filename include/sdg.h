@@ -235,7 +235,23 @@ typedef struct {
     float lambda_depth; /* 0.1 */
     float lambda_sem;   /* 0.1 */
     int32_t ray_order;  /* SDG_ORDER_*; used by sdg_train_step_rays only */
+    int32_t learn_beta; /* sdg_train_step_rays: also accumulate dL/dbeta (see below) */
 } sdg_loss_opts;
+
+/* Learnable Laplace scale (beta of Sec. 3.5.1 as a parameter, as VolSDF
+ * learns it).  With lo->learn_beta set, sdg_train_step_rays also accumulates
+ *   dL/dbeta = sum_k dL/dtau_k delta_k dsigma_k/dbeta
+ *            = -(1/beta) sum_k dL/dtau_k (tau_k + d_k delta_k dsigma_k/dd)
+ * (sigma = Psi(-d/beta)/beta, so dsigma/dbeta = -sigma/beta - (d/beta) dsigma/dd)
+ * into a grid-owned device scalar; the next sdg_adam_step reads it back (the
+ * one host synchronisation such a step needs), updates beta on the host with
+ * the same optimiser, hyper-parameters and step index as the voxels (moments
+ * kept in the grid and in checkpoints), clamps beta >= 1e-3 voxel sizes and
+ * zeroes the scalar.  sdg_grid_beta_grad reads the pending gradient
+ * (synchronises); sdg_grid_get_beta / sdg_grid_set_beta read and set beta. */
+int sdg_grid_get_beta(sdg_grid g, float* beta);
+int sdg_grid_set_beta(sdg_grid g, float beta);
+int sdg_grid_beta_grad(sdg_grid g, float* grad);
 
 /* Order in which sdg_train_step_rays processes a batch's rays.  The result of
  * each ray (its samples, its loss term, its gradient contributions) does not
@@ -264,6 +280,20 @@ typedef struct {
 int sdg_loss_l1(sdg_grid g, int64_t n, const float* rgb_dev, const float* depth_dev, const float* sem_dev,
                 const float* t_rgb_dev, const float* t_depth_dev, const float* t_sem_dev, const sdg_loss_opts* lo,
                 float* g_rgb_dev, float* g_depth_dev, float* g_sem_dev, float* loss_dev);
+
+/* Scale- and shift-invariant depth loss (Eq. 13 with the per-batch least
+ * squares scale a and shift b of MiDaS): (a, b) = argmin sum_i (a t_i + b - D_i)^2
+ * over the n rays (t = target depth, D = rendered depth), from FP64 sums in a
+ * fixed order (deterministic); targets without spread leave the scale
+ * undetermined and give a = 1, b = mean(D - t).
+ *   loss_i = (lambda / n) (D_i - a t_i - b)^2,  g_depth_i = 2 lambda (D_i - a t_i - b) / n
+ * (at the optimum dL/da = dL/db = 0, so the dependence of a and b on D adds
+ * nothing).  depth_dev, t_depth_dev [n]; g_depth_dev [n], loss_dev [n],
+ * loss_sum_dev [1] may each be NULL; ab (host, 2 doubles, may be NULL)
+ * receives (a, b) and makes the call synchronise.  Use with
+ * sdg_render_forward / sdg_render_backward (g_depth as the depth seed). */
+int sdg_loss_depth_ssi(sdg_grid g, int64_t n, const float* depth_dev, const float* t_depth_dev, float lambda,
+                       float* g_depth_dev, float* loss_dev, float* loss_sum_dev, double* ab);
 
 /* One fused training pass (forward, sdg_loss_l1 and backward of the same
  * rays in a single kernel; no per-sample state leaves the SM): accumulates

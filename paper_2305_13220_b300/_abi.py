@@ -36,7 +36,8 @@ class RenderOut(C.Structure):
 
 
 class LossOpts(C.Structure):
-    _fields_ = [("lambda_depth", C.c_float), ("lambda_sem", C.c_float), ("ray_order", C.c_int32)]
+    _fields_ = [("lambda_depth", C.c_float), ("lambda_sem", C.c_float), ("ray_order", C.c_int32),
+                ("learn_beta", C.c_int32)]
 
 
 class AdamOpts(C.Structure):
@@ -95,6 +96,10 @@ SIGNATURES = {
     "sdg_loss_l1": [_p, _i64, _p, _p, _p, _p, _p, _p, _P(LossOpts), _p, _p, _p, _p],
     "sdg_query": [_p, _p, _i64, _p, _p],
     "sdg_eikonal": [_p, _p, _i64, C.c_float, _p, _p],
+    "sdg_grid_get_beta": [_p, _p],
+    "sdg_grid_set_beta": [_p, C.c_float],
+    "sdg_grid_beta_grad": [_p, _p],
+    "sdg_loss_depth_ssi": [_p, _i64, _p, _p, C.c_float, _p, _p, _p, _p],
     "sdg_fuse_frames": [_p, _i64, C.c_int32, C.c_int32, _p, _p, _p, _p, _p, C.c_float],
     "sdg_fuse_finalize": [_p],
     "sdg_train_step_rays": [_p, _p, _i64, _p, _p, _p, _P(RenderOpts), _P(LossOpts), _p, _p],

@@ -3,6 +3,7 @@
 // default here).  A streaming kernel: every parameter is read and written once
 // per step (theta, g, m, v in; theta, m, v out; g zeroed), so it is bound by
 // HBM bandwidth.  Paper: arXiv 2305.13220.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -113,6 +114,31 @@ int run(sdg_grid g, const OptParams& p) {
     return SDG_OK;
 }
 
+// The learnable Laplace scale (a single parameter) is updated on the host with the same optimiser and step
+// index: its gradient, accumulated on the device by the training passes since the last step, is read back (the
+// one synchronisation a step with a learnable scale needs), then zeroed.  beta stays >= 1e-3 voxel sizes.
+int beta_step(sdg_grid g, const sdg_adam_opts* a, int32_t step) {
+    float grad = 0.f;
+    SDG_CUDA_TRY(cudaMemcpyAsync(&grad, g->beta_grad, sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    SDG_CUDA_TRY(cudaMemsetAsync(g->beta_grad, 0, sizeof(float), g->stream));
+    SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    g->beta_grad_pending = false;
+    const double gb = grad;
+    double beta = g->beta;
+    if (a->algo == SDG_OPT_ADAM) {
+        g->beta_m = a->beta1 * g->beta_m + (1.0 - a->beta1) * gb;
+        g->beta_v = a->beta2 * g->beta_v + (1.0 - a->beta2) * gb * gb;
+        const double mh = g->beta_m / (1.0 - std::pow(a->beta1, step));
+        const double vh = g->beta_v / (1.0 - std::pow(a->beta2, step));
+        beta -= a->lr * mh / (std::sqrt(vh) + a->eps);
+    } else {
+        g->beta_v = a->beta2 * g->beta_v + (1.0 - a->beta2) * gb * gb;
+        beta -= a->lr * gb / (std::sqrt(g->beta_v) + a->eps);
+    }
+    g->beta = (float)std::max(beta, 1e-3 * (double)g->desc.voxel_size);
+    return SDG_OK;
+}
+
 }  // namespace
 
 extern "C" int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a) {
@@ -123,6 +149,7 @@ extern "C" int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a) {
     if (rc) return rc;
     const int32_t step = a->step > 0 ? a->step : g->step + 1;
     g->step = step;
+    if (g->beta_grad_pending && (rc = beta_step(g, a, step))) return rc;
     if (g->n_blocks == 0) return SDG_OK;
     OptParams p;
     p.lr = (float)a->lr;

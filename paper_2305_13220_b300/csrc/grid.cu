@@ -3,6 +3,7 @@
 // checkpointing.  Paper: arXiv 2305.13220.
 #include <atomic>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -331,7 +332,8 @@ void free_grid_buffers(sdg_grid g) {
     void* ptrs[] = {g->table, g->tmp_table, g->keys, g->nbr, g->bitmap, g->geo, g->ggeo, g->m_geo, g->v_geo,
                     g->sdf, g->gsdf, g->m_sdf, g->v_sdf, g->rgbh, g->grgb, g->m_rgb, g->v_rgb, g->sem, g->gsem,
                     g->m_sem, g->v_sem, g->weight, g->sort_buf, g->counters, g->minmax, g->loss_buf,
-                    g->order_keys, g->order_perm, g->order_hist, g->fuse_cams};
+                    g->order_keys, g->order_perm, g->order_hist, g->fuse_cams, g->beta_grad, g->beta_part,
+                    g->ssi_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->h_counters) cudaFreeHost(g->h_counters);
@@ -525,6 +527,8 @@ extern "C" int sdg_grid_create(const sdg_grid_desc* d, sdg_grid* out) {
         if ((r = dalloc(&g->sort_buf, g->sort_cap, s))) return r;
         if ((r = dalloc(&g->counters, 8, s))) return r;
         if ((r = dalloc(&g->minmax, 6, s))) return r;
+        if ((r = dalloc(&g->beta_grad, 1, s))) return r;
+        if ((r = dalloc(&g->ssi_dev, 2, s))) return r;
         SDG_CUDA_TRY(cudaMallocHost((void**)&g->h_counters, 8 * sizeof(unsigned long long)));
         SDG_CUDA_TRY(cudaMallocHost((void**)&g->h_minmax, 6 * sizeof(int)));
         SDG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -705,6 +709,27 @@ extern "C" int sdg_grid_set_step(sdg_grid g, int32_t step) {
     return SDG_OK;
 }
 
+extern "C" int sdg_grid_get_beta(sdg_grid g, float* beta) {
+    if (!g || !beta) return fail(SDG_ERR_ARG, "sdg_grid_get_beta: null argument");
+    *beta = g->beta;
+    return SDG_OK;
+}
+
+extern "C" int sdg_grid_set_beta(sdg_grid g, float beta) {
+    if (!g || !(beta > 0.f)) return fail(SDG_ERR_ARG, "sdg_grid_set_beta: beta must be > 0");
+    g->beta = beta;
+    return SDG_OK;
+}
+
+extern "C" int sdg_grid_beta_grad(sdg_grid g, float* grad) {
+    if (!g || !grad) return fail(SDG_ERR_ARG, "sdg_grid_beta_grad: null argument");
+    int rc = use_device(g);
+    if (rc) return rc;
+    SDG_CUDA_TRY(cudaMemcpyAsync(grad, g->beta_grad, sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return SDG_OK;
+}
+
 extern "C" int sdg_grid_sync(sdg_grid g) {
     if (!g) return fail(SDG_ERR_ARG, "null grid");
     int rc = use_device(g);
@@ -718,12 +743,14 @@ extern "C" int sdg_grid_sync(sdg_grid g) {
 // ---------------------------------------------------------------------------
 namespace {
 struct FileHeader {
-    char magic[8];  // "SDGGRID1"
+    char magic[8];  // "SDGGRID2" ("SDGGRID1": the same without the fields after `reserved`)
     float voxel_size, beta;
     int32_t rgb_dtype, n_sem;
     int64_t n_blocks;
     int32_t step, reserved;
+    double beta_m, beta_v;  // optimiser moments of the learnable Laplace scale
 };
+constexpr size_t kHeaderV1 = offsetof(FileHeader, beta_m);
 
 // (group, kind) pairs saved, in file order.
 const int kSaved[][2] = {{SDG_GROUP_GEO, SDG_KIND_VALUE},  {SDG_GROUP_GEO, SDG_KIND_GRAD},
@@ -746,7 +773,9 @@ extern "C" int sdg_grid_save(sdg_grid g, const char* path) {
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(SDG_ERR_IO, std::string("cannot open ") + path);
     FileHeader h{};
-    std::memcpy(h.magic, "SDGGRID1", 8);
+    std::memcpy(h.magic, "SDGGRID2", 8);
+    h.beta_m = g->beta_m;
+    h.beta_v = g->beta_v;
     h.voxel_size = g->desc.voxel_size;
     h.beta = g->beta;
     h.rgb_dtype = g->desc.rgb_dtype;
@@ -777,7 +806,10 @@ extern "C" int sdg_grid_load(const char* path, const sdg_grid_desc* over, sdg_gr
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(SDG_ERR_IO, std::string("cannot open ") + path);
     FileHeader h{};
-    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "SDGGRID1", 8) != 0 || h.n_blocks < 0) {
+    bool head = std::fread(&h, kHeaderV1, 1, f) == 1 && h.n_blocks >= 0;
+    const bool v2 = head && std::memcmp(h.magic, "SDGGRID2", 8) == 0;
+    if (v2) head = std::fread(reinterpret_cast<char*>(&h) + kHeaderV1, sizeof(h) - kHeaderV1, 1, f) == 1;
+    if (!head || (!v2 && std::memcmp(h.magic, "SDGGRID1", 8) != 0)) {
         std::fclose(f);
         return fail(SDG_ERR_IO, "not a grid file");
     }
@@ -833,6 +865,8 @@ extern "C" int sdg_grid_load(const char* path, const sdg_grid_desc* over, sdg_gr
         }
     }
     g->step = h.step;
+    g->beta_m = v2 ? h.beta_m : 0.0;
+    g->beta_v = v2 ? h.beta_v : 0.0;
     SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
     *out = g;
     return SDG_OK;

@@ -51,6 +51,14 @@ struct sdg_grid_s {
     int64_t order_cap = 0;
     void* fuse_cams = nullptr;  // per-frame cameras of a fusion call [fuse_cam_cap]
     int64_t fuse_cam_cap = 0;
+    // learnable Laplace scale: dL/dbeta accumulates on the device until the next optimiser step
+    float* beta_grad = nullptr;  // device [1]
+    float* beta_part = nullptr;  // per-ray dL/dbeta [beta_part_cap]
+    int64_t beta_part_cap = 0;
+    bool beta_grad_pending = false;
+    double beta_m = 0.0, beta_v = 0.0;  // the scale's optimiser moments
+    double ssi_ab[2] = {0.0, 0.0};
+    double* ssi_dev = nullptr;  // device [2]: (a, b) of the last scale/shift-invariant depth loss
 
     std::mutex mu;  // serialises host-side mutation (activation, load) of this grid
 

@@ -93,6 +93,56 @@ __global__ void k_loss_l1(int64_t n, int ns, const float* __restrict__ rgb, cons
     }
 }
 
+// Least-squares alignment (a, b) of the targets t to the rendered depths D (scale/shift-invariant depth loss):
+// FP64 sums of t, D, t^2, t D in a fixed order by one block, then the 2x2 normal equations; targets without
+// spread leave the scale undetermined, and a = 1, b = mean(D - t).
+__global__ void __launch_bounds__(1024) k_ssi_fit(const float* __restrict__ D, const float* __restrict__ t,
+                                                  int64_t n, double* ab) {
+    __shared__ double s[4][1024];
+    double st = 0.0, sd = 0.0, stt = 0.0, std_ = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) {
+        const double ti = t[i], di = D[i];
+        st += ti;
+        sd += di;
+        stt += ti * ti;
+        std_ += ti * di;
+    }
+    s[0][threadIdx.x] = st;
+    s[1][threadIdx.x] = sd;
+    s[2][threadIdx.x] = stt;
+    s[3][threadIdx.x] = std_;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 4; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double nn = (double)n, T = s[0][0], Dd = s[1][0], TT = s[2][0], TD = s[3][0];
+        const double det = nn * TT - T * T;
+        double a = 1.0, b = (Dd - T) / nn;
+        if (det > 1e-12 * nn * TT) {
+            a = (nn * TD - T * Dd) / det;
+            b = (Dd - a * T) / nn;
+        }
+        ab[0] = a;
+        ab[1] = b;
+    }
+}
+
+// (lambda/n)(D - a t - b)^2 per ray and its derivative 2 lambda (D - a t - b)/n (the envelope theorem: a and b
+// are at their optimum, so their own dependence on D adds nothing).
+__global__ void k_ssi_seeds(const float* __restrict__ D, const float* __restrict__ t, int64_t n,
+                            const double* __restrict__ ab, float lam_over_n, float* __restrict__ g_depth,
+                            float* __restrict__ loss) {
+    const float a = (float)ab[0], b = (float)ab[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float r = D[i] - fmaf(a, t[i], b);
+        if (g_depth) g_depth[i] = 2.f * lam_over_n * r;
+        if (loss) loss[i] = lam_over_n * r * r;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -240,11 +290,57 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
     if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
         if ((rc = order_rays_by_surface(g, rays, tdepth, n, &a.perm))) return rc;
     }
-    rc = launch_pass<PASS_TRAIN>(g, rays, o->ray_id0, a);
-    if (rc) return rc;
+    if (lo->learn_beta) {
+        if (g->beta_part_cap < n) {
+            if (g->beta_part) {
+                SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
+                cudaFree(g->beta_part);
+            }
+            g->beta_part = nullptr;
+            g->beta_part_cap = 0;
+            SDG_CUDA_TRY(cudaMalloc((void**)&g->beta_part, sizeof(float) * n));
+            g->beta_part_cap = n;
+        }
+        a.beta_part = g->beta_part;
+        rc = launch_pass<PASS_TRAIN_BETA>(g, rays, o->ray_id0, a);
+        if (rc) return rc;
+        k_sum<true><<<1, 1024, 0, g->stream>>>(g->beta_part, n, g->beta_grad);  // dL/dbeta += sum over rays
+        SDG_LAUNCH_CHECK("beta gradient sum");
+        g->beta_grad_pending = true;
+    } else {
+        rc = launch_pass<PASS_TRAIN>(g, rays, o->ray_id0, a);
+        if (rc) return rc;
+    }
     if (loss_sum) {
         k_sum<<<1, 1024, 0, g->stream>>>(per_ray, n, loss_sum);
         SDG_LAUNCH_CHECK("loss sum");
+    }
+    return SDG_OK;
+}
+
+extern "C" int sdg_loss_depth_ssi(sdg_grid g, int64_t n, const float* depth, const float* t_depth, float lambda,
+                                  float* g_depth, float* loss, float* loss_sum, double* ab_host) {
+    if (!g || n < 0 || (n > 0 && (!depth || !t_depth))) return fail(SDG_ERR_ARG, "sdg_loss_depth_ssi: null argument");
+    int rc = use_device(g);
+    if (rc) return rc;
+    if (n == 0) {
+        if (loss_sum) SDG_CUDA_TRY(cudaMemsetAsync(loss_sum, 0, sizeof(float), g->stream));
+        return SDG_OK;
+    }
+    k_ssi_fit<<<1, 1024, 0, g->stream>>>(depth, t_depth, n, g->ssi_dev);
+    SDG_LAUNCH_CHECK("depth alignment");
+    float* per_ray = loss;
+    if (!per_ray && loss_sum && (rc = loss_scratch(g, n, &per_ray))) return rc;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    k_ssi_seeds<<<blocks, 256, 0, g->stream>>>(depth, t_depth, n, g->ssi_dev, lambda / (float)n, g_depth, per_ray);
+    SDG_LAUNCH_CHECK("depth loss");
+    if (loss_sum) {
+        k_sum<<<1, 1024, 0, g->stream>>>(per_ray, n, loss_sum);
+        SDG_LAUNCH_CHECK("depth loss sum");
+    }
+    if (ab_host) {
+        SDG_CUDA_TRY(cudaMemcpyAsync(ab_host, g->ssi_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+        SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
     }
     return SDG_OK;
 }

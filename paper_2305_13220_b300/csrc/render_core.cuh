@@ -32,7 +32,15 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWarpsPerBlock = 8;
 constexpr int kSegs = 8;  // allocated cells recorded per lane piece
 
-enum PassMode { PASS_FWD = 0, PASS_FWD_STORE = 1, PASS_BWD = 2, PASS_BWD_STORE = 3, PASS_TRAIN = 4 };
+// PASS_TRAIN_BETA is PASS_TRAIN that also returns dL/dbeta per ray (the Laplace scale as a parameter).
+enum PassMode {
+    PASS_FWD = 0,
+    PASS_FWD_STORE = 1,
+    PASS_BWD = 2,
+    PASS_BWD_STORE = 3,
+    PASS_TRAIN = 4,
+    PASS_TRAIN_BETA = 5
+};
 
 // Store-mode record channels per sample: t, sdf (NaN if invalid), r, g, b, block index (int bits).
 constexpr int kRecChannels = 6;
@@ -51,6 +59,7 @@ struct PassArgs {
     float lam_d, lam_s, inv_n;
     float* loss;
     const int* perm;  // optional processing order: warp slot i runs ray perm[i] (NULL: ray i)
+    float* beta_part;  // PASS_TRAIN_BETA: dL/dbeta of each ray [n]
 };
 
 struct RayJob {
@@ -355,7 +364,9 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                                             int lane) {
     constexpr bool kStoreIn = MODE == PASS_BWD_STORE;
     constexpr bool kStoreOut = MODE == PASS_FWD_STORE;
-    constexpr bool kBwd = MODE == PASS_BWD || MODE == PASS_BWD_STORE || MODE == PASS_TRAIN;
+    constexpr bool kTrain = MODE == PASS_TRAIN || MODE == PASS_TRAIN_BETA;
+    constexpr bool kBeta = MODE == PASS_TRAIN_BETA;
+    constexpr bool kBwd = MODE == PASS_BWD || MODE == PASS_BWD_STORE || kTrain;
     constexpr bool kFwdOut = MODE == PASS_FWD || MODE == PASS_FWD_STORE;
     constexpr int SEMCAP = SEM ? 32 : 0;
     const int N = a.N;
@@ -391,11 +402,13 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 
     float t_[Q], dl_[Q], d_[Q], cr_[Q], cg_[Q], cb_[Q], tau_[Q], dsig_[Q], fx_[Q], fy_[Q], fz_[Q];
     int blk_[Q], lc_[Q];
+    float bq_[kBeta ? Q : 1];
     unsigned vmask = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int k = lane * Q + i;
         t_[i] = 0.f; dl_[i] = 0.f; d_[i] = 0.f; cr_[i] = cg_[i] = cb_[i] = 0.f; tau_[i] = 0.f; dsig_[i] = 0.f;
+        if constexpr (kBeta) bq_[i] = 0.f;
         fx_[i] = fy_[i] = fz_[i] = 0.f; blk_[i] = -1; lc_[i] = 0;
         if (!any || k >= N) continue;
         float sn;
@@ -458,6 +471,9 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             const float sig = d_[i] >= 0.f ? 0.5f * g.inv_beta * e : g.inv_beta * (1.f - 0.5f * e);
             tau_[i] = sig * dl_[i];
             dsig_[i] = -0.5f * g.inv_beta * g.inv_beta * e * dl_[i];  // delta * dsigma/dd
+            // sigma = Psi(-d/beta)/beta gives dsigma/dbeta = -sigma/beta - (d/beta) dsigma/dd, so
+            // delta dsigma/dbeta = -(tau + d * dsig) / beta: keep tau + d * dsig for the backward
+            if constexpr (kBeta) bq_[i] = fmaf(d_[i], dsig_[i], tau_[i]);
         }
         if constexpr (kStoreOut) {
             float* rec = a.rec + j.idx * RS + i * 32 + lane;
@@ -506,7 +522,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 #pragma unroll
         for (int c = 0; c < SEMCAP; ++c) sem_acc[c] = 0.f;
     }
-    if constexpr (SEM && (kFwdOut || MODE == PASS_TRAIN)) {
+    if constexpr (SEM && (kFwdOut || kTrain)) {
         if (any) {
             float W[8];
             int addr[8];
@@ -585,7 +601,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     // ---------------- gradient seeds ----------------
     float gC0, gC1, gC2, gD, gO;
     float gS[SEMCAP > 0 ? SEMCAP : 1];
-    if constexpr (MODE == PASS_TRAIN) {
+    if constexpr (kTrain) {
         // L1 colour + lambda_d L1 depth (+ lambda_s squared L2 logits), mean over rays
         const float e0 = C0 - a.t_rgb[3 * j.idx], e1 = C1 - a.t_rgb[3 * j.idx + 1], e2 = C2 - a.t_rgb[3 * j.idx + 2];
         const float ed = D - a.t_depth[j.idx];
@@ -615,7 +631,11 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             for (int c = 0; c < SEMCAP; ++c) gS[c] = (c < ns && a.g_sem) ? a.g_sem[j.idx * ns + c] : 0.f;
         }
     }
-    if (!any) return;
+    if (!any) {
+        if constexpr (kBeta)
+            if (lane == 0) a.beta_part[j.idx] = 0.f;
+        return;
+    }
 
     // v_k = g_rgb . c_k + g_depth t_k + g_opac + g_sem . s_k
     float v_[Q];
@@ -667,11 +687,17 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     float R = warp_excl_suffix(lane_wv, lane);
     const float ubg = TN * (gC0 * a.bg[0] + gC1 * a.bg[1] + gC2 * a.bg[2]);
     float dd_[Q];
+    float bsum = 0.f;  // sum_k dL/dtau_k (tau_k + d_k dsig_k)
 #pragma unroll
     for (int i = Q - 1; i >= 0; --i) {
         const float dtau = Tn_[i] * v_[i] - R - ubg;
         R = fmaf(w_[i], v_[i], R);
         dd_[i] = ((vmask >> i) & 1u) ? dsig_[i] * dtau : 0.f;
+        if constexpr (kBeta) bsum = fmaf(dtau, bq_[i], bsum);
+    }
+    if constexpr (kBeta) {
+        bsum = warp_sum(bsum);
+        if (lane == 0) a.beta_part[j.idx] = -bsum * g.inv_beta;
     }
 
     // ---------------- scatter to voxels (runs of same-cell samples) ----------------

@@ -4,3 +4,4 @@
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD, true, true)
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD_STORE, true, true)
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN, true, true)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_BETA, true, true)

@@ -4,3 +4,4 @@
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD, false, true)
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD_STORE, false, true)
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN, false, true)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_BETA, false, true)

@@ -182,6 +182,23 @@ class Grid:
         A.call("sdg_grid_sync", self._h)
 
     @property
+    def beta(self) -> float:
+        """Laplace scale of the SDF-to-density transform (learnable through train_step_rays(learn_beta=True))."""
+        b = C.c_float()
+        A.call("sdg_grid_get_beta", self._h, C.byref(b))
+        return b.value
+
+    @beta.setter
+    def beta(self, v: float):
+        A.call("sdg_grid_set_beta", self._h, float(v))
+
+    def beta_grad(self) -> float:
+        """dL/dbeta accumulated since the last optimiser step (synchronises)."""
+        b = C.c_float()
+        A.call("sdg_grid_beta_grad", self._h, C.byref(b))
+        return b.value
+
+    @property
     def step(self) -> int:
         s = C.c_int32()
         A.call("sdg_grid_get_step", self._h, C.byref(s))

@@ -72,20 +72,33 @@ def loss_l1(grid: Grid, rgb, depth, t_rgb, t_depth, sem=None, t_sem=None, lambda
     return loss, g
 
 
+def loss_depth_ssi(grid: Grid, depth, t_depth, lam: float = 0.1, want_ab: bool = False):
+    """Scale/shift-invariant depth loss: per-ray terms, depth seeds dL/dD and, if want_ab, the fitted (a, b)."""
+    n = depth.shape[0]
+    g = torch.empty_like(depth)
+    loss = torch.empty(n, device=depth.device)
+    ab = (C.c_double * 2)()
+    A.call("sdg_loss_depth_ssi", grid.handle, n, _ptr(depth, torch.float32, "depth"),
+           _ptr(t_depth, torch.float32, "t_depth"), float(lam), _ptr(g), _ptr(loss), None, ab if want_ab else None)
+    return (loss, g, (ab[0], ab[1])) if want_ab else (loss, g)
+
+
 def train_step_rays(grid: Grid, rays: torch.Tensor, t_rgb: torch.Tensor, t_depth: torch.Tensor,
                     t_sem: Optional[torch.Tensor] = None, n_samples: int = 128, seed: int = 0, ray_id0: int = 0,
                     stratified: bool = True, bg=(0.0, 0.0, 0.0), lambda_depth: float = 0.1, lambda_sem: float = 0.1,
                     loss: Optional[torch.Tensor] = None, loss_sum: Optional[torch.Tensor] = None,
-                    ray_order: str = "auto"):
+                    ray_order: str = "auto", learn_beta: bool = False):
     """Fused forward + L1 losses + backward; gradients accumulate into the grid.
 
     ray_order: "auto" (surface order for batches of 65536 rays or more), "given" or "surface" (rays grouped by
-    the coarse cell of their target surface point; per-ray results are unchanged)."""
+    the coarse cell of their target surface point; per-ray results are unchanged).  learn_beta: also accumulate
+    dL/dbeta for the next optimiser step, which then updates the grid's Laplace scale."""
     o = render_opts(n_samples, seed, ray_id0, stratified, "recompute", bg)
     orders = {"auto": A.ORDER_AUTO, "given": A.ORDER_GIVEN, "surface": A.ORDER_SURFACE}
     if ray_order not in orders:
         raise ValueError(f"ray_order must be one of {sorted(orders)}")
-    lo = A.LossOpts(lambda_depth=lambda_depth, lambda_sem=lambda_sem, ray_order=orders[ray_order])
+    lo = A.LossOpts(lambda_depth=lambda_depth, lambda_sem=lambda_sem, ray_order=orders[ray_order],
+                    learn_beta=1 if learn_beta else 0)
     A.call("sdg_train_step_rays", grid.handle, _ptr(rays, torch.float32, "rays"), rays.shape[0],
            _ptr(t_rgb, torch.float32, "t_rgb"), _ptr(t_depth, torch.float32, "t_depth"), _ptr(t_sem), C.byref(o),
            C.byref(lo), _ptr(loss), _ptr(loss_sum))

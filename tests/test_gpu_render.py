@@ -111,6 +111,7 @@ def _oracle_backward_runs(O, rays, runs, N, seed, stratified, bg, seeds):
     for a, b in runs:
         g = O.backward(rays[a:b], N, gc[a:b], gd[a:b], go[a:b], None if gs is None else gs[a:b], seed=seed,
                        ray_id0=a, stratified=stratified, bg=bg)
+        g = {k: g[k] for k in ("sdf", "rgb", "sem", "beta") if k in g}  # per-voxel arrays and the scalar beta
         tot = g if tot is None else {k: tot[k] + g[k] for k in g}
     return tot
 
