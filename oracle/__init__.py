@@ -90,10 +90,11 @@ def _declare(L):
         "orc_query": (None, [_p, _p, _i64, _p, _p, _p]),
         "orc_query_grad": (None, [_p, _p, _i64, _p, _p, _p]),
         "orc_eikonal": (_d, [_p, _p, _i64, _d, _p, _p]),
-        "orc_render": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p]),
+        "orc_render": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p]),
+        "orc_loss_normal": (_d, [_i64, _p, _p, _d, _p]),
         "orc_trace": (C.c_int, [_p, _p, C.c_int, _u32, _u32, C.c_int, _p]),
         "orc_render_backward": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p,
-                                       _p, _p]),
+                                       _p, _p, _p]),
         "orc_depth_ssi": (_d, [_i64, _p, _p, _d, _p, _p]),
         "orc_count_touched": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p]),
         "orc_loss": (_d, [_i64, C.c_int, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p]),
@@ -244,14 +245,15 @@ class Grid:
         rays = _np(rays, np.float32).reshape(-1, 8)
         n = rays.shape[0]
         bgv = np.asarray(bg, np.float64)
-        out = {"rgb": np.empty((n, 3)), "depth": np.empty(n), "opac": np.empty(n), "diag": np.empty((n, 4))}
+        out = {"rgb": np.empty((n, 3)), "depth": np.empty(n), "opac": np.empty(n), "diag": np.empty((n, 4)),
+               "normal": np.empty((n, 3))}
         semp = None
         if self.n_sem:
             out["sem"] = np.empty((n, self.n_sem))
             semp = out["sem"].ctypes.data
         lib().orc_render(self._h, rays.ctypes.data, n, int(n_samples), _u32(seed), _u32(ray_id0), int(stratified),
                          bgv.ctypes.data, out["rgb"].ctypes.data, out["depth"].ctypes.data, out["opac"].ctypes.data,
-                         semp, out["diag"].ctypes.data)
+                         semp, out["diag"].ctypes.data, out["normal"].ctypes.data)
         out["S"] = out["diag"][:, 0]
         out["n_valid"] = out["diag"][:, 1]
         out["degenerate"] = out["diag"][:, 2] > 0
@@ -268,7 +270,7 @@ class Grid:
         return {c: out[:k, i] for i, c in enumerate(cols)}
 
     def backward(self, rays, n_samples: int, g_rgb, g_depth=None, g_opac=None, g_sem=None, seed: int = 0,
-                 ray_id0: int = 0, stratified: bool = True, bg=(0, 0, 0)):
+                 ray_id0: int = 0, stratified: bool = True, bg=(0, 0, 0), g_normal=None):
         rays = _np(rays, np.float32).reshape(-1, 8)
         n = rays.shape[0]
         g_rgb = _np(g_rgb, np.float64).reshape(n, 3)
@@ -282,13 +284,14 @@ class Grid:
             grad["sem"] = np.zeros((N, 512, self.n_sem))
             gsp = grad["sem"].ctypes.data
         bgv = np.asarray(bg, np.float64)
+        gn = _np(g_normal, np.float64).reshape(n, 3) if g_normal is not None else None
         lib().orc_render_backward(self._h, rays.ctypes.data, n, int(n_samples), _u32(seed), _u32(ray_id0),
                                   int(stratified), bgv.ctypes.data, g_rgb.ctypes.data,
                                   gd.ctypes.data if gd is not None else None,
                                   go.ctypes.data if go is not None else None,
                                   gs.ctypes.data if gs is not None else None,
                                   grad["sdf"].ctypes.data, grad["rgb"].ctypes.data, gsp,
-                                  grad["beta_per_ray"].ctypes.data)
+                                  grad["beta_per_ray"].ctypes.data, gn.ctypes.data if gn is not None else None)
         grad["beta"] = float(grad["beta_per_ray"].sum())
         return grad
 
@@ -401,3 +404,12 @@ def depth_ssi(depth, t_depth, lam: float = 0.1):
     ab = np.empty(2)
     L = lib().orc_depth_ssi(D.shape[0], D.ctypes.data, t.ctypes.data, float(lam), g.ctypes.data, ab.ctypes.data)
     return L, g, (float(ab[0]), float(ab[1]))
+
+
+def loss_normal(normal, t_normal, lam: float = 0.05):
+    """L1 normal loss (Eq. 14): (loss, dL/dN (n,3))."""
+    N = _np(normal, np.float64).reshape(-1, 3)
+    Nt = _np(t_normal, np.float64).reshape(-1, 3)
+    g = np.empty_like(N)
+    L = lib().orc_loss_normal(N.shape[0], N.ctypes.data, Nt.ctypes.data, float(lam), g.ctypes.data)
+    return L, g

@@ -214,6 +214,7 @@ struct Sample {
     bool valid;
     Stencil st;
     double d, c[3];
+    double gf[3];  // grad f at the sample (Eq. 17), for the rendered normal of Eq. 14
     std::vector<double> sem;
     double sigma, tau, T, w;
 };
@@ -223,10 +224,27 @@ struct RayResult {
     std::vector<Interval> iv;
     double S = 0.0, TN = 1.0;
     double C[3] = {0, 0, 0}, D = 0.0, O = 0.0;
+    double Nrm[3] = {0, 0, 0};  // rendered normal sum_k w_k grad f(x_k) (Eq. 14)
     std::vector<double> sem;
     int n_valid = 0;
     bool degenerate = false;
 };
+
+// Trilinear weight r(x, x_i) of stencil corner e and its gradient in x (Sec. 3.5.2): r is a product over the
+// axes of f_a (far corner) or 1 - f_a (near corner), f = x/vs - floor(x/vs); its derivative along axis a replaces
+// that axis's factor by +1/vs (far corner) or -1/vs (near corner).
+void corner_weight_grad(const Stencil& s, double vs, int e, double* r, double dr[3]) {
+    const int bit[3] = {e & 1, (e >> 1) & 1, (e >> 2) & 1};
+    double fac[3], dfac[3];
+    for (int a = 0; a < 3; ++a) {
+        fac[a] = bit[a] ? s.f[a] : 1.0 - s.f[a];
+        dfac[a] = (bit[a] ? 1.0 : -1.0) / vs;
+    }
+    *r = fac[0] * fac[1] * fac[2];
+    dr[0] = dfac[0] * fac[1] * fac[2];
+    dr[1] = fac[0] * dfac[1] * fac[2];
+    dr[2] = fac[0] * fac[1] * dfac[2];
+}
 
 bool valid_at(const Grid& g, const double x[3]) { return stencil_at(g, x).valid; }
 
@@ -264,10 +282,14 @@ RayResult render_ray(const Grid& g, const float* ray, int N, uint32_t seed, uint
         sm.valid = sm.st.valid;
         sm.d = 0.0;
         sm.c[0] = sm.c[1] = sm.c[2] = 0.0;
+        sm.gf[0] = sm.gf[1] = sm.gf[2] = 0.0;
         sm.sem.assign(g.n_sem, 0.0);
         if (sm.valid) {
             for (int e = 0; e < 8; ++e) {
                 int64_t li = sm.st.lin[e];
+                double r, dr[3];
+                corner_weight_grad(sm.st, g.vs, e, &r, dr);
+                for (int a = 0; a < 3; ++a) sm.gf[a] += dr[a] * g.sdf[li];
                 sm.d += sm.st.r[e] * g.sdf[li];
                 for (int c = 0; c < 3; ++c) sm.c[c] += sm.st.r[e] * g.rgb[li * 3 + c];
                 for (int c = 0; c < g.n_sem; ++c) sm.sem[c] += sm.st.r[e] * g.sem[li * g.n_sem + c];
@@ -294,6 +316,7 @@ RayResult render_ray(const Grid& g, const float* ray, int N, uint32_t seed, uint
         sm.w = sm.T * (1.0 - std::exp(-sm.tau));
         cum += sm.tau;
         for (int c = 0; c < 3; ++c) R.C[c] += sm.w * sm.c[c];
+        for (int a = 0; a < 3; ++a) R.Nrm[a] += sm.w * sm.gf[a];
         R.D += sm.w * sm.t;
         R.O += sm.w;
         for (int c = 0; c < g.n_sem; ++c) R.sem[c] += sm.w * sm.sem[c];
@@ -457,22 +480,6 @@ void orc_query(void* gp, const double* x, int64_t n, double* sdf, double* rgb, u
     }
 }
 
-// Trilinear weight r(x, x_i) of stencil corner e and its gradient in x (Sec. 3.5.2): r is a product over the
-// axes of f_a (far corner) or 1 - f_a (near corner), f = x/vs - floor(x/vs); its derivative along axis a replaces
-// that axis's factor by +1/vs (far corner) or -1/vs (near corner).
-void corner_weight_grad(const Stencil& s, double vs, int e, double* r, double dr[3]) {
-    const int bit[3] = {e & 1, (e >> 1) & 1, (e >> 2) & 1};
-    double fac[3], dfac[3];
-    for (int a = 0; a < 3; ++a) {
-        fac[a] = bit[a] ? s.f[a] : 1.0 - s.f[a];
-        dfac[a] = (bit[a] ? 1.0 : -1.0) / vs;
-    }
-    *r = fac[0] * fac[1] * fac[2];
-    dr[0] = dfac[0] * fac[1] * fac[2];
-    dr[1] = fac[0] * dfac[1] * fac[2];
-    dr[2] = fac[0] * fac[1] * dfac[2];
-}
-
 // SDF and its gradient at points x (n,3) in one pass (Eq. 16-17):
 //   f(x) = sum_i r(x, x_i) theta_d(x_i),  grad_x f(x) = sum_i grad_x r(x, x_i) theta_d(x_i).
 // Invalid points (a grid point unallocated) get valid = 0 and zeros.
@@ -529,11 +536,14 @@ double orc_eikonal(void* gp, const double* x, int64_t n, double lambda, double* 
 
 // Forward render of n rays (ray i uses hash id ray_id0 + i).  diag[i] = {S, n_valid, degenerate, T_N}.
 void orc_render(void* gp, const float* rays, int64_t n, int N, uint32_t seed, uint32_t ray_id0, int stratified,
-                const double* bg, double* rgb, double* depth, double* opac, double* sem, double* diag) {
+                const double* bg, double* rgb, double* depth, double* opac, double* sem, double* diag,
+                double* normal) {
     Grid* g = (Grid*)gp;
     for (int64_t i = 0; i < n; ++i) {
         RayResult R = render_ray(*g, rays + 8 * i, N, seed, ray_id0 + (uint32_t)i, stratified, bg);
         for (int c = 0; c < 3; ++c) rgb[i * 3 + c] = R.C[c];
+        if (normal)
+            for (int a = 0; a < 3; ++a) normal[i * 3 + a] = R.Nrm[a];
         depth[i] = R.D;
         opac[i] = R.O;
         if (sem)
@@ -560,17 +570,21 @@ int orc_trace(void* gp, const float* ray, int N, uint32_t seed, uint32_t ray_id,
     return (int)R.smp.size();
 }
 
-// Backward: accumulates dL/dtheta (+=) for L = sum_i g_rgb_i.C_i + g_depth_i D_i + g_opac_i O_i + g_sem_i.Sem_i,
+// Backward: accumulates dL/dtheta (+=) for
+//   L = sum_i g_rgb_i.C_i + g_depth_i D_i + g_opac_i O_i + g_sem_i.Sem_i (+ g_normal_i . N_i)
+// with N_i = sum_k w_k grad f(x_k) the rendered normal of Eq. 14 (its grad f part adds
+// w_k g_normal . grad_x r(x_k, x_e) to the SDF of each corner e),
 // and, if grad_beta is given, dL/dbeta per ray (grad_beta[i] = sum_k dL/dtau_k delta_k dsigma_k/dbeta, the
 // Laplace scale beta as a parameter as in VolSDF).
 // Derivation of Eq. 15 w.r.t. tau_k = sigma_k delta_k (T_k = exp(-sum_{j<k} tau_j)):
-//   dL/dtau_k = T_{k+1} v_k - sum_{j>k} w_j v_j - T_N (g_rgb . bg),   v_k = g_rgb.c_k + g_depth t_k + g_opac + g_sem.s_k
+//   dL/dtau_k = T_{k+1} v_k - sum_{j>k} w_j v_j - T_N (g_rgb . bg),
+//   v_k = g_rgb.c_k + g_depth t_k + g_opac + g_sem.s_k (+ g_normal . grad f(x_k))
 //   dL/dd_k   = delta_k sigma'(d_k) dL/dtau_k ;  dL/dc_k = w_k g_rgb ;  dL/ds_k = w_k g_sem
 // and the trilinear weights r_e scatter each onto the 8 grid points (Sec. 3.5.2).
 void orc_render_backward(void* gp, const float* rays, int64_t n, int N, uint32_t seed, uint32_t ray_id0,
                          int stratified, const double* bg, const double* g_rgb, const double* g_depth,
                          const double* g_opac, const double* g_sem, double* grad_sdf, double* grad_rgb,
-                         double* grad_sem, double* grad_beta) {
+                         double* grad_sem, double* grad_beta, const double* g_normal) {
     Grid* g = (Grid*)gp;
     const int ns = g->n_sem;
     for (int64_t i = 0; i < n; ++i) {
@@ -585,6 +599,8 @@ void orc_render_backward(void* gp, const float* rays, int64_t n, int N, uint32_t
             const Sample& s = R.smp[k];
             double vk = gd * s.t + go;
             for (int c = 0; c < 3; ++c) vk += gc[c] * s.c[c];
+            if (g_normal)
+                for (int a = 0; a < 3; ++a) vk += g_normal[3 * i + a] * s.gf[a];
             if (gs)
                 for (int c = 0; c < ns; ++c) vk += gs[c] * s.sem[c];
             v[k] = vk;
@@ -602,6 +618,12 @@ void orc_render_backward(void* gp, const float* rays, int64_t n, int N, uint32_t
                 int64_t li = s.st.lin[e];
                 double r = s.st.r[e];
                 grad_sdf[li] += r * dd;
+                if (g_normal) {
+                    double rr, dr[3];
+                    corner_weight_grad(s.st, g->vs, e, &rr, dr);
+                    const double* gn = g_normal + 3 * i;
+                    grad_sdf[li] += s.w * (gn[0] * dr[0] + gn[1] * dr[1] + gn[2] * dr[2]);
+                }
                 for (int c = 0; c < 3; ++c) grad_rgb[li * 3 + c] += r * s.w * gc[c];
                 if (gs)
                     for (int c = 0; c < ns; ++c) grad_sem[li * ns + c] += r * s.w * gs[c];
@@ -651,6 +673,19 @@ double orc_loss(int64_t n, int n_sem, const double* rgb, const double* depth, co
             L += lam_s * es * es / n;
             g_sem[i * n_sem + c] = 2.0 * lam_s * es / n;
         }
+    }
+    return L;
+}
+
+// Normal loss (Eq. 14), L1 per component like the colour loss: L = (lambda / (3n)) sum_i |N_i - N^_i|_1 between
+// the rendered normals N and the target normals N^ (both world frame, N unnormalised), with
+// dL/dN = lambda sign(N - N^) / (3n), sign(0) = 0.  Returns L.
+double orc_loss_normal(int64_t n, const double* N, const double* Nt, double lambda, double* g_normal) {
+    double L = 0.0;
+    for (int64_t i = 0; i < 3 * n; ++i) {
+        const double e = N[i] - Nt[i];
+        L += lambda * std::fabs(e) / (3.0 * n);
+        g_normal[i] = lambda * (double)((e > 0.0) - (e < 0.0)) / (3.0 * n);
     }
     return L;
 }

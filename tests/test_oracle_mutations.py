@@ -15,6 +15,7 @@ from tests import test_oracle_activation as A
 from tests import test_oracle_beta_ssi as Bs
 from tests import test_oracle_eikonal as Ek
 from tests import test_oracle_fusion as Fu
+from tests import test_oracle_normal as Nm
 from tests import test_oracle_render as R
 
 MUTANTS = [
@@ -71,6 +72,16 @@ MUTANTS = [
     ("ssi_no_shift", "b = (sd - a * st) / nn;", "b = 0.0;", [Bs.test_ssi_loss_zero_for_affine_targets_and_invariant]),
     ("ssi_grad_factor", "g_depth[i] = 2.0 * lambda * r / nn;", "g_depth[i] = lambda * r / nn;",
      [Bs.test_ssi_gradient_matches_central_differences]),
+    ("normal_drop_gradf_term", "grad_sdf[li] += s.w * (gn[0] * dr[0] + gn[1] * dr[1] + gn[2] * dr[2]);", "",
+     [Nm.test_normal_backward_matches_central_differences]),
+    ("normal_drop_weight_term", "for (int a = 0; a < 3; ++a) vk += g_normal[3 * i + a] * s.gf[a];", "",
+     [Nm.test_normal_backward_matches_central_differences]),
+    ("normal_swapped_axes", "for (int a = 0; a < 3; ++a) R.Nrm[a] += sm.w * sm.gf[a];",
+     "for (int a = 0; a < 3; ++a) R.Nrm[a] += sm.w * sm.gf[(a + 1) % 3];",
+     [Nm.test_linear_field_renders_opacity_times_normal]),
+    ("normal_loss_factor", "g_normal[i] = lambda * (double)((e > 0.0) - (e < 0.0)) / (3.0 * n);",
+     "g_normal[i] = lambda * (double)((e > 0.0) - (e < 0.0)) / n;",
+     [Nm.test_normal_loss_seeds_match_finite_differences]),
 ]
 
 
