@@ -281,6 +281,21 @@ int sdg_loss_l1(sdg_grid g, int64_t n, const float* rgb_dev, const float* depth_
                 const float* t_rgb_dev, const float* t_depth_dev, const float* t_sem_dev, const sdg_loss_opts* lo,
                 float* g_rgb_dev, float* g_depth_dev, float* g_sem_dev, float* loss_dev);
 
+/* The fused training pass with the normal loss of Eq. 14 added:
+ *   N_i = sum_k w_k grad f(x_k)  (the rendered normal; grad f in closed form,
+ *         Eq. 17, from the same 8 corner values as f; world frame, unnormalised)
+ *   loss_i += lambda_normal |N_i - N^_i|_1 / (3n),  dL/dN = lambda_normal sign(N - N^) / (3n)
+ * The normal seeds enter the backward twice: through the weights
+ * (v_k += g_N . grad f(x_k)) and through grad f itself (the SDF of each
+ * corner e gains w_k g_N . grad_x r(x_k, x_e)).  t_normal_dev [n][3] world-
+ * frame target normals (e.g. a monocular normal prior rotated to the world);
+ * the paper uses lambda_normal = 0.05.  Other arguments as
+ * sdg_train_step_rays; grids with logits and lo->learn_beta are not
+ * supported here (SDG_ERR_ARG). */
+int sdg_train_step_rays_normal(sdg_grid g, const float* rays_dev, int64_t n, const float* t_rgb_dev,
+                               const float* t_depth_dev, const float* t_normal_dev, const sdg_render_opts* opts,
+                               const sdg_loss_opts* lo, float lambda_normal, float* loss_dev, float* loss_sum_dev);
+
 /* Scale- and shift-invariant depth loss (Eq. 13 with the per-batch least
  * squares scale a and shift b of MiDaS): (a, b) = argmin sum_i (a t_i + b - D_i)^2
  * over the n rays (t = target depth, D = rendered depth), from FP64 sums in a

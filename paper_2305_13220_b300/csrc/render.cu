@@ -45,6 +45,16 @@ int launch_pass(sdg_grid g, const float* rays, uint32_t id0, const PassArgs& a) 
     return launch_q<MODE, true, true>(gd, rays, id0, a, Q, g->stream);
 }
 
+// Same for passes instantiated only for grids without logits.
+template <int MODE>
+int launch_pass_nosem(sdg_grid g, const float* rays, uint32_t id0, const PassArgs& a) {
+    if (a.n == 0) return SDG_OK;
+    const GridDev gd = g->dev();
+    const int Q = pick_q(a.N);
+    if (g->desc.rgb_dtype == SDG_BF16) return launch_q<MODE, true, false>(gd, rays, id0, a, Q, g->stream);
+    return launch_q<MODE, false, false>(gd, rays, id0, a, Q, g->stream);
+}
+
 int check_opts(const sdg_render_opts* o) {
     if (!o || o->n_samples < 1 || o->n_samples > 256 || (o->mode != SDG_MODE_RECOMPUTE && o->mode != SDG_MODE_STORE))
         return fail(SDG_ERR_ARG, "render opts: n_samples must be in [1, 256] and mode RECOMPUTE or STORE");
@@ -311,6 +321,48 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
         rc = launch_pass<PASS_TRAIN>(g, rays, o->ray_id0, a);
         if (rc) return rc;
     }
+    if (loss_sum) {
+        k_sum<<<1, 1024, 0, g->stream>>>(per_ray, n, loss_sum);
+        SDG_LAUNCH_CHECK("loss sum");
+    }
+    return SDG_OK;
+}
+
+extern "C" int sdg_train_step_rays_normal(sdg_grid g, const float* rays, int64_t n, const float* trgb,
+                                          const float* tdepth, const float* tnormal, const sdg_render_opts* o,
+                                          const sdg_loss_opts* lo, float lambda_normal, float* loss,
+                                          float* loss_sum) {
+    if (!g || !lo || n < 0 || (n > 0 && (!rays || !trgb || !tdepth || !tnormal)))
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: null argument");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (n > 0 && !aligned16(rays))
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: rays must be 16-byte aligned");
+    if (n > (int64_t)1 << 31) return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: at most 2^31 rays per call");
+    if (g->desc.n_sem) return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: grids with logits are not supported");
+    if (lo->learn_beta) return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: learn_beta is not supported");
+    if (lo->ray_order != SDG_ORDER_AUTO && lo->ray_order != SDG_ORDER_GIVEN && lo->ray_order != SDG_ORDER_SURFACE)
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: unknown ray_order");
+    if ((rc = use_device(g))) return rc;
+    if (n == 0) {
+        if (loss_sum) SDG_CUDA_TRY(cudaMemsetAsync(loss_sum, 0, sizeof(float), g->stream));
+        return SDG_OK;
+    }
+    float* per_ray = loss;
+    if (!per_ray && loss_sum && (rc = loss_scratch(g, n, &per_ray))) return rc;
+    PassArgs a = base_args(o, n);
+    a.t_rgb = trgb;
+    a.t_depth = tdepth;
+    a.t_normal = tnormal;
+    a.lam_d = lo->lambda_depth;
+    a.lam_n = lambda_normal;
+    a.inv_n = 1.0f / (float)n;
+    a.loss = per_ray;
+    if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
+        if ((rc = order_rays_by_surface(g, rays, tdepth, n, &a.perm))) return rc;
+    }
+    rc = launch_pass_nosem<PASS_TRAIN_NRM>(g, rays, o->ray_id0, a);
+    if (rc) return rc;
     if (loss_sum) {
         k_sum<<<1, 1024, 0, g->stream>>>(per_ray, n, loss_sum);
         SDG_LAUNCH_CHECK("loss sum");

@@ -39,7 +39,8 @@ enum PassMode {
     PASS_BWD = 2,
     PASS_BWD_STORE = 3,
     PASS_TRAIN = 4,
-    PASS_TRAIN_BETA = 5
+    PASS_TRAIN_BETA = 5,
+    PASS_TRAIN_NRM = 6  // PASS_TRAIN plus the normal loss of Eq. 14 on the rendered normal sum_k w_k grad f(x_k)
 };
 
 // Store-mode record channels per sample: t, sdf (NaN if invalid), r, g, b, block index (int bits).
@@ -60,6 +61,8 @@ struct PassArgs {
     float* loss;
     const int* perm;  // optional processing order: warp slot i runs ray perm[i] (NULL: ray i)
     float* beta_part;  // PASS_TRAIN_BETA: dL/dbeta of each ray [n]
+    const float* t_normal;  // PASS_TRAIN_NRM: target normals [n][3] (world frame)
+    float lam_n;
 };
 
 struct RayJob {
@@ -318,6 +321,31 @@ __device__ __forceinline__ void trilinear_weights(float fx, float fy, float fz, 
     w[4] = gx * gy * fz; w[5] = fx * gy * fz; w[6] = gx * fy * fz; w[7] = fx * fy * fz;
 }
 
+// grad f = sum_e grad_x r_e theta_e (Eq. 17): the derivative of a trilinear weight along an axis swaps that axis's
+// factor (f or 1 - f) for +-1/vs.
+__device__ __forceinline__ void sdf_gradient(float fx, float fy, float fz, float inv_vs, const float th[8], float& gx,
+                                             float& gy, float& gz) {
+    const float gxm = 1.f - fx, gym = 1.f - fy, gzm = 1.f - fz;
+    // differences along x at the four (y, z) corner pairs, and likewise for y and z
+    const float dx00 = th[1] - th[0], dx10 = th[3] - th[2], dx01 = th[5] - th[4], dx11 = th[7] - th[6];
+    const float dy00 = th[2] - th[0], dy10 = th[3] - th[1], dy01 = th[6] - th[4], dy11 = th[7] - th[5];
+    const float dz00 = th[4] - th[0], dz10 = th[5] - th[1], dz01 = th[6] - th[2], dz11 = th[7] - th[3];
+    gx = inv_vs * (gzm * (gym * dx00 + fy * dx10) + fz * (gym * dx01 + fy * dx11));
+    gy = inv_vs * (gzm * (gxm * dy00 + fx * dy10) + fz * (gxm * dy01 + fx * dy11));
+    gz = inv_vs * (gym * (gxm * dz00 + fx * dz10) + fy * (gxm * dz01 + fx * dz11));
+}
+
+// q . grad_x r_e for the 8 corners e (q already scaled by 1/vs): corner e = ex | ey << 1 | ez << 2.
+__device__ __forceinline__ void dot_weight_gradients(float fx, float fy, float fz, float qx, float qy, float qz,
+                                                     float out[8]) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const bool ex = e & 1, ey = (e >> 1) & 1, ez = (e >> 2) & 1;
+        const float ax = ex ? fx : 1.f - fx, ay = ey ? fy : 1.f - fy, az = ez ? fz : 1.f - fz;
+        out[e] = (ex ? qx : -qx) * ay * az + ax * (ey ? qy : -qy) * az + ax * ay * (ez ? qz : -qz);
+    }
+}
+
 __device__ __forceinline__ void sem_load4(const GridDev& g, int addr, int c0, float v[4]) {
     uint2 u = __ldg(reinterpret_cast<const uint2*>(g.sem + (int64_t)addr * g.n_sem + c0));
     v[0] = sdg_bf16_lo(u.x); v[1] = sdg_bf16_hi(u.x); v[2] = sdg_bf16_lo(u.y); v[3] = sdg_bf16_hi(u.y);
@@ -364,8 +392,9 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                                             int lane) {
     constexpr bool kStoreIn = MODE == PASS_BWD_STORE;
     constexpr bool kStoreOut = MODE == PASS_FWD_STORE;
-    constexpr bool kTrain = MODE == PASS_TRAIN || MODE == PASS_TRAIN_BETA;
+    constexpr bool kTrain = MODE == PASS_TRAIN || MODE == PASS_TRAIN_BETA || MODE == PASS_TRAIN_NRM;
     constexpr bool kBeta = MODE == PASS_TRAIN_BETA;
+    constexpr bool kNrm = MODE == PASS_TRAIN_NRM;
     constexpr bool kBwd = MODE == PASS_BWD || MODE == PASS_BWD_STORE || kTrain;
     constexpr bool kFwdOut = MODE == PASS_FWD || MODE == PASS_FWD_STORE;
     constexpr int SEMCAP = SEM ? 32 : 0;
@@ -403,12 +432,14 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     float t_[Q], dl_[Q], d_[Q], cr_[Q], cg_[Q], cb_[Q], tau_[Q], dsig_[Q], fx_[Q], fy_[Q], fz_[Q];
     int blk_[Q], lc_[Q];
     float bq_[kBeta ? Q : 1];
+    float gnx_[kNrm ? Q : 1], gny_[kNrm ? Q : 1], gnz_[kNrm ? Q : 1];  // grad f at the samples (Eq. 17)
     unsigned vmask = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int k = lane * Q + i;
         t_[i] = 0.f; dl_[i] = 0.f; d_[i] = 0.f; cr_[i] = cg_[i] = cb_[i] = 0.f; tau_[i] = 0.f; dsig_[i] = 0.f;
         if constexpr (kBeta) bq_[i] = 0.f;
+        if constexpr (kNrm) gnx_[i] = gny_[i] = gnz_[i] = 0.f;
         fx_[i] = fy_[i] = fz_[i] = 0.f; blk_[i] = -1; lc_[i] = 0;
         if (!any || k >= N) continue;
         float sn;
@@ -461,6 +492,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                     bb = fmaf(w[e], cbb[e], bb);
                 }
                 d_[i] = dd; cr_[i] = r; cg_[i] = gg; cb_[i] = bb;
+                if constexpr (kNrm) sdf_gradient(fx_[i], fy_[i], fz_[i], g.inv_vs, cs, gnx_[i], gny_[i], gnz_[i]);
             }
         }
         blk_[i] = blk;
@@ -580,6 +612,18 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 if (c < ns) sem_acc[c] = warp_sum(sem_acc[c]);
         }
     }
+    float Nx = 0.f, Ny = 0.f, Nz = 0.f;  // rendered normal sum_k w_k grad f(x_k) (Eq. 14)
+    if constexpr (kNrm) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            Nx = fmaf(w_[i], gnx_[i], Nx);
+            Ny = fmaf(w_[i], gny_[i], Ny);
+            Nz = fmaf(w_[i], gnz_[i], Nz);
+        }
+        Nx = warp_sum(Nx);
+        Ny = warp_sum(Ny);
+        Nz = warp_sum(Nz);
+    }
     if constexpr (kFwdOut) {
         if (lane == 0) {
             a.out_rgb[3 * j.idx] = C0;
@@ -600,6 +644,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 
     // ---------------- gradient seeds ----------------
     float gC0, gC1, gC2, gD, gO;
+    float gNx = 0.f, gNy = 0.f, gNz = 0.f;  // normal seeds (PASS_TRAIN_NRM)
     float gS[SEMCAP > 0 ? SEMCAP : 1];
     if constexpr (kTrain) {
         // L1 colour + lambda_d L1 depth (+ lambda_s squared L2 logits), mean over rays
@@ -610,6 +655,16 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         gD = a.lam_d * sgnf(ed) * a.inv_n;
         gO = 0.f;
         float L = (fabsf(e0) + fabsf(e1) + fabsf(e2)) * third + a.lam_d * fabsf(ed) * a.inv_n;
+        if constexpr (kNrm) {
+            // L1 normal loss (Eq. 14): lambda_n |N - N^|_1 / (3n)
+            const float nth = a.lam_n * third;
+            const float n0 = Nx - a.t_normal[3 * j.idx], n1 = Ny - a.t_normal[3 * j.idx + 1],
+                        n2 = Nz - a.t_normal[3 * j.idx + 2];
+            gNx = sgnf(n0) * nth;
+            gNy = sgnf(n1) * nth;
+            gNz = sgnf(n2) * nth;
+            L += (fabsf(n0) + fabsf(n1) + fabsf(n2)) * nth;
+        }
         if constexpr (SEM) {
 #pragma unroll
             for (int c = 0; c < SEMCAP; ++c) {
@@ -641,6 +696,10 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     float v_[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) v_[i] = fmaf(gC0, cr_[i], fmaf(gC1, cg_[i], fmaf(gC2, cb_[i], fmaf(gD, t_[i], gO))));
+    if constexpr (kNrm) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v_[i] = fmaf(gNx, gnx_[i], fmaf(gNy, gny_[i], fmaf(gNz, gnz_[i], v_[i])));
+    }
     bool sem_grad = false;
     if constexpr (SEM) {
         bool need = false;
@@ -721,6 +780,14 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 for (int e = 0; e < 8; ++e) {
                     aS[e] = fmaf(r[e], dd_[i], aS[e]);
                     aW[e] = fmaf(r[e], w_[i], aW[e]);
+                }
+                if constexpr (kNrm) {
+                    // the rendered normal's grad f part: w_i g_N . grad_x r_e(x_i) onto each corner's SDF
+                    const float sc = w_[i] * g.inv_vs;
+                    float q[8];
+                    dot_weight_gradients(fx_[i], fy_[i], fz_[i], sc * gNx, sc * gNy, sc * gNz, q);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) aS[e] += q[e];
                 }
             }
             if (run_end(i)) {

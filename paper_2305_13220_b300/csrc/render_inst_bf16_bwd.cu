@@ -5,3 +5,4 @@ SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD, true, false)
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD_STORE, true, false)
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN, true, false)
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_BETA, true, false)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_NRM, true, false)

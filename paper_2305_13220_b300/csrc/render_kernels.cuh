@@ -14,7 +14,7 @@ constexpr int render_min_blocks() {
 #ifdef SDG_RENDER_MIN_BLOCKS
     return SDG_RENDER_MIN_BLOCKS;
 #else
-    return SEM ? (Q >= 6 ? 1 : 2) : (Q >= 6 ? 2 : 3);
+    return SEM ? (Q >= 6 ? 1 : 2) : (MODE == PASS_TRAIN_NRM || Q >= 6 ? 2 : 3);
 #endif
 }
 

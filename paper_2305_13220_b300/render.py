@@ -72,6 +72,21 @@ def loss_l1(grid: Grid, rgb, depth, t_rgb, t_depth, sem=None, t_sem=None, lambda
     return loss, g
 
 
+def train_step_rays_normal(grid: Grid, rays: torch.Tensor, t_rgb: torch.Tensor, t_depth: torch.Tensor,
+                           t_normal: torch.Tensor, n_samples: int = 128, seed: int = 0, ray_id0: int = 0,
+                           stratified: bool = True, bg=(0.0, 0.0, 0.0), lambda_depth: float = 0.1,
+                           lambda_normal: float = 0.05, loss: Optional[torch.Tensor] = None,
+                           loss_sum: Optional[torch.Tensor] = None, ray_order: str = "auto"):
+    """Fused training pass with the L1 normal loss of Eq. 14 on the rendered normal sum_k w_k grad f(x_k)."""
+    o = render_opts(n_samples, seed, ray_id0, stratified, "recompute", bg)
+    orders = {"auto": A.ORDER_AUTO, "given": A.ORDER_GIVEN, "surface": A.ORDER_SURFACE}
+    lo = A.LossOpts(lambda_depth=lambda_depth, lambda_sem=0.0, ray_order=orders[ray_order], learn_beta=0)
+    A.call("sdg_train_step_rays_normal", grid.handle, _ptr(rays, torch.float32, "rays"), rays.shape[0],
+           _ptr(t_rgb, torch.float32, "t_rgb"), _ptr(t_depth, torch.float32, "t_depth"),
+           _ptr(t_normal, torch.float32, "t_normal"), C.byref(o), C.byref(lo), float(lambda_normal), _ptr(loss),
+           _ptr(loss_sum))
+
+
 def loss_depth_ssi(grid: Grid, depth, t_depth, lam: float = 0.1, want_ab: bool = False):
     """Scale/shift-invariant depth loss: per-ray terms, depth seeds dL/dD and, if want_ab, the fitted (a, b)."""
     n = depth.shape[0]
