@@ -92,6 +92,9 @@ def _declare(L):
         "orc_eikonal": (_d, [_p, _p, _i64, _d, _p, _p]),
         "orc_render": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p]),
         "orc_loss_normal": (_d, [_i64, _p, _p, _d, _p]),
+        "orc_lattice_simplex": (None, [_p, C.c_int, _p, _p]),
+        "orc_lattice_filter": (_i64, [_i64, C.c_int, _p, C.c_int, _p, _p, C.c_int]),
+        "orc_crf_meanfield": (None, [_i64, C.c_int, _p, C.c_int, _p, _p, _d, _p]),
         "orc_trace": (C.c_int, [_p, _p, C.c_int, _u32, _u32, C.c_int, _p]),
         "orc_render_backward": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p,
                                        _p, _p, _p]),
@@ -413,3 +416,38 @@ def loss_normal(normal, t_normal, lam: float = 0.05):
     g = np.empty_like(N)
     L = lib().orc_loss_normal(N.shape[0], N.ctypes.data, Nt.ctypes.data, float(lam), g.ctypes.data)
     return L, g
+
+
+def lattice_simplex(p):
+    """Enclosing simplex of one scaled feature p (d,) in the permutohedral lattice: vertices ((d+1), (d+1)) int64
+    and barycentric weights (d+1,)."""
+    p = _np(p, np.float64).reshape(-1)
+    d = p.shape[0]
+    vert = np.empty((d + 1, d + 1), np.int64)
+    bary = np.empty(d + 1)
+    lib().orc_lattice_simplex(p.ctypes.data, d, vert.ctypes.data, bary.ctypes.data)
+    return vert, bary
+
+
+def lattice_filter(pos, val, normalize: bool = False):
+    """Permutohedral-lattice Gaussian filter of val (n, c) at scaled features pos (n, d); returns (out, lattice
+    points)."""
+    pos = _np(pos, np.float64)
+    val = _np(val, np.float64)
+    n, d = pos.shape
+    c = val.shape[1]
+    out = np.empty((n, c))
+    M = lib().orc_lattice_filter(n, d, pos.ctypes.data, c, val.ctypes.data, out.ctypes.data, int(normalize))
+    return out, M
+
+
+def crf_meanfield(pos, unary, Q, w: float):
+    """One Potts mean-field update of label distributions Q (n, L) with unaries (n, L) and pairwise weight w."""
+    pos = _np(pos, np.float64)
+    unary = _np(unary, np.float64)
+    Q = _np(Q, np.float64)
+    n, d = pos.shape
+    L = Q.shape[1]
+    out = np.empty((n, L))
+    lib().orc_crf_meanfield(n, d, pos.ctypes.data, L, unary.ctypes.data, Q.ctypes.data, float(w), out.ctypes.data)
+    return out

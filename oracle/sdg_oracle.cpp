@@ -820,6 +820,162 @@ void orc_fuse(const int32_t* keys, int64_t N, float vs, int F, int H, int W, con
         }
 }
 
+// ------------------------ permutohedral lattice ------------------------------
+// Gaussian message passing of the continuous CRF (Sec. 3.5.3, Eq. 19-22) through the permutohedral lattice
+// (Adams, Baek and Davis, Eurographics 2010), written from its definition:
+//  * elevation: a d-dimensional (already scaled) feature p goes to x = s sum_i p_i u_i on the hyperplane
+//    H_d = {x in R^(d+1): sum x = 0}, u_i = (1, .., 1, -i, 0, .., 0) / sqrt(i (i + 1)) (i ones), an orthonormal
+//    basis of H_d, s = (d + 1) sqrt(2/3);
+//  * enclosing simplex: the nearest remainder-0 lattice point r (coordinates multiples of d + 1, sum 0) found by
+//    rounding each coordinate and then moving the coordinates with the most extreme residuals by d + 1 until the
+//    sum is 0; the residual x - r ranked in decreasing order gives the simplex vertices r + c_j, j = 0..d, with
+//    c_j = j on the coordinates of rank < d + 1 - j and j - (d + 1) on the others, and the barycentric weights;
+//  * splat: every point adds weight x value to its d + 1 vertices;
+//  * blur: along each of the d + 1 lattice directions o_k (d on coordinate k, -1 on the others), in order,
+//    v <- (v[- o_k] + 2 v + v[+ o_k]) / 4 over the splatted lattice points (absent neighbours are 0);
+//  * slice: every point reads the barycentric combination of its vertices.
+// The filter output is slice(blur(splat(v))); the normalised filter divides it by the same filter of ones.
+
+struct LatticeSimplex {
+    std::vector<std::vector<int64_t>> vert;  // d + 1 vertices, d + 1 coordinates each
+    std::vector<double> bary;                // d + 1 weights
+};
+
+LatticeSimplex lattice_simplex(const double* p, int d) {
+    const int d1 = d + 1;
+    std::vector<double> x(d1, 0.0);
+    const double sc = d1 * std::sqrt(2.0 / 3.0);
+    for (int i = 1; i <= d; ++i) {
+        const double f = sc * p[i - 1] / std::sqrt((double)i * (i + 1));
+        for (int k = 0; k < i; ++k) x[k] += f;
+        x[i] -= i * f;
+    }
+    std::vector<int64_t> r(d1);
+    int64_t sum = 0;
+    for (int k = 0; k < d1; ++k) {
+        const int64_t q = (int64_t)std::llround(x[k] / d1);
+        r[k] = q * d1;
+        sum += q;
+    }
+    std::vector<double> res(d1);
+    for (int k = 0; k < d1; ++k) res[k] = x[k] - (double)r[k];
+    std::vector<int> rank(d1, 0);
+    for (int k = 0; k < d1; ++k)
+        for (int m = 0; m < d1; ++m)
+            if (res[m] > res[k] || (res[m] == res[k] && m < k)) rank[k]++;
+    for (int k = 0; k < d1; ++k) {
+        rank[k] += (int)sum;
+        if (rank[k] >= d1) {
+            rank[k] -= d1;
+            r[k] -= d1;
+        } else if (rank[k] < 0) {
+            rank[k] += d1;
+            r[k] += d1;
+        }
+    }
+    std::vector<double> b(d1 + 1, 0.0);
+    for (int k = 0; k < d1; ++k) {
+        const double v = (x[k] - (double)r[k]) / d1;
+        b[d - rank[k]] += v;
+        b[d1 - rank[k]] -= v;
+    }
+    b[0] += 1.0 + b[d1];
+    LatticeSimplex S;
+    S.bary.assign(b.begin(), b.begin() + d1);
+    S.vert.assign(d1, std::vector<int64_t>(d1));
+    for (int j = 0; j < d1; ++j)
+        for (int k = 0; k < d1; ++k) S.vert[j][k] = r[k] + (rank[k] < d1 - j ? j : j - d1);
+    return S;
+}
+
+// The simplex of one feature: vert [(d+1) x (d+1)] and bary [d+1].
+void orc_lattice_simplex(const double* p, int d, int64_t* vert, double* bary) {
+    LatticeSimplex S = lattice_simplex(p, d);
+    for (int j = 0; j <= d; ++j) {
+        bary[j] = S.bary[j];
+        for (int k = 0; k <= d; ++k) vert[j * (d + 1) + k] = S.vert[j][k];
+    }
+}
+
+// out [n][c] = slice(blur(splat(val))) at features pos [n][d]; normalised by the filter of ones if normalize.
+// Returns the number of lattice points.
+int64_t orc_lattice_filter(int64_t n, int d, const double* pos, int c, const double* val, double* out,
+                           int normalize) {
+    const int d1 = d + 1;
+    const int cc = c + 1;  // channels + the homogeneous one
+    std::map<std::vector<int64_t>, int64_t> index;
+    std::vector<LatticeSimplex> simp(n);
+    std::vector<std::vector<int64_t>> vid(n, std::vector<int64_t>(d1));
+    std::vector<std::vector<int64_t>> keys;
+    for (int64_t i = 0; i < n; ++i) {
+        simp[i] = lattice_simplex(pos + (int64_t)d * i, d);
+        for (int j = 0; j < d1; ++j) {
+            auto it = index.find(simp[i].vert[j]);
+            if (it == index.end()) {
+                it = index.emplace(simp[i].vert[j], (int64_t)keys.size()).first;
+                keys.push_back(simp[i].vert[j]);
+            }
+            vid[i][j] = it->second;
+        }
+    }
+    const int64_t M = (int64_t)keys.size();
+    std::vector<double> v((size_t)M * cc, 0.0), w((size_t)M * cc, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < d1; ++j) {
+            const double b = simp[i].bary[j];
+            for (int q = 0; q < c; ++q) v[(size_t)vid[i][j] * cc + q] += b * val[(int64_t)c * i + q];
+            v[(size_t)vid[i][j] * cc + c] += b;
+        }
+    for (int dir = 0; dir < d1; ++dir) {
+        for (int64_t m = 0; m < M; ++m) {
+            std::vector<int64_t> kp = keys[m], km = keys[m];
+            for (int k = 0; k < d1; ++k) {
+                const int64_t o = k == dir ? d : -1;
+                kp[k] += o;
+                km[k] -= o;
+            }
+            auto ip = index.find(kp), im = index.find(km);
+            for (int q = 0; q < cc; ++q) {
+                double s2 = 2.0 * v[(size_t)m * cc + q];
+                if (ip != index.end()) s2 += v[(size_t)ip->second * cc + q];
+                if (im != index.end()) s2 += v[(size_t)im->second * cc + q];
+                w[(size_t)m * cc + q] = 0.25 * s2;
+            }
+        }
+        std::swap(v, w);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        std::vector<double> o(cc, 0.0);
+        for (int j = 0; j < d1; ++j)
+            for (int q = 0; q < cc; ++q) o[q] += simp[i].bary[j] * v[(size_t)vid[i][j] * cc + q];
+        for (int q = 0; q < c; ++q) out[(int64_t)c * i + q] = normalize ? o[q] / o[c] : o[q];
+    }
+    return M;
+}
+
+// One mean-field update of the label distribution with a Potts compatibility (Eq. 22; Krahenbuhl and Koltun
+// 2011): with F the lattice filter above (not normalised), Qt = F(Q) - Q (the message without the node itself),
+//   E_i(l) = U_i(l) + w (sum_l' Qt_i(l') - Qt_i(l)),   Q_i^+ = softmax(-E_i).
+void orc_crf_meanfield(int64_t n, int d, const double* pos, int L, const double* unary, const double* Q, double w,
+                       double* Qout) {
+    std::vector<double> FQ((size_t)n * L);
+    orc_lattice_filter(n, d, pos, L, Q, FQ.data(), 0);
+    for (int64_t i = 0; i < n; ++i) {
+        double tot = 0.0;
+        for (int l = 0; l < L; ++l) tot += FQ[(size_t)i * L + l] - Q[i * L + l];
+        std::vector<double> e(L);
+        double emin = 1e300;
+        for (int l = 0; l < L; ++l) {
+            const double qt = FQ[(size_t)i * L + l] - Q[i * L + l];
+            e[l] = unary[i * L + l] + w * (tot - qt);
+            emin = std::min(emin, e[l]);
+        }
+        double z = 0.0;
+        for (int l = 0; l < L; ++l) z += std::exp(-(e[l] - emin));
+        for (int l = 0; l < L; ++l) Qout[i * L + l] = std::exp(-(e[l] - emin)) / z;
+    }
+}
+
 // Pinhole rays of one H x W view (serve requests): o = t, d = normalize(R * ((u+0.5-cx)/fx, (v+0.5-cy)/fy, 1)).
 void orc_view_rays(int H, int W, const double* K, const double* T, float tnear, float tfar, float* rays) {
     for (int v = 0; v < H; ++v)

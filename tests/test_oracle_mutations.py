@@ -15,6 +15,7 @@ from tests import test_oracle_activation as A
 from tests import test_oracle_beta_ssi as Bs
 from tests import test_oracle_eikonal as Ek
 from tests import test_oracle_fusion as Fu
+from tests import test_oracle_lattice as La
 from tests import test_oracle_normal as Nm
 from tests import test_oracle_render as R
 
@@ -79,6 +80,16 @@ MUTANTS = [
     ("normal_swapped_axes", "for (int a = 0; a < 3; ++a) R.Nrm[a] += sm.w * sm.gf[a];",
      "for (int a = 0; a < 3; ++a) R.Nrm[a] += sm.w * sm.gf[(a + 1) % 3];",
      [Nm.test_linear_field_renders_opacity_times_normal]),
+    ("lattice_blur_weight", "w[(size_t)m * cc + q] = 0.25 * s2;", "w[(size_t)m * cc + q] = 0.5 * s2;",
+     [La.test_d1_filter_is_the_grid_filter]),
+    ("lattice_no_rank_shift", "        rank[k] += (int)sum;\n", "",
+     [lambda: La.test_simplex_is_the_enclosing_lattice_simplex(3)]),
+    ("lattice_bary_closure", "b[0] += 1.0 + b[d1];", "b[0] += 1.0;",
+     [lambda: La.test_simplex_is_the_enclosing_lattice_simplex(2)]),
+    ("lattice_neighbour_offset", "const int64_t o = k == dir ? d : -1;", "const int64_t o = k == dir ? d + 1 : -1;",
+     [La.test_d1_filter_is_the_grid_filter]),
+    ("meanfield_sign", "e[l] = unary[i * L + l] + w * (tot - qt);", "e[l] = unary[i * L + l] - w * (tot - qt);",
+     [La.test_meanfield_update]),
     ("normal_loss_factor", "g_normal[i] = lambda * (double)((e > 0.0) - (e < 0.0)) / (3.0 * n);",
      "g_normal[i] = lambda * (double)((e > 0.0) - (e < 0.0)) / n;",
      [Nm.test_normal_loss_seeds_match_finite_differences]),
