@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--views", type=int, default=N_VIEWS)
     p.add_argument("--max-blocks", type=int, default=80_000, help="grid capacity (room: 53,855 active blocks)")
     p.add_argument("--config", default="room", choices=["room", "room_bf16_sem", "serve", "apartment", "fusion",
-                                                              "query"],
+                                                              "query", "crf"],
                    help="room: the headline training step; the others are the precision, serving and apartment "
                         "workloads (one JSON line each)")
     p.add_argument("--requests", type=int, default=2000, help="serve: requests per arrival rate")
@@ -885,6 +885,49 @@ def run_query(args):
     print(json.dumps(line), flush=True)
 
 
+def run_crf(args):
+    """CRF message passing (Eq. 19-22) on the room: 2^18 surface samples of the 50 views (first hits), features
+    = position / 0.1 m, colour / 0.1, unit normal (d = 9); the permutohedral-lattice filter of 20 label
+    channels and one Potts mean-field update."""
+    import torch
+    import paper_2305_13220_b300 as sdg
+    import synth
+    device = "cuda:0"
+    sc = synth.scene_room(0)
+    poses = synth.random_poses(sc, args.views, seed=0)
+    K = synth.intrinsics(W, H)
+    n = 1 << 18
+    b = synth.training_batch(sc, poses, W, H, K, n, seed=5, device=device, n_sem=20)
+    x = b["rays"][:, :3].double() + b["depth"].double()[:, None] * b["rays"][:, 4:7].double()
+    eps = 1e-4
+    grad = torch.stack([(synth.scene_sdf(sc, x + eps * e) - synth.scene_sdf(sc, x - eps * e)) / (2 * eps)
+                        for e in torch.eye(3, dtype=torch.float64, device=device)], -1)
+    nrm = grad / grad.norm(dim=-1, keepdim=True).clamp_min(1e-12)
+    feat = torch.cat([x / 0.1, b["rgb"].double() / 0.1, nrm], 1).to(torch.float32).contiguous()
+    U = (-b["sem"]).contiguous()
+    Q = torch.softmax(-U, dim=1).contiguous()
+    G = sdg.Grid(VS, 16, beta=BETA)  # stream and scratch owner (the filter does not read the grid's voxels)
+    stats = {}
+
+    def filt(_b, _i):
+        stats["M"] = G.lattice_filter(feat, Q)[1]
+
+    def mf(_b, _i):
+        G.crf_meanfield(feat, U, Q, 1.0)
+
+    ms_f = _timed_steps(torch, filt, [None], args.steps, args.warmup)
+    ms_mf = _timed_steps(torch, mf, [None], args.steps, args.warmup)
+    line = _line(n / (ms_mf / 1e3), "points/s", args.steps, args.warmup, ms_mf,
+                 {"workload": "continuous-CRF mean-field update on 2^18 surface samples of the room (features: "
+                              "position/0.1 m, colour/0.1, normal; d = 9; 20 labels), permutohedral lattice",
+                  "points": n, "d": 9, "labels": 20},
+                 lattice={"points": int(stats["M"]), "filter_ms": round(ms_f, 4),
+                          "meanfield_ms": round(ms_mf, 4)},
+                 gpu_launches=(6 + 10) * args.steps,
+                 note="each call synchronises once: the lattice size sizes the blur launches")
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -899,6 +942,8 @@ def main():
         run_fusion(args)
     elif args.config == "query":
         run_query(args)
+    elif args.config == "crf":
+        run_crf(args)
     else:
         run_ours(args)
 

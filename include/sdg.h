@@ -431,6 +431,37 @@ int sdg_query(sdg_grid g, const float* xyz_dev, int64_t n, float* sdf_dev, float
  * blocks, or both, as the paper combines them.  Asynchronous. */
 int sdg_eikonal(sdg_grid g, const float* xyz_dev, int64_t n, float lambda, float* terms_dev, float* loss_sum_dev);
 
+/* ---------------------------------------------------------------------------
+ * Continuous CRF message passing (Sec. 3.5.3, Eq. 19-22): the Gaussian edge
+ * potential's sum over all sample points is evaluated with a permutohedral
+ * lattice (Adams, Baek and Davis 2010) on a hash map of lattice points.
+ *   elevation: x = (d+1) sqrt(2/3) sum_i p_i u_i on the hyperplane sum x = 0 of
+ *     R^(d+1), u_i = (1, .., 1, -i, 0, ..) / sqrt(i (i+1)), computed in FP64 in
+ *     a fixed order (the lattice point set is exactly that of an FP64 evaluation);
+ *   splat onto the d + 1 vertices of the enclosing simplex (barycentric weights);
+ *   blur along each of the d + 1 lattice directions with [1 2 1]/4 over the
+ *     splatted lattice points; slice back with the same weights.
+ * out = slice(blur(splat(val))), divided by the same filter of ones when
+ * normalize is set (a Gaussian-weighted mean of unit standard deviation in the
+ * scaled features, to a few per cent).
+ *   pos_dev [n][d] float features already divided by their standard deviations
+ *   (the paper concatenates positions, colours, normals and logits), 1 <= d <= 16;
+ *   val_dev [n][c], out_dev [n][c] float, 1 <= c <= 64.  n_lattice (host, may be
+ *   NULL) receives the number of lattice points.  Uses grid-owned scratch and the
+ *   grid's stream; synchronises once (the lattice size sizes the blur).
+ * SDG_ERR_ARG for non-finite or out-of-range features; a 64-bit fingerprint
+ * collision between distinct lattice points is detected and reported. */
+int sdg_lattice_filter(sdg_grid g, int64_t n, int32_t d, const float* pos_dev, int32_t c, const float* val_dev,
+                       float* out_dev, int32_t normalize, int64_t* n_lattice);
+
+/* One mean-field update of per-point label distributions with a Potts
+ * compatibility (Eq. 22, after Krahenbuhl and Koltun 2011): with F the
+ * (unnormalised) lattice filter above and Qt = F(Q) - Q,
+ *   E_i(l) = U_i(l) + w (sum_l' Qt_i(l') - Qt_i(l)),   Q_i^+ = softmax(-E_i).
+ * unary_dev, q_dev, q_out_dev [n][L] float, 1 <= L <= 64. */
+int sdg_crf_meanfield(sdg_grid g, int64_t n, int32_t d, const float* pos_dev, int32_t L, const float* unary_dev,
+                      const float* q_dev, float w, float* q_out_dev);
+
 /* Ends a fusion: for every voxel with a non-zero weight writes the BF16
  * colour (SDG_BF16 layout) and theta_s = s* / |s*| (grids with logits) into
  * the value channels, then zeroes the FP32 accumulators (colour and semantic

@@ -8,6 +8,22 @@
 
 #include "common.cuh"
 
+// Grid-owned scratch of the permutohedral lattice filter (lattice.cu), grown on demand.
+struct LatticeScratch {
+    unsigned long long* fp = nullptr;  // slot fingerprints
+    int* idx = nullptr;                // slot -> lattice index
+    int* skey = nullptr;               // slot -> coordinates
+    int* keys = nullptr;               // lattice index -> coordinates
+    int* vidx = nullptr;               // point -> vertex lattice indices
+    float* vbary = nullptr;            // point -> barycentric weights
+    float *val0 = nullptr, *val1 = nullptr;  // lattice values (double buffer)
+    int* nb = nullptr;                 // lattice neighbours per direction
+    int* counters = nullptr;           // lattice size, status
+    float* fq = nullptr;               // mean field: filtered label distributions
+    int64_t cap_fp = 0, cap_idx = 0, cap_skey = 0, cap_keys = 0, cap_vidx = 0, cap_vbary = 0, cap_val0 = 0,
+            cap_val1 = 0, cap_nb = 0, cap_counters = 0, cap_fq = 0;
+};
+
 struct sdg_grid_s {
     sdg_grid_desc desc;
     cudaStream_t stream = nullptr;
@@ -59,6 +75,7 @@ struct sdg_grid_s {
     double beta_m = 0.0, beta_v = 0.0;  // the scale's optimiser moments
     double ssi_ab[2] = {0.0, 0.0};
     double* ssi_dev = nullptr;  // device [2]: (a, b) of the last scale/shift-invariant depth loss
+    LatticeScratch lat;
 
     std::mutex mu;  // serialises host-side mutation (activation, load) of this grid
 

@@ -118,6 +118,22 @@ class Grid:
                _ptr(sem, torch.float32, "sem") if sem is not None else None,
                Kt.data_ptr(), Tt.data_ptr(), float(mu))
 
+    def lattice_filter(self, pos: torch.Tensor, val: torch.Tensor, normalize: bool = False):
+        """Permutohedral-lattice Gaussian filter (the CRF's message passing): val (n, c) at scaled features
+        pos (n, d); returns (out (n, c), number of lattice points).  Uses this grid's stream and scratch."""
+        out = torch.empty_like(val)
+        m = C.c_int64()
+        A.call("sdg_lattice_filter", self._h, pos.shape[0], pos.shape[1], _ptr(pos, torch.float32, "pos"),
+               val.shape[1], _ptr(val, torch.float32, "val"), _ptr(out), 1 if normalize else 0, C.byref(m))
+        return out, m.value
+
+    def crf_meanfield(self, pos: torch.Tensor, unary: torch.Tensor, q: torch.Tensor, w: float):
+        """One Potts mean-field update (Eq. 22) of label distributions q (n, L) with unaries (n, L)."""
+        out = torch.empty_like(q)
+        A.call("sdg_crf_meanfield", self._h, pos.shape[0], pos.shape[1], _ptr(pos, torch.float32, "pos"),
+               q.shape[1], _ptr(unary, torch.float32, "unary"), _ptr(q, torch.float32, "q"), float(w), _ptr(out))
+        return out
+
     def fuse_finalize(self):
         A.call("sdg_fuse_finalize", self._h)
 
