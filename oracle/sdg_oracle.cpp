@@ -826,7 +826,8 @@ void orc_fuse(const int32_t* keys, int64_t N, float vs, int F, int H, int W, con
 //  * elevation: a d-dimensional (already scaled) feature p goes to x = s sum_i p_i u_i on the hyperplane
 //    H_d = {x in R^(d+1): sum x = 0}, u_i = (1, .., 1, -i, 0, .., 0) / sqrt(i (i + 1)) (i ones), an orthonormal
 //    basis of H_d, s = (d + 1) sqrt(2/3);
-//  * enclosing simplex: the nearest remainder-0 lattice point r (coordinates multiples of d + 1, sum 0) found by
+//  * enclosing simplex (an integer decision, taken in FP32 in a fixed order like the activation's quantisation):
+//    the nearest remainder-0 lattice point r (coordinates multiples of d + 1, sum 0) found by
 //    rounding each coordinate and then moving the coordinates with the most extreme residuals by d + 1 until the
 //    sum is 0; the residual x - r ranked in decreasing order gives the simplex vertices r + c_j, j = 0..d, with
 //    c_j = j on the coordinates of rank < d + 1 - j and j - (d + 1) on the others, and the barycentric weights;
@@ -841,24 +842,26 @@ struct LatticeSimplex {
     std::vector<double> bary;                // d + 1 weights
 };
 
-LatticeSimplex lattice_simplex(const double* p, int d) {
+LatticeSimplex lattice_simplex(const double* pd, int d) {
+    // The simplex is an integer decision: it is taken in FP32 with this exact order (no fused multiply-add), so
+    // that any FP32 evaluation of the same order finds the same lattice points.
     const int d1 = d + 1;
-    std::vector<double> x(d1, 0.0);
-    const double sc = d1 * std::sqrt(2.0 / 3.0);
+    std::vector<float> x(d1, 0.0f);
+    const float sc = (float)d1 * std::sqrt(2.0f / 3.0f);
     for (int i = 1; i <= d; ++i) {
-        const double f = sc * p[i - 1] / std::sqrt((double)i * (i + 1));
+        const float f = (sc * (float)pd[i - 1]) / std::sqrt((float)(i * (i + 1)));
         for (int k = 0; k < i; ++k) x[k] += f;
-        x[i] -= i * f;
+        x[i] -= (float)i * f;
     }
     std::vector<int64_t> r(d1);
     int64_t sum = 0;
     for (int k = 0; k < d1; ++k) {
-        const int64_t q = (int64_t)std::llround(x[k] / d1);
+        const int64_t q = (int64_t)std::llround(x[k] / (float)d1);
         r[k] = q * d1;
         sum += q;
     }
-    std::vector<double> res(d1);
-    for (int k = 0; k < d1; ++k) res[k] = x[k] - (double)r[k];
+    std::vector<float> res(d1);
+    for (int k = 0; k < d1; ++k) res[k] = x[k] - (float)r[k];
     std::vector<int> rank(d1, 0);
     for (int k = 0; k < d1; ++k)
         for (int m = 0; m < d1; ++m)
@@ -873,15 +876,16 @@ LatticeSimplex lattice_simplex(const double* p, int d) {
             r[k] += d1;
         }
     }
-    std::vector<double> b(d1 + 1, 0.0);
+    std::vector<float> b(d1 + 1, 0.0f);
     for (int k = 0; k < d1; ++k) {
-        const double v = (x[k] - (double)r[k]) / d1;
+        const float v = (x[k] - (float)r[k]) / (float)d1;
         b[d - rank[k]] += v;
         b[d1 - rank[k]] -= v;
     }
-    b[0] += 1.0 + b[d1];
+    b[0] += 1.0f + b[d1];
     LatticeSimplex S;
-    S.bary.assign(b.begin(), b.begin() + d1);
+    S.bary.assign(d1, 0.0);
+    for (int j = 0; j < d1; ++j) S.bary[j] = (double)b[j];
     S.vert.assign(d1, std::vector<int64_t>(d1));
     for (int j = 0; j < d1; ++j)
         for (int k = 0; k < d1; ++k) S.vert[j][k] = r[k] + (rank[k] < d1 - j ? j : j - d1);

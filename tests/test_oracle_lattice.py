@@ -1,5 +1,8 @@
 """Pins of the oracle's permutohedral lattice filter and CRF mean-field update (Sec. 3.5.3, Eq. 19-22).
 
+The simplex search is an integer decision taken in FP32 (fixed order), so its geometry is checked to FP32
+rounding; planted mistakes are off by whole lattice units.
+
 The simplex search is checked against the lattice's definition (vertices are lattice points of remainder
 0..d, the barycentric weights are a convex combination reproducing the elevated point, and the remainder-0
 vertex is the nearest remainder-0 point); for d = 1 the whole filter equals a 1-D grid filter computed here by
@@ -40,14 +43,15 @@ def test_simplex_is_the_enclosing_lattice_simplex(d):
         assert np.all(V.sum(1) == 0)
         for j in range(d + 1):
             assert np.all(np.mod(V[j], d + 1) == j)  # vertex j is a remainder-j lattice point
-        assert abs(b.sum() - 1) < 1e-12 and b.min() > -1e-12
-        np.testing.assert_allclose(b @ V, x, atol=1e-9)
+        # the simplex is decided in FP32: weights and reconstruction to FP32 rounding of coordinates ~ 10-100
+        assert abs(b.sum() - 1) < 1e-5 and b.min() > -1e-5
+        np.testing.assert_allclose(b @ V, x, atol=1e-3)
         if d <= 3:  # the remainder-0 vertex is the nearest remainder-0 point
             r0 = V[0]
             best = np.linalg.norm(x - r0)
             for delta in itertools.product((-1, 0, 1), repeat=d + 1):
                 if sum(delta) == 0:
-                    assert np.linalg.norm(x - (r0 + (d + 1) * np.array(delta))) >= best - 1e-9
+                    assert np.linalg.norm(x - (r0 + (d + 1) * np.array(delta))) >= best - 1e-3
 
 
 def test_d1_filter_is_the_grid_filter():
@@ -74,7 +78,7 @@ def test_d1_filter_is_the_grid_filter():
         g = h / 4
     want = np.array([(1 - t[i]) * g[idx[lo[i]]] + t[i] * g[idx[lo[i] + 1]] for i in range(60)])
     assert M == len(pts)
-    np.testing.assert_allclose(out, want, atol=1e-12)
+    np.testing.assert_allclose(out, want, atol=1e-5)  # the oracle's weights are FP32 (its simplex decision)
 
 
 @pytest.mark.parametrize("d", [2, 5])
@@ -90,7 +94,7 @@ def test_filter_is_shift_invariant(d):
     w[0], w[1] = d + 1, -(d + 1)
     delta = basis(d).T @ w / ((d + 1) * np.sqrt(2.0 / 3.0))
     Fs, _ = oracle.lattice_filter(p + delta, a)
-    np.testing.assert_allclose(Fs, Fa, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(Fs, Fa, rtol=1e-4, atol=1e-6)  # FP32 weights: shifted coordinates round apart
 
 
 @pytest.mark.parametrize("d,tol", [(2, 0.03), (3, 0.04)])

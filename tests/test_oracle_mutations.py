@@ -84,7 +84,7 @@ MUTANTS = [
      [La.test_d1_filter_is_the_grid_filter]),
     ("lattice_no_rank_shift", "        rank[k] += (int)sum;\n", "",
      [lambda: La.test_simplex_is_the_enclosing_lattice_simplex(3)]),
-    ("lattice_bary_closure", "b[0] += 1.0 + b[d1];", "b[0] += 1.0;",
+    ("lattice_bary_closure", "b[0] += 1.0f + b[d1];", "b[0] += 1.0f;",
      [lambda: La.test_simplex_is_the_enclosing_lattice_simplex(2)]),
     ("lattice_neighbour_offset", "const int64_t o = k == dir ? d : -1;", "const int64_t o = k == dir ? d + 1 : -1;",
      [La.test_d1_filter_is_the_grid_filter]),
