@@ -334,7 +334,8 @@ void free_grid_buffers(sdg_grid g) {
                     g->m_sem, g->v_sem, g->weight, g->sort_buf, g->counters, g->minmax, g->loss_buf,
                     g->order_keys, g->order_perm, g->order_hist, g->fuse_cams, g->beta_grad, g->beta_part,
                     g->ssi_dev, g->lat.fp, g->lat.idx, g->lat.skey, g->lat.keys, g->lat.vidx, g->lat.vbary,
-                    g->lat.val0, g->lat.val1, g->lat.nb, g->lat.counters, g->lat.fq};
+                    g->lat.val0, g->lat.val1, g->lat.nb, g->lat.counters, g->lat.fq, g->lat.sr, g->lat.srank,
+                    g->lat.vslot, g->lat.fp2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->h_counters) cudaFreeHost(g->h_counters);

@@ -11,6 +11,7 @@
 // Grid-owned scratch of the permutohedral lattice filter (lattice.cu), grown on demand.
 struct LatticeScratch {
     unsigned long long* fp = nullptr;  // slot fingerprints
+    unsigned* fp2 = nullptr;           // second slot fingerprints
     int* idx = nullptr;                // slot -> lattice index
     int* skey = nullptr;               // slot -> coordinates
     int* keys = nullptr;               // lattice index -> coordinates
@@ -20,8 +21,12 @@ struct LatticeScratch {
     int* nb = nullptr;                 // lattice neighbours per direction
     int* counters = nullptr;           // lattice size, status
     float* fq = nullptr;               // mean field: filtered label distributions
+    int* sr = nullptr;                 // point -> remainder-0 vertex of its simplex
+    signed char* srank = nullptr;      // point -> ranks of its residual
+    int* vslot = nullptr;              // point -> table slots of its vertices
     int64_t cap_fp = 0, cap_idx = 0, cap_skey = 0, cap_keys = 0, cap_vidx = 0, cap_vbary = 0, cap_val0 = 0,
-            cap_val1 = 0, cap_nb = 0, cap_counters = 0, cap_fq = 0;
+            cap_val1 = 0, cap_nb = 0, cap_counters = 0, cap_fq = 0, cap_sr = 0, cap_srank = 0, cap_vslot = 0,
+            cap_fp2 = 0;
 };
 
 struct sdg_grid_s {
