@@ -17,7 +17,7 @@
  *    unless stated.  The caller owns every buffer it passes in and must keep
  *    it alive until the work enqueued on the grid's stream has finished.
  *  * The grid owns its hash table, voxel channels, gradients, optimiser
- *    state, neighbour table and occupancy bitmap.  sdg_grid_channel exposes
+ *    state, neighbour table and dense block-index grid.  sdg_grid_channel exposes
  *    channels zero-copy; those pointers stay valid until sdg_grid_destroy.
  *  * All work is enqueued on the stream given in sdg_grid_desc.  Calls are
  *    asynchronous, except those that return a count to the host
@@ -119,8 +119,9 @@ int sdg_grid_destroy(sdg_grid g);
  * xyz_dev: [n][3] float device points.  Points whose scaled coordinates are
  * non-finite or beyond 8e6 voxels are skipped.  0 <= dilate_voxels <= 64.
  * n_new (host, may be NULL): number of blocks added.  Synchronises.
- * All-or-nothing: on SDG_ERR_CAPACITY (more than max_blocks in total) the
- * grid is unchanged. */
+ * All-or-nothing: on SDG_ERR_CAPACITY (more than max_blocks in total, or a
+ * block bounding box of more than 2^31 blocks: the traversal keeps a 4-byte
+ * block index for every block cell of the box) the grid is unchanged. */
 int sdg_grid_activate_points(sdg_grid g, const float* xyz_dev, int64_t n, int32_t dilate_voxels, int64_t* n_new);
 
 /* Same as sdg_grid_activate_points on the points of a depth map, unprojected

@@ -120,7 +120,7 @@ __device__ __forceinline__ int sdg_table_insert(ulonglong2* t, uint32_t mask, ui
 struct GridDev {
     const ulonglong2* table;  // hash slots
     const int4* nbr;          // [N][2] int4: block index of +{0,x,y,xy,z,xz,yz,xyz} neighbours, -1 if absent
-    const uint32_t* bitmap;   // occupancy bits over the block AABB, x fastest
+    const int32_t* dense;     // block index of every cell of the block AABB (-1: not allocated), x fastest
     const int4* keys;         // [N] {x, y, z, 0}
     uint32_t mask;
     int32_t n_sem;

@@ -1,5 +1,5 @@
 // Grid life cycle, block activation (Sec. 3.4.1, Eq. 7-8), hash lookups, the
-// neighbour table and occupancy bitmap derived from the hash map, and
+// neighbour table and dense block-index grid derived from the hash map, and
 // checkpointing.  Paper: arXiv 2305.13220.
 #include <atomic>
 #include <cstdio>
@@ -262,12 +262,14 @@ __global__ void k_keys_to_list(const int4* __restrict__ keys, int64_t n, uint64_
     }
 }
 
-__global__ void k_bitmap(const int4* __restrict__ keys, int64_t n, int bx, int by, int bz, int dx, int dy,
-                         uint32_t* bitmap) {
+// Dense block-index grid over the block AABB: cell (x, y, z) holds the index of that block (-1 elsewhere), so
+// the traversal reads occupancy and block index with one load per cell.
+__global__ void k_dense(const int4* __restrict__ keys, int64_t n, int bx, int by, int bz, int dx, int dy,
+                        int32_t* dense) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int4 k = keys[i];
-        int64_t bit = ((int64_t)(k.z - bz) * dy + (k.y - by)) * (int64_t)dx + (k.x - bx);
-        atomicOr(bitmap + (bit >> 5), 1u << (bit & 31));
+        int64_t cell = ((int64_t)(k.z - bz) * dy + (k.y - by)) * (int64_t)dx + (k.x - bx);
+        dense[cell] = (int32_t)i;
     }
 }
 
@@ -329,7 +331,7 @@ int dalloc(T** p, size_t count, cudaStream_t s) {
 }
 
 void free_grid_buffers(sdg_grid g) {
-    void* ptrs[] = {g->table, g->tmp_table, g->keys, g->nbr, g->bitmap, g->geo, g->ggeo, g->m_geo, g->v_geo,
+    void* ptrs[] = {g->table, g->tmp_table, g->keys, g->nbr, g->dense, g->geo, g->ggeo, g->m_geo, g->v_geo,
                     g->sdf, g->gsdf, g->m_sdf, g->v_sdf, g->rgbh, g->grgb, g->m_rgb, g->v_rgb, g->sem, g->gsem,
                     g->m_sem, g->v_sem, g->weight, g->sort_buf, g->counters, g->minmax, g->loss_buf,
                     g->order_keys, g->order_perm, g->order_hist, g->fuse_cams, g->beta_grad, g->beta_part,
@@ -360,23 +362,23 @@ int sort_keys(sdg_grid g, int64_t n) {
     return SDG_OK;
 }
 
-// Makes the occupancy bitmap hold at least `words` words (the old contents are not kept).
-int reserve_bitmap(sdg_grid g, int64_t words) {
-    if (words <= g->bitmap_words_cap) return SDG_OK;
-    uint32_t* nb = nullptr;
-    SDG_CUDA_TRY(device_malloc((void**)&nb, words * sizeof(uint32_t)));
-    if (g->bitmap) cudaFree(g->bitmap);
-    g->bitmap = nb;
-    g->bitmap_words_cap = words;
+// Makes the dense block-index grid hold at least `cells` cells (the old contents are not kept).
+int reserve_dense(sdg_grid g, int64_t cells) {
+    if (cells <= g->dense_cap) return SDG_OK;
+    int32_t* nd = nullptr;
+    SDG_CUDA_TRY(device_malloc((void**)&nd, cells * sizeof(int32_t)));
+    if (g->dense) cudaFree(g->dense);
+    g->dense = nd;
+    g->dense_cap = cells;
     return SDG_OK;
 }
 
-// Recomputes the AABB (from all keys), the occupancy bitmap and the neighbour table.
+// Recomputes the AABB (from all keys), the dense block-index grid and the neighbour table.
 int rebuild_derived(sdg_grid g) {
     const int64_t N = g->n_blocks;
     if (N == 0) {
         for (int a = 0; a < 3; ++a) g->bmin[a] = g->bdim[a] = 0;
-        g->bitmap_words = 0;
+        g->dense_cells = 0;
         return SDG_OK;
     }
     int init[6] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, INT32_MIN};
@@ -387,26 +389,25 @@ int rebuild_derived(sdg_grid g) {
     SDG_LAUNCH_CHECK("minmax");
     SDG_CUDA_TRY(cudaMemcpyAsync(g->h_minmax, g->minmax, sizeof(init), cudaMemcpyDeviceToHost, g->stream));
     SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    int64_t bits = 1;
+    int64_t cells = 1;
     for (int a = 0; a < 3; ++a) {
         g->bmin[a] = g->h_minmax[a];
         g->bdim[a] = g->h_minmax[3 + a] - g->h_minmax[a] + 1;
-        bits *= g->bdim[a];
+        cells *= g->bdim[a];
     }
-    int64_t words = (bits + 31) / 32;
-    int rc = reserve_bitmap(g, words);
+    int rc = reserve_dense(g, cells);
     if (rc) return rc;
-    g->bitmap_words = words;
-    SDG_CUDA_TRY(cudaMemsetAsync(g->bitmap, 0, words * sizeof(uint32_t), g->stream));
-    k_bitmap<<<grid_blocks(N), kThreads, 0, g->stream>>>(g->keys, N, g->bmin[0], g->bmin[1], g->bmin[2], g->bdim[0],
-                                                          g->bdim[1], g->bitmap);
+    g->dense_cells = cells;
+    SDG_CUDA_TRY(cudaMemsetAsync(g->dense, 0xFF, cells * sizeof(int32_t), g->stream));
+    k_dense<<<grid_blocks(N), kThreads, 0, g->stream>>>(g->keys, N, g->bmin[0], g->bmin[1], g->bmin[2], g->bdim[0],
+                                                        g->bdim[1], g->dense);
     k_neighbours<<<grid_blocks(N), kThreads, 0, g->stream>>>(g->keys, N, g->table, g->mask, g->nbr);
-    SDG_LAUNCH_CHECK("bitmap/neighbours");
+    SDG_LAUNCH_CHECK("block index/neighbours");
     return SDG_OK;
 }
 
-// Largest block AABB the occupancy bitmap may cover (bits).
-constexpr int64_t kMaxBitmapBits = 1ll << 34;
+// Largest block AABB the dense block-index grid may cover (cells; 4 bytes each).
+constexpr int64_t kMaxDenseCells = 1ll << 31;
 
 // Second half of every activation: the candidate kernel has filled tmp_table and counters.
 int finish_activation(sdg_grid g, int64_t* n_new) {
@@ -439,7 +440,7 @@ int finish_activation(sdg_grid g, int64_t* n_new) {
     SDG_LAUNCH_CHECK("compact");
     int rc = sort_keys(g, (int64_t)cnt);
     if (rc) return rc;
-    // the AABB of old + new keys must stay within the bitmap limit (checked before any insertion)
+    // the AABB of old + new keys must stay within the block-index grid's limit (checked before any insertion)
     int init[6] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MIN, INT32_MIN, INT32_MIN};
     if (g->n_blocks > 0)
         for (int a = 0; a < 3; ++a) {
@@ -451,12 +452,12 @@ int finish_activation(sdg_grid g, int64_t* n_new) {
     k_minmax<<<grid_blocks(cnt), kThreads, 0, g->stream>>>(g->sort_buf, (int64_t)cnt, g->minmax);
     SDG_CUDA_TRY(cudaMemcpyAsync(g->h_minmax, g->minmax, sizeof(init), cudaMemcpyDeviceToHost, g->stream));
     SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    int64_t bits = 1;
-    for (int a = 0; a < 3; ++a) bits *= (int64_t)g->h_minmax[3 + a] - g->h_minmax[a] + 1;
-    if (bits > kMaxBitmapBits)
-        return fail(SDG_ERR_CAPACITY, "activation: block bounding box exceeds 2^34 blocks; grid unchanged");
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) cells *= (int64_t)g->h_minmax[3 + a] - g->h_minmax[a] + 1;
+    if (cells > kMaxDenseCells)
+        return fail(SDG_ERR_CAPACITY, "activation: block bounding box exceeds 2^31 blocks; grid unchanged");
     // every allocation happens before the first insertion, so a failure leaves the grid unchanged
-    rc = reserve_bitmap(g, (bits + 31) / 32);
+    rc = reserve_dense(g, cells);
     if (rc) return rc;
     k_insert<<<grid_blocks(cnt), kThreads, 0, g->stream>>>(g->sort_buf, (int64_t)cnt, g->n_blocks, g->table, g->mask,
                                                             g->keys, g->counters);

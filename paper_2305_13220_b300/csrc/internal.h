@@ -44,8 +44,8 @@ struct sdg_grid_s {
     ulonglong2* tmp_table = nullptr;
     int4* keys = nullptr;  // [max_blocks] {x, y, z, 0} in index order
     int4* nbr = nullptr;   // [max_blocks][2]
-    uint32_t* bitmap = nullptr;
-    int64_t bitmap_words = 0, bitmap_words_cap = 0;
+    int32_t* dense = nullptr;  // block index of every cell of the block AABB (-1: not allocated), x fastest
+    int64_t dense_cells = 0, dense_cap = 0;
     int bmin[3] = {0, 0, 0}, bdim[3] = {0, 0, 0};
 
     // channels
@@ -88,7 +88,7 @@ struct sdg_grid_s {
         GridDev d{};
         d.table = table;
         d.nbr = nbr;
-        d.bitmap = bitmap;
+        d.dense = dense;
         d.keys = keys;
         d.mask = mask;
         d.n_sem = desc.n_sem;

@@ -7,7 +7,7 @@
 // uniform across the warp:
 //  * traversal: the ray's clipped range [t0, t1] is cut into 32 equal pieces;
 //    lane j walks the block cells of piece j once (a block-level
-//    Amanatides-Woo walk against the occupancy bitmap) and records each
+//    Amanatides-Woo walk reading the dense block-index grid) and records each
 //    allocated cell it crosses -- t range, block index, block key -- in
 //    shared memory (up to kSegs per piece; a piece with more is re-walked
 //    exactly when one of its samples is placed).  A sequential shuffle prefix
@@ -129,12 +129,8 @@ __device__ __forceinline__ bool clip_to_grid(const GridDev& g, const float3& o, 
     return t0 < t1;
 }
 
-__device__ __forceinline__ bool occupied(const GridDev& g, int cx, int cy, int cz) {
-    int64_t bit = ((int64_t)cz * g.bdim[1] + cy) * (int64_t)g.bdim[0] + cx;
-    return (__ldg(g.bitmap + (bit >> 5)) >> (bit & 31)) & 1u;
-}
 
-// Calls f(a, b, key) for every allocated block cell the ray crosses inside
+// Calls f(a, b, key, blk) for every allocated block cell the ray crosses inside
 // [ta, tb), in order of increasing t, with [a, b) its stretch of the ray.
 template <class F>
 __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, const float3& d, const float3& invd,
@@ -158,8 +154,10 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
         float tz = sz ? ((float)(g.bmin[2] + cz + (sz > 0)) * g.L - o.z) * invd.z : INF;
         float te = fminf(tx, fminf(ty, tz));
         float b = fminf(te, tb);
-        if (b > tcur && occupied(g, cx, cy, cz))
-            f(tcur, b, sdg_pack_key(g.bmin[0] + cx, g.bmin[1] + cy, g.bmin[2] + cz));
+        if (b > tcur) {
+            const int blk = __ldg(g.dense + ((int64_t)cz * g.bdim[1] + cy) * (int64_t)g.bdim[0] + cx);
+            if (blk >= 0) f(tcur, b, sdg_pack_key(g.bmin[0] + cx, g.bmin[1] + cy, g.bmin[2] + cz), blk);
+        }
         if (!(te < tb)) break;
         if (tx == te) cx += sx;
         if (ty == te) cy += sy;
@@ -169,6 +167,13 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
             (unsigned)cz >= (unsigned)g.bdim[2])
             break;
     }
+}
+
+// Index of the block at block coordinates (bx, by, bz), -1 if it is not allocated (or outside the AABB).
+__device__ __forceinline__ int block_at(const GridDev& g, int bx, int by, int bz) {
+    const unsigned x = (unsigned)(bx - g.bmin[0]), y = (unsigned)(by - g.bmin[1]), z = (unsigned)(bz - g.bmin[2]);
+    if (x >= (unsigned)g.bdim[0] || y >= (unsigned)g.bdim[1] || z >= (unsigned)g.bdim[2]) return -1;
+    return __ldg(g.dense + ((int64_t)z * g.bdim[1] + y) * (int64_t)g.bdim[0] + x);
 }
 
 struct Pieces {
@@ -196,11 +201,11 @@ __device__ __forceinline__ float walk_pieces(const GridDev& g, const RayJob& j, 
         pc.t0 = t0;
         pc.dt = (t1 - t0) * (1.0f / 32.0f);
         const float ta = piece_start(pc, lane), tb = piece_end(pc, t1, lane);
-        walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, uint64_t key) {
+        walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, uint64_t key, int blk) {
             if (cnt < kSegs) {
                 sm.tin[cnt][lane] = x0;
                 sm.len[cnt][lane] = x1 - x0;
-                sm.blk[cnt][lane] = sdg_table_find(g.table, g.mask, key);
+                sm.blk[cnt][lane] = blk;
                 sm.key[cnt][lane] = key;
             }
             ++cnt;
@@ -249,11 +254,13 @@ __device__ __forceinline__ float locate(const GridDev& g, const RayJob& j, const
     float t = ta, best_a = ta, best_len = 0.f;
     uint64_t best_key = SDG_EMPTY_KEY;
     bool found = false;
-    walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, uint64_t k) {
+    int best_blk = -1;
+    walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, uint64_t k, int kb) {
         if (found) return;
         best_a = x0;
         best_len = x1 - x0;
         best_key = k;
+        best_blk = kb;
         if (local < best_len) {
             found = true;
             return;
@@ -262,7 +269,7 @@ __device__ __forceinline__ float locate(const GridDev& g, const RayJob& j, const
     });
     t = best_a + fminf(local, best_len);
     key = best_key;
-    blk = best_key == SDG_EMPTY_KEY ? -1 : sdg_table_find(g.table, g.mask, best_key);
+    blk = best_blk;
     return t;
 }
 
@@ -476,7 +483,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         } else {
             // the sample's own block: the traversal cell's, unless rounding put it across a block face
             const uint64_t own = sdg_pack_key(cx >> 3, cy >> 3, cz >> 3);
-            if (own != key) blk = sdg_table_find(g.table, g.mask, own);
+            if (own != key) blk = block_at(g, cx >> 3, cy >> 3, cz >> 3);
             int addr[8];
             valid = blk >= 0 && corner_addresses(g, blk, lc_[i], addr);
             if (valid) {

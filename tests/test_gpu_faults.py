@@ -39,7 +39,7 @@ def test_activation_allocation_failure_leaves_grid_usable(sdg):
     A = sdg._abi
     G = sdg.Grid(0.01, 5000)
     pts = torch.as_tensor(np.random.default_rng(0).uniform(0, 0.3, (500, 3)).astype(np.float32), device="cuda")
-    A.lib().sdg_debug_fail_alloc_after(0)  # the bitmap allocation of the first activation fails
+    A.lib().sdg_debug_fail_alloc_after(0)  # the block-index grid allocation of the first activation fails
     try:
         with pytest.raises(sdg.SdgError) as e:
             G.activate_points(pts, 2)
