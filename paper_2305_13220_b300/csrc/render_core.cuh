@@ -148,24 +148,26 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
     const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
     float tcur = ta;
     const int maxit = g.bdim[0] + g.bdim[1] + g.bdim[2] + 3;
+    // the next cell's block index is loaded before the current cell is handed to f, so the loads of successive
+    // cells overlap instead of each waiting for the previous one
+    int blk = __ldg(g.dense + ((int64_t)cz * g.bdim[1] + cy) * (int64_t)g.bdim[0] + cx);
     for (int it = 0; it < maxit; ++it) {
-        float tx = sx ? ((float)(g.bmin[0] + cx + (sx > 0)) * g.L - o.x) * invd.x : INF;
-        float ty = sy ? ((float)(g.bmin[1] + cy + (sy > 0)) * g.L - o.y) * invd.y : INF;
-        float tz = sz ? ((float)(g.bmin[2] + cz + (sz > 0)) * g.L - o.z) * invd.z : INF;
-        float te = fminf(tx, fminf(ty, tz));
-        float b = fminf(te, tb);
-        if (b > tcur) {
-            const int blk = __ldg(g.dense + ((int64_t)cz * g.bdim[1] + cy) * (int64_t)g.bdim[0] + cx);
-            if (blk >= 0) f(tcur, b, sdg_pack_key(g.bmin[0] + cx, g.bmin[1] + cy, g.bmin[2] + cz), blk);
-        }
-        if (!(te < tb)) break;
-        if (tx == te) cx += sx;
-        if (ty == te) cy += sy;
-        if (tz == te) cz += sz;
+        const float tx = sx ? ((float)(g.bmin[0] + cx + (sx > 0)) * g.L - o.x) * invd.x : INF;
+        const float ty = sy ? ((float)(g.bmin[1] + cy + (sy > 0)) * g.L - o.y) * invd.y : INF;
+        const float tz = sz ? ((float)(g.bmin[2] + cz + (sz > 0)) * g.L - o.z) * invd.z : INF;
+        const float te = fminf(tx, fminf(ty, tz));
+        const float b = fminf(te, tb);
+        const int nx = cx + (tx == te ? sx : 0), ny = cy + (ty == te ? sy : 0), nz = cz + (tz == te ? sz : 0);
+        const bool more = te < tb && (unsigned)nx < (unsigned)g.bdim[0] && (unsigned)ny < (unsigned)g.bdim[1] &&
+                          (unsigned)nz < (unsigned)g.bdim[2];
+        const int nblk = more ? __ldg(g.dense + ((int64_t)nz * g.bdim[1] + ny) * (int64_t)g.bdim[0] + nx) : -1;
+        if (b > tcur && blk >= 0) f(tcur, b, sdg_pack_key(g.bmin[0] + cx, g.bmin[1] + cy, g.bmin[2] + cz), blk);
+        if (!more) break;
+        cx = nx;
+        cy = ny;
+        cz = nz;
+        blk = nblk;
         tcur = fmaxf(te, ta);
-        if ((unsigned)cx >= (unsigned)g.bdim[0] || (unsigned)cy >= (unsigned)g.bdim[1] ||
-            (unsigned)cz >= (unsigned)g.bdim[2])
-            break;
     }
 }
 
