@@ -90,6 +90,7 @@ def _declare(L):
         "orc_query": (None, [_p, _p, _i64, _p, _p, _p]),
         "orc_query_grad": (None, [_p, _p, _i64, _p, _p, _p]),
         "orc_eikonal": (_d, [_p, _p, _i64, _d, _p, _p]),
+        "orc_crf_loss": (_d, [_p, C.c_int, _p, _i64, _p, _d, _p, _p]),
         "orc_render": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p]),
         "orc_loss_normal": (_d, [_i64, _p, _p, _d, _p]),
         "orc_lattice_simplex": (None, [_p, C.c_int, _p, _p]),
@@ -242,6 +243,21 @@ class Grid:
         g = np.zeros((self.n_blocks, 512))
         terms = np.empty(n)
         L = lib().orc_eikonal(self._h, x.ctypes.data, n, float(lam), g.ctypes.data, terms.ctypes.data)
+        return L, terms, g
+
+    def crf_loss(self, prop: str, x, target, lam: float):
+        """CRF loss of a property ("label", "color", "normal") at points x (n,3) against fixed targets; returns
+        (loss, per-point terms, dL/d(stored values): [N,512,n_sem], [N,512,3] or [N,512])."""
+        x = _np(x, np.float64).reshape(-1, 3)
+        n = x.shape[0]
+        pid = {"label": 0, "color": 1, "normal": 2}[prop]
+        ch = self.n_sem if pid == 0 else 3
+        t = _np(target, np.float64).reshape(n, ch)
+        shape = (self.n_blocks, 512) + ((ch,) if pid < 2 else ())
+        g = np.zeros(shape)
+        terms = np.empty(n)
+        L = lib().orc_crf_loss(self._h, pid, x.ctypes.data, n, t.ctypes.data, float(lam), g.ctypes.data,
+                               terms.ctypes.data)
         return L, terms, g
 
     def render(self, rays, n_samples: int, seed: int = 0, ray_id0: int = 0, stratified: bool = True, bg=(0, 0, 0)):

@@ -502,6 +502,75 @@ void orc_query_grad(void* gp, const double* x, int64_t n, double* sdf, double* g
     }
 }
 
+// CRF losses (Sec. 3.5.3, Eq. 22: "L_prop = D_f(x_prop || Q(x_prop))"), read as the divergence between each
+// property at surface points x_i and its CRF message-passed value, the latter a fixed target:
+//   prop 0 (labels):  (lambda/n) sum_i KL(Q_i || softmax(s(x_i))),  s the trilinear logits;
+//                     dL/ds_i = (lambda/n) (softmax(s_i) - Q_i)   (Q_i sums to one)
+//   prop 1 (colour):  (lambda/n) sum_i |c(x_i) - t_i|^2;           dL/dc_i = 2 (lambda/n) (c_i - t_i)
+//   prop 2 (normal):  (lambda/n) sum_i |grad f(x_i) - t_i|^2;      dL/dgrad f_i = 2 (lambda/n) (grad f_i - t_i)
+// each scattered onto the stored values through the trilinear weights (through their x-gradients for the
+// normal).  Invalid points contribute 0.  Gradients are ADDED to g [N][512][channels]; returns L.
+double orc_crf_loss(void* gp, int prop, const double* x, int64_t n, const double* target, double lambda,
+                    double* g_out, double* terms) {
+    Grid* g = (Grid*)gp;
+    const int ns = g->n_sem;
+    const int ch = prop == 0 ? ns : 3;
+    double L = 0.0;
+    const double k = lambda / (double)n;
+    for (int64_t i = 0; i < n; ++i) {
+        Stencil st = stencil_at(*g, x + 3 * i);
+        double term = 0.0;
+        if (st.valid) {
+            const double* t = target + (int64_t)ch * i;
+            std::vector<double> gp_(ch, 0.0);  // dL/d(property at x_i)
+            if (prop == 0) {
+                std::vector<double> s(ns, 0.0);
+                for (int e = 0; e < 8; ++e)
+                    for (int c = 0; c < ns; ++c) s[c] += st.r[e] * g->sem[st.lin[e] * ns + c];
+                double mx = -1e300;
+                for (int c = 0; c < ns; ++c) mx = std::max(mx, s[c]);
+                double z = 0.0;
+                for (int c = 0; c < ns; ++c) z += std::exp(s[c] - mx);
+                for (int c = 0; c < ns; ++c) {
+                    const double logp = s[c] - mx - std::log(z);
+                    if (t[c] > 0.0) term += k * t[c] * (std::log(t[c]) - logp);
+                    gp_[c] = k * (std::exp(logp) - t[c]);
+                }
+            } else if (prop == 1) {
+                for (int c = 0; c < 3; ++c) {
+                    double v = 0.0;
+                    for (int e = 0; e < 8; ++e) v += st.r[e] * g->rgb[st.lin[e] * 3 + c];
+                    term += k * (v - t[c]) * (v - t[c]);
+                    gp_[c] = 2.0 * k * (v - t[c]);
+                }
+            } else {
+                double gf[3] = {0.0, 0.0, 0.0};
+                for (int e = 0; e < 8; ++e) {
+                    double r, dr[3];
+                    corner_weight_grad(st, g->vs, e, &r, dr);
+                    for (int a = 0; a < 3; ++a) gf[a] += dr[a] * g->sdf[st.lin[e]];
+                }
+                for (int a = 0; a < 3; ++a) {
+                    term += k * (gf[a] - t[a]) * (gf[a] - t[a]);
+                    gp_[a] = 2.0 * k * (gf[a] - t[a]);
+                }
+            }
+            for (int e = 0; e < 8; ++e) {
+                if (prop == 2) {
+                    double r, dr[3];
+                    corner_weight_grad(st, g->vs, e, &r, dr);
+                    g_out[st.lin[e]] += gp_[0] * dr[0] + gp_[1] * dr[1] + gp_[2] * dr[2];
+                } else {
+                    for (int c = 0; c < ch; ++c) g_out[st.lin[e] * ch + c] += st.r[e] * gp_[c];
+                }
+            }
+        }
+        if (terms) terms[i] = term;
+        L += term;
+    }
+    return L;
+}
+
 // Eikonal regularisation (Sec. 3.5.3): L = (lambda / n) * sum over the n points of (|grad f(x)| - 1)^2, invalid
 // points contributing 0.  Its gradient with respect to the stored SDF values,
 //   dL/dtheta_d(x_i) = (lambda / n) * 2 (|grad f| - 1) * (grad f / |grad f|) . grad_x r(x, x_i),

@@ -94,6 +94,21 @@ def test_capacity_error_leaves_grid_unchanged(sdg):
     assert G.num_blocks == n0 + 1
 
 
+def test_block_bounding_box_limit_leaves_grid_unchanged(sdg):
+    """The traversal keeps a 4-byte block index for every cell of the block AABB; a batch that would stretch the
+    AABB beyond 2^31 cells is refused before anything is inserted."""
+    G = sdg.Grid(0.01, 64)
+    k0 = torch.tensor([[0, 0, 0], [1, 0, 0]], dtype=torch.int32, device="cuda")
+    assert G.activate_keys(k0) == 2
+    far = torch.tensor([[(1 << 20) - 1, (1 << 20) - 1, 0], [2, 0, 0]], dtype=torch.int32, device="cuda")
+    with pytest.raises(sdg.SdgError) as e:
+        G.activate_keys(far)  # AABB 2^20 x 2^20 x 1 cells
+    assert e.value.code == sdg._abi.ERR_CAPACITY
+    assert G.num_blocks == 2
+    np.testing.assert_array_equal(G.lookup(k0).cpu().numpy(), [0, 1])
+    assert G.activate_keys(torch.tensor([[2, 0, 0]], dtype=torch.int32, device="cuda")) == 1  # still usable
+
+
 def test_activate_keys_duplicates_and_present(sdg):
     G = sdg.Grid(0.01, 64)
     k = torch.tensor([[0, 0, 0], [1, 0, 0], [0, 0, 0], [-3, 2, 1]], dtype=torch.int32, device="cuda")

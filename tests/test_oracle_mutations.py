@@ -13,6 +13,7 @@ import pytest
 import oracle
 from tests import test_oracle_activation as A
 from tests import test_oracle_beta_ssi as Bs
+from tests import test_oracle_crf_loss as Cl
 from tests import test_oracle_eikonal as Ek
 from tests import test_oracle_fusion as Fu
 from tests import test_oracle_lattice as La
@@ -80,6 +81,13 @@ MUTANTS = [
     ("normal_swapped_axes", "for (int a = 0; a < 3; ++a) R.Nrm[a] += sm.w * sm.gf[a];",
      "for (int a = 0; a < 3; ++a) R.Nrm[a] += sm.w * sm.gf[(a + 1) % 3];",
      [Nm.test_linear_field_renders_opacity_times_normal]),
+    ("crf_label_grad_sign", "gp_[c] = k * (std::exp(logp) - t[c]);", "gp_[c] = k * (t[c] - std::exp(logp));",
+     [lambda: Cl.test_crf_loss_zero_at_target_and_matches_central_differences("label")]),
+    ("crf_color_factor", "gp_[c] = 2.0 * k * (v - t[c]);", "gp_[c] = k * (v - t[c]);",
+     [lambda: Cl.test_crf_loss_zero_at_target_and_matches_central_differences("color")]),
+    ("crf_normal_axes", "g_out[st.lin[e]] += gp_[0] * dr[0] + gp_[1] * dr[1] + gp_[2] * dr[2];",
+     "g_out[st.lin[e]] += gp_[0] * dr[0] + gp_[1] * dr[2] + gp_[2] * dr[1];",
+     [lambda: Cl.test_crf_loss_zero_at_target_and_matches_central_differences("normal")]),
     ("lattice_blur_weight", "w[(size_t)m * cc + q] = 0.25 * s2;", "w[(size_t)m * cc + q] = 0.5 * s2;",
      [La.test_d1_filter_is_the_grid_filter]),
     ("lattice_no_rank_shift", "        rank[k] += (int)sum;\n", "",
