@@ -455,6 +455,24 @@ int sdg_eikonal(sdg_grid g, const float* xyz_dev, int64_t n, float lambda, float
 int sdg_lattice_filter(sdg_grid g, int64_t n, int32_t d, const float* pos_dev, int32_t c, const float* val_dev,
                        float* out_dev, int32_t normalize, int64_t* n_lattice);
 
+/* CRF losses (Sec. 3.5.3, Eq. 22 reads "L_prop = D_f(x_prop || Q(x_prop))"):
+ * the divergence between a property at surface points and its CRF
+ * message-passed value, the latter a fixed target (e.g. from
+ * sdg_crf_meanfield for labels, or a normalised sdg_lattice_filter of the
+ * colours / normals):
+ *   prop 0, labels: (lambda/n) sum_i KL(Q_i || softmax(s(x_i))), s the
+ *     trilinear logits; dL/ds_i = (lambda/n)(softmax(s_i) - Q_i);
+ *     target [n][n_sem] distributions (SDG_ERR_ARG without logits);
+ *   prop 1, colour: (lambda/n) sum_i |c(x_i) - t_i|^2, target [n][3];
+ *   prop 2, normal: (lambda/n) sum_i |grad f(x_i) - t_i|^2, target [n][3]
+ *     (grad f of Eq. 17).
+ * The gradients are ADDED to the matching gradient channel through the
+ * trilinear weights (their x-gradients for the normal); points whose 8 grid
+ * points are not all allocated contribute 0.  terms_dev [n] (may be NULL),
+ * loss_sum_dev [1] (may be NULL; deterministic).  Asynchronous. */
+int sdg_crf_loss(sdg_grid g, int32_t prop, int64_t n, const float* xyz_dev, const float* target_dev, float lambda,
+                 float* terms_dev, float* loss_sum_dev);
+
 /* One mean-field update of per-point label distributions with a Potts
  * compatibility (Eq. 22, after Krahenbuhl and Koltun 2011): with F the
  * (unnormalised) lattice filter above and Qt = F(Q) - Q,

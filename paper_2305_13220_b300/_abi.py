@@ -103,6 +103,7 @@ SIGNATURES = {
     "sdg_train_step_rays_normal": [_p, _p, _i64, _p, _p, _p, _P(RenderOpts), _P(LossOpts), C.c_float, _p, _p],
     "sdg_lattice_filter": [_p, _i64, C.c_int32, _p, C.c_int32, _p, _p, C.c_int32, _p],
     "sdg_crf_meanfield": [_p, _i64, C.c_int32, _p, C.c_int32, _p, _p, C.c_float, _p],
+    "sdg_crf_loss": [_p, C.c_int32, _i64, _p, _p, C.c_float, _p, _p],
     "sdg_fuse_frames": [_p, _i64, C.c_int32, C.c_int32, _p, _p, _p, _p, _p, C.c_float],
     "sdg_fuse_finalize": [_p],
     "sdg_train_step_rays": [_p, _p, _i64, _p, _p, _p, _P(RenderOpts), _P(LossOpts), _p, _p],

@@ -127,6 +127,118 @@ __global__ void __launch_bounds__(kThreads) k_eikonal(GridDev g, const float* __
     }
 }
 
+// CRF losses (Sec. 3.5.3, Eq. 22): the divergence between a property at surface points and its fixed CRF target.
+//   PROP 0, labels: (lambda/n) KL(Q || softmax(s)), dL/ds = (lambda/n)(softmax(s) - Q), s the trilinear logits;
+//   PROP 1, colour: (lambda/n) |c - t|^2;  PROP 2, normal: (lambda/n) |grad f - t|^2.
+// Gradients go through the trilinear weights (their x-gradients for the normal) into the gradient channels.
+template <bool BF16, int PROP>
+__global__ void __launch_bounds__(kThreads) k_crf_loss(GridDev g, const float* __restrict__ xyz, int64_t n,
+                                                       const float* __restrict__ target, float k,
+                                                       float* __restrict__ terms) {
+    const int ns = g.n_sem;
+    const int ch = PROP == 0 ? ns : 3;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const PointStencil s =
+            point_stencil(g, __ldg(xyz + 3 * i), __ldg(xyz + 3 * i + 1), __ldg(xyz + 3 * i + 2));
+        float term = 0.f;
+        if (s.valid) {
+            const float* t = target + (int64_t)ch * i;
+            float r[8];
+            trilinear_weights(s.f[0], s.f[1], s.f[2], r);
+            if constexpr (PROP == 0) {
+                float lg[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) lg[c] = 0.f;
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+#pragma unroll
+                    for (int c4 = 0; c4 < 8; ++c4)
+                        if (4 * c4 < ns) {
+                            float v[4];
+                            sem_load4(g, s.addr[e], 4 * c4, v);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) lg[4 * c4 + q] = fmaf(r[e], v[q], lg[4 * c4 + q]);
+                        }
+                float mx = -3.0e38f;
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c < ns) mx = fmaxf(mx, lg[c]);
+                float z = 0.f;
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c < ns) z += __expf(lg[c] - mx);
+                const float lz = __logf(z);
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c < ns) {
+                        const float logp = lg[c] - mx - lz;
+                        const float tc = __ldg(t + c);
+                        if (tc > 0.f) term += k * tc * (__logf(tc) - logp);
+                        lg[c] = k * (__expf(logp) - tc);  // now dL/ds_c
+                    }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    float* gs = g.gsem + (int64_t)s.addr[e] * ns;
+#pragma unroll
+                    for (int c4 = 0; c4 < 8; ++c4)
+                        if (4 * c4 < ns)
+                            red_add_v4(reinterpret_cast<float4*>(gs) + c4, r[e] * lg[4 * c4], r[e] * lg[4 * c4 + 1],
+                                       r[e] * lg[4 * c4 + 2], r[e] * lg[4 * c4 + 3]);
+                }
+            } else if constexpr (PROP == 1) {
+                float cv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    float c0, c1, c2;
+                    if constexpr (BF16) {
+                        const uint2 u = __ldg(g.rgbh + s.addr[e]);
+                        c0 = sdg_bf16_lo(u.x);
+                        c1 = sdg_bf16_hi(u.x);
+                        c2 = sdg_bf16_lo(u.y);
+                    } else {
+                        const float4 v = __ldg(g.geo + s.addr[e]);
+                        c0 = v.y;
+                        c1 = v.z;
+                        c2 = v.w;
+                    }
+                    cv[0] = fmaf(r[e], c0, cv[0]);
+                    cv[1] = fmaf(r[e], c1, cv[1]);
+                    cv[2] = fmaf(r[e], c2, cv[2]);
+                }
+                float gp[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float dlt = cv[c] - __ldg(t + c);
+                    term += k * dlt * dlt;
+                    gp[c] = 2.f * k * dlt;
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    if constexpr (BF16) red_add_v4(g.grgb + s.addr[e], r[e] * gp[0], r[e] * gp[1], r[e] * gp[2], 0.f);
+                    else red_add_v4(g.ggeo + s.addr[e], 0.f, r[e] * gp[0], r[e] * gp[1], r[e] * gp[2]);
+                }
+            } else {
+                float f, gr[3], dr[8][3];
+                sdf_and_grad<BF16>(g, s, f, gr, dr);
+                float gp[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float dlt = gr[a] - __ldg(t + a);
+                    term += k * dlt * dlt;
+                    gp[a] = 2.f * k * dlt;
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float v = gp[0] * dr[e][0] + gp[1] * dr[e][1] + gp[2] * dr[e][2];
+                    if constexpr (BF16) atomicAdd(g.gsdf + s.addr[e], v);
+                    else atomicAdd(&g.ggeo[s.addr[e]].x, v);
+                }
+            }
+        }
+        terms[i] = term;
+    }
+}
+
 int grid_blocks(int64_t n) { return (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 148 * 32); }
 
 bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
@@ -173,6 +285,43 @@ extern "C" int sdg_eikonal(sdg_grid g, const float* xyz, int64_t n, float lambda
     if (loss_sum) {
         k_sum<<<1, 1024, 0, g->stream>>>(per_point, n, loss_sum);
         SDG_LAUNCH_CHECK("eikonal loss sum");
+    }
+    return SDG_OK;
+}
+
+extern "C" int sdg_crf_loss(sdg_grid g, int32_t prop, int64_t n, const float* xyz, const float* target, float lambda,
+                            float* terms, float* loss_sum) {
+    if (!g || n < 0 || prop < 0 || prop > 2 || (n > 0 && (!xyz || !target)))
+        return fail(SDG_ERR_ARG, "sdg_crf_loss: bad argument (prop 0 labels, 1 colour, 2 normal)");
+    if (prop == 0 && g->desc.n_sem == 0) return fail(SDG_ERR_ARG, "sdg_crf_loss: the grid has no logits");
+    if (n > 0 && (!aligned4(xyz) || !aligned4(target))) return fail(SDG_ERR_ARG, "sdg_crf_loss: misaligned arrays");
+    int rc = use_device(g);
+    if (rc) return rc;
+    if (n == 0) {
+        if (loss_sum) SDG_CUDA_TRY(cudaMemsetAsync(loss_sum, 0, sizeof(float), g->stream));
+        return SDG_OK;
+    }
+    float* per_point = terms;
+    if (!per_point && (rc = loss_scratch(g, n, &per_point))) return rc;
+    const GridDev gd = g->dev();
+    const float k = lambda / (float)n;
+    const bool bf16 = g->desc.rgb_dtype == SDG_BF16;
+    const int nb = grid_blocks(n);
+    cudaStream_t st = g->stream;
+    if (prop == 0) {
+        if (bf16) k_crf_loss<true, 0><<<nb, kThreads, 0, st>>>(gd, xyz, n, target, k, per_point);
+        else k_crf_loss<false, 0><<<nb, kThreads, 0, st>>>(gd, xyz, n, target, k, per_point);
+    } else if (prop == 1) {
+        if (bf16) k_crf_loss<true, 1><<<nb, kThreads, 0, st>>>(gd, xyz, n, target, k, per_point);
+        else k_crf_loss<false, 1><<<nb, kThreads, 0, st>>>(gd, xyz, n, target, k, per_point);
+    } else {
+        if (bf16) k_crf_loss<true, 2><<<nb, kThreads, 0, st>>>(gd, xyz, n, target, k, per_point);
+        else k_crf_loss<false, 2><<<nb, kThreads, 0, st>>>(gd, xyz, n, target, k, per_point);
+    }
+    SDG_LAUNCH_CHECK("crf loss");
+    if (loss_sum) {
+        k_sum<<<1, 1024, 0, st>>>(per_point, n, loss_sum);
+        SDG_LAUNCH_CHECK("crf loss sum");
     }
     return SDG_OK;
 }

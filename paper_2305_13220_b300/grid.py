@@ -134,6 +134,14 @@ class Grid:
                q.shape[1], _ptr(unary, torch.float32, "unary"), _ptr(q, torch.float32, "q"), float(w), _ptr(out))
         return out
 
+    def crf_loss(self, prop: str, xyz: torch.Tensor, target: torch.Tensor, lam: float,
+                 terms: Optional[torch.Tensor] = None, loss_sum: Optional[torch.Tensor] = None):
+        """CRF loss of a property ("label", "color", "normal") at points xyz (n, 3) against fixed targets; the
+        gradient is ADDED into the property's gradient channel."""
+        pid = {"label": 0, "color": 1, "normal": 2}[prop]
+        A.call("sdg_crf_loss", self._h, pid, xyz.shape[0], _ptr(xyz, torch.float32, "xyz"),
+               _ptr(target, torch.float32, "target"), float(lam), _ptr(terms), _ptr(loss_sum))
+
     def fuse_finalize(self):
         A.call("sdg_fuse_finalize", self._h)
 
