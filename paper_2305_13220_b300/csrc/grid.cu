@@ -168,7 +168,8 @@ __global__ void k_compact(ulonglong2* tmp, uint32_t cap, uint64_t* out, unsigned
 }
 
 __global__ void k_fill_u64(uint64_t* a, int64_t from, int64_t to, uint64_t v) {
-    for (int64_t i = from + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < to; i += (int64_t)gridDim.x * blockDim.x)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = from + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < to; i += stride)
         a[i] = v;
 }
 
@@ -598,10 +599,11 @@ extern "C" int sdg_grid_activate_keys(sdg_grid g, const int32_t* keys, int64_t n
     std::lock_guard<std::mutex> lk(g->mu);
     int rc = begin_activation(g);
     if (rc) return rc;
-    if (n > 0)
+    if (n > 0) {
+        const unsigned long long room = (unsigned long long)(g->max_blocks - g->n_blocks);
         k_candidates_keys<<<grid_blocks(n), kThreads, 0, g->stream>>>(keys, n, g->table, g->mask, g->tmp_table,
-                                                                      g->counters,
-                                                                      (unsigned long long)(g->max_blocks - g->n_blocks));
+                                                                      g->counters, room);
+    }
     return finish_activation(g, n_new);
 }
 

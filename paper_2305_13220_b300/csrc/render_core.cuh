@@ -590,7 +590,8 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                                 float sv[4];
                                 sem_load4(g, addr[e], 4 * c4, sv);
 #pragma unroll
-                                for (int q = 0; q < 4; ++q) sem_acc[4 * c4 + q] = fmaf(W[e], sv[q], sem_acc[4 * c4 + q]);
+                                for (int q = 0; q < 4; ++q)
+                                    sem_acc[4 * c4 + q] = fmaf(W[e], sv[q], sem_acc[4 * c4 + q]);
                             }
                         }
                     }

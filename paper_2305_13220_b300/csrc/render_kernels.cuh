@@ -19,8 +19,8 @@ constexpr int render_min_blocks() {
 }
 
 template <int MODE, bool BF16, bool SEM, int Q>
-__global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>())) k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0,
-                                                PassArgs a) {
+__global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>()))
+    k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
     __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t slot = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
