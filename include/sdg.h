@@ -334,7 +334,9 @@ int sdg_train_step_rays(sdg_grid g, const float* rays_dev, int64_t n, const floa
  * Same arguments and results as sdg_train_step_rays without loss_dev: the
  * gradients accumulate into the grid and loss_sum_dev [1] (may be NULL)
  * receives the summed loss.  lo->ray_order is ignored: the rays run in the
- * given order (surface ordering would need a further scratch).  n may be at most 1048576 rays; larger n returns
+ * given order (surface ordering would need a further scratch).
+ * lo->learn_beta must be 0 (dL/dbeta needs a per-ray partial buffer):
+ * SDG_ERR_ARG otherwise.  n may be at most 1048576 rays; larger n returns
  * SDG_ERR_CAPACITY before any work is enqueued.  The first call on each
  * device looks up the array's device address (a one-time set-up); make that
  * first call before any stream capture.  Every call on a device shares the

@@ -430,6 +430,8 @@ extern "C" int sdg_train_step_rays_noalloc(sdg_grid g, const float* rays, int64_
                                            const sdg_loss_opts* lo, float* loss_sum) {
     if (!g || !lo || n < 0 || (n > 0 && (!rays || !trgb || !tdepth)))
         return fail(SDG_ERR_ARG, "sdg_train_step_rays_noalloc: null argument");
+    if (lo->learn_beta)  // dL/dbeta needs a per-ray partial buffer this entry point does not have
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays_noalloc: learn_beta is not supported");
     if (n > kNoAllocMaxRays)
         return fail(SDG_ERR_CAPACITY, "sdg_train_step_rays_noalloc: n = " + std::to_string(n) +
                                           " rays exceeds the fixed scratch capacity of 1048576 rays");

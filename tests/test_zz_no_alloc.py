@@ -74,3 +74,9 @@ def test_noalloc_rejects_batches_beyond_its_capacity():
            C.byref(lo), None)
     assert rc == A.ERR_CAPACITY
     assert b"1048576" in A.lib().sdg_last_error()
+    # dL/dbeta needs a per-ray buffer: learning beta is refused, not silently skipped
+    lb = A.LossOpts(lambda_depth=0.1, lambda_sem=0.1, learn_beta=1)
+    rc = f(G.handle, rays.data_ptr(), rays.shape[0], t_rgb.data_ptr(), t_depth.data_ptr(), None, C.byref(o),
+           C.byref(lb), None)
+    assert rc == A.ERR_ARG
+    assert b"learn_beta" in A.lib().sdg_last_error()
