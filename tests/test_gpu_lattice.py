@@ -1,6 +1,6 @@
 """Permutohedral-lattice filter and the CRF mean-field update on the GPU against the oracle (Eq. 19-22).
 
-The simplex search runs in FP64 in the oracle's operation order on both sides, so the lattice (its size) must be
+The simplex search runs in FP32 in one fixed operation order on both sides, so the lattice (its size) must be
 identical; splat / blur / slice run in FP32 on the GPU: outputs within 1e-5 of the output scale.  Features are
 CRF-like: positions, colours and normals of surface samples of the tiny room, each divided by its bandwidth."""
 import numpy as np
@@ -41,6 +41,23 @@ def test_lattice_filter_matches_oracle(d, normalize):
     assert M == M_ref
     got = out.double().cpu().numpy()
     np.testing.assert_allclose(got, ref, atol=1e-5 * np.abs(ref).max(), rtol=1e-4)
+
+
+@pytest.mark.parametrize("d", [2, 3, 9])
+def test_filter_does_not_depend_on_point_order(d):
+    """The memory order of the lattice rows follows the points that created them; permuting the points permutes
+    the outputs and leaves the lattice size unchanged (values equal up to the order of FP32 splat atomics)."""
+    sc, G, O, _, _ = tiny_room()
+    f = crf_features(4000, seed=10 + d)[:, :d].copy()
+    rng = np.random.default_rng(d)
+    v = rng.normal(size=(4000, 6)).astype(np.float32)
+    perm = rng.permutation(4000)
+    out, M = G.lattice_filter(torch.as_tensor(f, device="cuda"), torch.as_tensor(v, device="cuda"), True)
+    out_p, M_p = G.lattice_filter(torch.as_tensor(f[perm], device="cuda"), torch.as_tensor(v[perm], device="cuda"),
+                                  True)
+    assert M_p == M and M > 100
+    a, b = out.double().cpu().numpy(), out_p.double().cpu().numpy()
+    np.testing.assert_allclose(b, a[perm], atol=1e-5 * np.abs(a).max(), rtol=1e-4)
 
 
 def test_meanfield_matches_oracle():
