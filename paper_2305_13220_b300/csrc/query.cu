@@ -6,9 +6,10 @@
 // in one pass, without a second differentiation.
 //
 // One thread per point: FP32 cell and block of the point, the block's index
-// from the hash map, corner addresses through the neighbour table (corners
-// past the block's +x/+y/+z faces live in the neighbour blocks).  A point with
-// a corner in an unallocated block, or outside the block-key range, is invalid.
+// from the dense block-index grid (one load), corner addresses through the
+// neighbour table (corners past the block's +x/+y/+z faces live in the
+// neighbour blocks).  A point with a corner in an unallocated block, or
+// outside the block-key range, is invalid.
 #include "internal.h"
 #include "reduce.cuh"
 #include "render_core.cuh"
@@ -39,7 +40,7 @@ __device__ __forceinline__ PointStencil point_stencil(const GridDev& g, float x,
     s.f[0] = gx - fx;
     s.f[1] = gy - fy;
     s.f[2] = gz - fz;
-    const int blk = sdg_table_find(g.table, g.mask, sdg_pack_key(cx >> 3, cy >> 3, cz >> 3));
+    const int blk = block_at(g, cx >> 3, cy >> 3, cz >> 3);  // dense block-index grid: one load, -1 if absent
     if (blk < 0) return s;
     const int lcell = (cx & 7) | ((cy & 7) << 3) | ((cz & 7) << 6);
     s.valid = corner_addresses(g, blk, lcell, s.addr);
