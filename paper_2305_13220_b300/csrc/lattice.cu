@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_lat_number(Table t, int* count, int* ke
 // checked against its slot's (a fingerprint collision is reported, never merged silently), then a 16-byte
 // vector atomic.  Group g holds channels 4g..4g+3; channel c is the homogeneous weight, the rest is padding.
 // The thread of group 0 records the vertices' lattice indices for the slice.
-__global__ void k_lat_splat(const float* __restrict__ val, int64_t n, int d, int c, int g4, Table t,
+__global__ void __launch_bounds__(256, 8) k_lat_splat(const float* __restrict__ val, int64_t n, int d, int c, int g4, Table t,
                             const int* __restrict__ keys, const int* __restrict__ sr,
                             const signed char* __restrict__ srank, const int* __restrict__ vslot,
                             const float* __restrict__ vbary, float4* __restrict__ lat, int* __restrict__ vidx,
@@ -288,7 +288,7 @@ __global__ void k_lat_splat(const float* __restrict__ val, int64_t n, int d, int
 // one thread per (point, direction) and both signs.  Both fingerprints of a neighbour key are formed
 // incrementally from the point's linear forms (multiplier tables in shared memory); a slot is accepted when both
 // match.
-__global__ void __launch_bounds__(256) k_lat_neighbours(const int* __restrict__ keys, int M, int d, Table t,
+__global__ void __launch_bounds__(256, 8) k_lat_neighbours(const int* __restrict__ keys, int M, int d, Table t,
                                                         int* __restrict__ nb) {
     __shared__ unsigned long long P[kMaxD], P2[kMaxD];
     if (threadIdx.x < kMaxD) {
