@@ -45,7 +45,9 @@ __global__ void __launch_bounds__(256) k_opt_f32(float4* __restrict__ th, float4
                                                  OptParams p) {
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        float4 t = SDG_LD(th + i), g = SDG_LD(gr + i), mm = SDG_LD(m + i), vv = SDG_LD(v + i);
+        // RMSProp has no first moment: m is neither read nor written
+        float4 t = SDG_LD(th + i), g = SDG_LD(gr + i), mm = ALGO == SDG_OPT_ADAM ? SDG_LD(m + i) : z,
+               vv = SDG_LD(v + i);
         t.x = update<ALGO>(t.x, g.x, mm.x, vv.x, p);
         t.y = update<ALGO>(t.y, g.y, mm.y, vv.y, p);
         t.z = update<ALGO>(t.z, g.z, mm.z, vv.z, p);
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(256) k_opt_bf16(uint2* __restrict__ th, float4
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
         uint2 t = SDG_LD(th + i);
-        float4 g = SDG_LD(gr + i), mm = SDG_LD(m + i), vv = SDG_LD(v + i);
+        float4 g = SDG_LD(gr + i), mm = ALGO == SDG_OPT_ADAM ? SDG_LD(m + i) : z, vv = SDG_LD(v + i);
         float a0 = bf_lo(t.x), a1 = bf_hi(t.x), a2 = bf_lo(t.y), a3 = bf_hi(t.y);
         a0 = update<ALGO>(a0, g.x, mm.x, vv.x, p);
         a1 = update<ALGO>(a1, g.y, mm.y, vv.y, p);
