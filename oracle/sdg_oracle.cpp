@@ -826,7 +826,7 @@ void orc_rmsprop(double* theta, double* grad, double* v, int64_t n, double lr, d
 // order takes the same integer decisions:
 //   x_a = (float)(8 b_a + l_a) * vs                       per axis a
 //   e_a = x_a - t_a;  c_j = (R_0j e_0 + R_1j e_1) + R_2j e_2   (c = R^T (x - t))
-//   kept only if c_2 > 0;  pu = fx * (c_0 / c_2) + cx,  pv = fy * (c_1 / c_2) + cy
+//   kept only if c_2 > 0;  r = 1 / c_2;  pu = fx * (c_0 * r) + cx,  pv = fy * (c_1 * r) + cy
 //   pixel (floor(pu), floor(pv)) inside the image, its depth D finite and > 0
 //   o = D - c_2 (the SDF seen from view i, positive in front of the surface)
 //   kept only if o >= -mu (farther behind the observed surface is occlusion)
@@ -858,8 +858,9 @@ void orc_fuse(const int32_t* keys, int64_t N, float vs, int F, int H, int W, con
                     c[j] = (p0 + p1) + p2;
                 }
                 if (!(c[2] > 0.0f)) continue;
-                float pu = k[0] * (c[0] / c[2]) + k[2];
-                float pv = k[1] * (c[1] / c[2]) + k[3];
+                const float r = 1.0f / c[2];
+                float pu = k[0] * (c[0] * r) + k[2];
+                float pv = k[1] * (c[1] * r) + k[3];
                 float fu = std::floor(pu), fv = std::floor(pv);
                 if (!(fu >= 0.0f && fu < (float)W && fv >= 0.0f && fv < (float)H)) continue;
                 const int64_t pix = (int64_t)i * H * W + (int64_t)fv * W + (int64_t)fu;
