@@ -4,17 +4,18 @@
 // voxel-pixel associations, kept here as running means with a per-voxel count
 // (the WEIGHT channel), so that frames can be fused in any number of calls.
 //
-// One CTA per voxel block, one thread per voxel.  The CTA first finds the
-// frames whose view frustum can contain the block (a conservative bounding-
-// sphere test, one frame per thread, then an order-preserving compaction in
-// shared memory), so each voxel only projects itself into those frames.  The
-// association itself is decided in FP32 with a fixed operation order
-// (round-to-nearest intrinsics, no contraction) so that the integer decisions
-// -- which pixel, kept or not -- are exactly those of any FP32 evaluation of
-// the same order:
+// One CTA per voxel block, one thread per voxel (cameras are read as four
+// 16-byte loads, logits as float4 when their count allows).  The CTA first
+// finds the frames whose view frustum can contain the block (a conservative
+// bounding-sphere test, one frame per thread, then an order-preserving
+// compaction in shared memory), so each voxel only projects itself into those
+// frames.  The association itself is decided in FP32 with a fixed operation
+// order (round-to-nearest intrinsics, no contraction) so that the integer
+// decisions -- which pixel, kept or not -- are exactly those of any FP32
+// evaluation of the same order:
 //   x_a = (float)(8 b_a + l_a) * vs;  e_a = x_a - t_a;
 //   c_j = (R_0j e_0 + R_1j e_1) + R_2j e_2        (c = R^T (x - t));  need c_2 > 0
-//   pu = fx (c_0 / c_2) + cx, pv = fy (c_1 / c_2) + cy; pixel (floor pu, floor pv) inside the image
+//   r = 1 / c_2;  pu = fx (c_0 r) + cx, pv = fy (c_1 r) + cy; pixel (floor pu, floor pv) inside the image
 //   D = depth there, finite and > 0;  o = D - c_2;  need o >= -mu;  psi = min(o, mu)
 // The sums of one call accumulate in FP32 in frame order and are folded into
 // the running mean once: theta' = (w theta + sum) / (w + n).
@@ -29,11 +30,23 @@ constexpr int kFuseThreads = 512;     // one voxel block
 constexpr int kFuseMaxFrames = 1024;  // frames per launch (their visible subset is listed in shared memory)
 constexpr int kSemCap = 32;
 
-struct FuseCam {
+struct __align__(16) FuseCam {
     float R[9];  // camera to world rotation, row-major
     float t[3];
     float fx, fy, cx, cy;
 };
+
+// A camera as four 16-byte loads (uniform across the CTA) instead of sixteen scalar ones.
+__device__ __forceinline__ FuseCam load_cam(const FuseCam* p) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+    FuseCam r;
+    r.R[0] = a.x; r.R[1] = a.y; r.R[2] = a.z; r.R[3] = a.w;
+    r.R[4] = b.x; r.R[5] = b.y; r.R[6] = b.z; r.R[7] = b.w;
+    r.R[8] = c.x; r.t[0] = c.y; r.t[1] = c.z; r.t[2] = c.w;
+    r.fx = d.x; r.fy = d.y; r.cx = d.z; r.cy = d.w;
+    return r;
+}
 
 struct FuseArgs {
     const int4* keys;
@@ -44,6 +57,7 @@ struct FuseArgs {
     const float* rgb;    // [F][H][W][3] or NULL
     const float* sem;    // [F][H][W][ns] or NULL
     int ns;
+    bool sem4;  // ns a multiple of 4 and sem 16-byte aligned: a pixel's logits load as float4
     float4* geo;   // FP32 layout: (sdf, r, g, b) running means
     float* sdf;    // BF16 layout: SDF running mean
     float4* racc;  // BF16 layout: FP32 colour running mean (the colour gradient channel)
@@ -84,7 +98,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_fuse(FuseArgs a) {
             const int f = f0 + l;
             bool in = false;
             if (f < a.F) {
-                const FuseCam c = a.cams[f];
+                const FuseCam c = load_cam(a.cams + f);
                 const float e[3] = {ctr[0] - c.t[0], ctr[1] - c.t[1], ctr[2] - c.t[2]};
                 float p[3];
                 for (int j = 0; j < 3; ++j) p[j] = c.R[j] * e[0] + c.R[3 + j] * e[1] + c.R[6 + j] * e[2];
@@ -119,14 +133,15 @@ __global__ void __launch_bounds__(kFuseThreads) k_fuse(FuseArgs a) {
     for (int q = 0; q < (SEM ? kSemCap : 1); ++q) ss[q] = 0.f;
     for (int k = 0; k < nv; ++k) {
         const int i = vis[k];
-        const FuseCam& c = a.cams[i];
+        const FuseCam c = load_cam(a.cams + i);
         const float e0 = __fsub_rn(x0, c.t[0]), e1 = __fsub_rn(x1, c.t[1]), e2 = __fsub_rn(x2, c.t[2]);
         const float c0 = __fadd_rn(__fadd_rn(__fmul_rn(c.R[0], e0), __fmul_rn(c.R[3], e1)), __fmul_rn(c.R[6], e2));
         const float c1 = __fadd_rn(__fadd_rn(__fmul_rn(c.R[1], e0), __fmul_rn(c.R[4], e1)), __fmul_rn(c.R[7], e2));
         const float c2 = __fadd_rn(__fadd_rn(__fmul_rn(c.R[2], e0), __fmul_rn(c.R[5], e1)), __fmul_rn(c.R[8], e2));
         if (!(c2 > 0.f)) continue;
-        const float pu = __fadd_rn(__fmul_rn(c.fx, __fdiv_rn(c0, c2)), c.cx);
-        const float pv = __fadd_rn(__fmul_rn(c.fy, __fdiv_rn(c1, c2)), c.cy);
+        const float rz = __frcp_rn(c2);  // one correctly rounded reciprocal, two products
+        const float pu = __fadd_rn(__fmul_rn(c.fx, __fmul_rn(c0, rz)), c.cx);
+        const float pv = __fadd_rn(__fmul_rn(c.fy, __fmul_rn(c1, rz)), c.cy);
         const float fu = floorf(pu), fv = floorf(pv);
         if (!(fu >= 0.f && fu < (float)a.W && fv >= 0.f && fv < (float)a.H)) continue;
         const int64_t pix = (int64_t)i * HW + (int64_t)fv * a.W + (int64_t)fu;
@@ -144,9 +159,21 @@ __global__ void __launch_bounds__(kFuseThreads) k_fuse(FuseArgs a) {
         if constexpr (SEM) {
             if (a.sem) {
                 const float* sp = a.sem + (int64_t)a.ns * pix;
+                if (a.sem4) {
 #pragma unroll
-                for (int q = 0; q < kSemCap; ++q)
-                    if (q < a.ns) ss[q] += __ldg(sp + q);
+                    for (int q4 = 0; q4 < kSemCap / 4; ++q4)
+                        if (4 * q4 < a.ns) {
+                            const float4 v = __ldg(reinterpret_cast<const float4*>(sp) + q4);
+                            ss[4 * q4] += v.x;
+                            ss[4 * q4 + 1] += v.y;
+                            ss[4 * q4 + 2] += v.z;
+                            ss[4 * q4 + 3] += v.w;
+                        }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kSemCap; ++q)
+                        if (q < a.ns) ss[q] += __ldg(sp + q);
+                }
             }
         }
     }
@@ -280,6 +307,7 @@ extern "C" int sdg_fuse_frames(sdg_grid g, int64_t F, int H, int W, const float*
     a.H = H;
     a.W = W;
     a.ns = g->desc.n_sem;
+    a.sem4 = with_sem && a.ns % 4 == 0 && ((uintptr_t)sem & 15u) == 0;
     a.geo = g->geo;
     a.sdf = g->sdf;
     a.racc = g->grgb;
