@@ -380,7 +380,8 @@ int sdg_adam_step(sdg_grid g, const sdg_adam_opts* a);
  * is taken in FP32 in this exact order (no fused multiply-add):
  *   x_a = (float)(8 b_a + l_a) * voxel_size;  e_a = x_a - t_a
  *   c_j = (R_0j e_0 + R_1j e_1) + R_2j e_2      (camera coordinates, c = R^T (x - t))
- *   kept only if c_2 > 0;  pu = fx (c_0 / c_2) + cx,  pv = fy (c_1 / c_2) + cy
+ *   kept only if c_2 > 0;  r = 1 / c_2 (correctly rounded);  pu = fx (c_0 r) + cx,
+ *   pv = fy (c_1 r) + cy
  *   pixel (floor pu, floor pv) inside the image (pixel centres at +0.5, as in
  *   activation); D = depth there finite and > 0;  o = D - c_2 (the SDF seen
  *   from frame i, positive in front of the surface); kept only if o >= -mu
