@@ -118,22 +118,25 @@ def _oracle_backward_runs(O, rays, runs, N, seed, stratified, bg, seeds):
 
 @pytest.mark.parametrize("mode", ["recompute", "store"])
 @pytest.mark.parametrize("stratified", [True, False])
-def test_backward_matches_oracle(sdg, room, mode, stratified):
+@pytest.mark.parametrize("N", [64, 192])  # 192: 6 samples per lane, where the forward reuses a cell's corners
+def test_backward_matches_oracle(sdg, room, mode, stratified, N):
     sc, G, O, _, _ = room
     rays = _view(sc, seed=2)
     bg = (0.3, 0.1, 0.7)
-    ref = O.render(rays, 64, seed=3, stratified=stratified, bg=bg)
+    ref = O.render(rays, N, seed=3, stratified=stratified, bg=bg)
     runs = _runs(~ref["degenerate"])
     n = len(rays)
     gen = torch.Generator().manual_seed(0)
     seeds = tuple(torch.randn(s, generator=gen).cuda() for s in ((n, 3), (n,), (n,))) + (None,)
-    got = _gpu_backward_runs(sdg, G, rays.cuda(), runs, 64, 3, stratified, bg, seeds, mode)
-    want = _oracle_backward_runs(O, rays.numpy(), runs, 64, 3, stratified, bg, seeds)
+    got = _gpu_backward_runs(sdg, G, rays.cuda(), runs, N, 3, stratified, bg, seeds, mode)
+    want = _oracle_backward_runs(O, rays.numpy(), runs, N, 3, stratified, bg, seeds)
     assert_grad_close(got["sdf"], want["sdf"], what="sdf")
     assert_grad_close(got["rgb"], want["rgb"], what="rgb")
 
 
-def test_store_and_recompute_agree(sdg, room):
+@pytest.mark.parametrize("N", [128, 256])
+def test_store_and_recompute_agree(sdg, room, N):
+    """At 256 samples (8 per lane) both forwards reuse a cell's corners and the recompute backward does not."""
     sc, G, O, _, _ = room
     rays = _view(sc, seed=4).cuda()
     n = rays.shape[0]
@@ -141,7 +144,7 @@ def test_store_and_recompute_agree(sdg, room):
     res = {}
     for mode in ("recompute", "store"):
         G.zero_grad()
-        o = sdg.render(G, rays, 128, seed=1, want_ctx=True, mode=mode)
+        o = sdg.render(G, rays, N, seed=1, want_ctx=True, mode=mode)
         sdg.backward(o["ctx"], *g)
         res[mode] = grad_arrays(G, G.num_blocks)
         res[mode + "_out"] = o["rgb"].clone()
