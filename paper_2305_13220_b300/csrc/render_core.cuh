@@ -440,11 +440,22 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     }
     const float s_after = __shfl_down_sync(kFull, s_[0], 1);  // first sample of the next lane
 
-    float t_[Q], dl_[Q], d_[Q], cr_[Q], cg_[Q], cb_[Q], tau_[Q], dsig_[Q], fx_[Q], fy_[Q], fz_[Q];
+    float t_[Q], dl_[Q], d_[Q], cr_[Q], cg_[Q], cb_[Q], tau_[Q], dsig_[Q];
     int blk_[Q], lc_[Q];
     float bq_[kBeta ? Q : 1];
     float gnx_[kNrm ? Q : 1], gny_[kNrm ? Q : 1], gnz_[kNrm ? Q : 1];  // grad f at the samples (Eq. 17)
     unsigned vmask = 0;
+    // fractional position of sample i in its cell, recomputed from t_[i] wherever it is needed (the same
+    // operations give the same bits), so no per-sample fractions stay in registers
+    auto cell_frac = [&](int i, float& fx, float& fy, float& fz) {
+        const float px = fmaf(t_[i], j.d.x, j.o.x) * g.inv_vs;
+        const float py = fmaf(t_[i], j.d.y, j.o.y) * g.inv_vs;
+        const float pz = fmaf(t_[i], j.d.z, j.o.z) * g.inv_vs;
+        fx = px - floorf(px);
+        fy = py - floorf(py);
+        fz = pz - floorf(pz);
+    };
+
     unsigned smask = 0;  // stored mode: samples whose record is valid
     // place sample i: its s, t, cell and block; false if the lane has no sample i
     auto place = [&](int i) -> bool {
@@ -452,7 +463,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         t_[i] = 0.f; dl_[i] = 0.f; d_[i] = 0.f; cr_[i] = cg_[i] = cb_[i] = 0.f; tau_[i] = 0.f; dsig_[i] = 0.f;
         if constexpr (kBeta) bq_[i] = 0.f;
         if constexpr (kNrm) gnx_[i] = gny_[i] = gnz_[i] = 0.f;
-        fx_[i] = fy_[i] = fz_[i] = 0.f; blk_[i] = -1; lc_[i] = 0;
+        blk_[i] = -1; lc_[i] = 0;
         if (!any || k >= N) return false;
         float sn;
         if (k + 1 >= N) sn = S;
@@ -479,7 +490,6 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         const float pz = fmaf(t_[i], j.d.z, j.o.z) * g.inv_vs;
         const float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
         const int cx = (int)flx, cy = (int)fly, cz = (int)flz;
-        fx_[i] = px - flx; fy_[i] = py - fly; fz_[i] = pz - flz;
         lc_[i] = (cx & 7) | ((cy & 7) << 3) | ((cz & 7) << 6);
         if constexpr (!kStoreIn) {
             // the sample's own block: the traversal cell's, unless rounding put it across a block face
@@ -507,8 +517,9 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 if (valid) load_corners<BF16>(g, addr, cs, crr, cgg, cbb);
             }
             if (valid) {
-                float w[8];
-                trilinear_weights(fx_[i], fy_[i], fz_[i], w);
+                float w[8], fx, fy, fz;
+                cell_frac(i, fx, fy, fz);
+                trilinear_weights(fx, fy, fz, w);
                 float dd = 0.f, r = 0.f, gg = 0.f, bb = 0.f;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
@@ -518,7 +529,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                     bb = fmaf(w[e], cbb[e], bb);
                 }
                 d_[i] = dd; cr_[i] = r; cg_[i] = gg; cb_[i] = bb;
-                if constexpr (kNrm) sdf_gradient(fx_[i], fy_[i], fz_[i], g.inv_vs, cs, gnx_[i], gny_[i], gnz_[i]);
+                if constexpr (kNrm) sdf_gradient(fx, fy, fz, g.inv_vs, cs, gnx_[i], gny_[i], gnz_[i]);
             }
         }
         if (valid) {
@@ -612,7 +623,9 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 }
                 if (v) {
                     float r[8];
-                    trilinear_weights(fx_[i], fy_[i], fz_[i], r);
+                    float fx, fy, fz;
+                    cell_frac(i, fx, fy, fz);
+                    trilinear_weights(fx, fy, fz, r);
 #pragma unroll
                     for (int e = 0; e < 8; ++e) W[e] = fmaf(w_[i], r[e], W[e]);
                 }
@@ -774,7 +787,9 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 }
                 if ((vmask >> i) & 1u) {
                     float r[8];
-                    trilinear_weights(fx_[i], fy_[i], fz_[i], r);
+                    float fx, fy, fz;
+                    cell_frac(i, fx, fy, fz);
+                    trilinear_weights(fx, fy, fz, r);
                     float acc = 0.f;
 #pragma unroll
                     for (int e = 0; e < 8; ++e) acc = fmaf(r[e], dot[e], acc);
@@ -820,7 +835,9 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             }
             if (v) {
                 float r[8];
-                trilinear_weights(fx_[i], fy_[i], fz_[i], r);
+                float fx, fy, fz;
+                cell_frac(i, fx, fy, fz);
+                trilinear_weights(fx, fy, fz, r);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     aS[e] = fmaf(r[e], dd_[i], aS[e]);
@@ -830,7 +847,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                     // the rendered normal's grad f part: w_i g_N . grad_x r_e(x_i) onto each corner's SDF
                     const float sc = w_[i] * g.inv_vs;
                     float q[8];
-                    dot_weight_gradients(fx_[i], fy_[i], fz_[i], sc * gNx, sc * gNy, sc * gNz, q);
+                    dot_weight_gradients(fx, fy, fz, sc * gNx, sc * gNy, sc * gNz, q);
 #pragma unroll
                     for (int e = 0; e < 8; ++e) aS[e] += q[e];
                 }
