@@ -104,11 +104,12 @@ def build_workload(sdg, torch, device, n_views, rays_per_step, n_batches=4, seed
     torch.cuda.synchronize()
     t_depth = time.time() - t0
     G = sdg.Grid(VS, max_blocks, beta=BETA)
-    # activation: timed separately (all 50 maps), CUDA events on the grid's stream
+    # activation: timed separately, all 50 maps in one batch (one synchronisation)
+    depth_all = torch.stack(depths).contiguous()
+    T_all = np.stack([np.asarray(T, np.float64) for T in poses])
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    for T, d in zip(poses, depths):
-        G.activate_depth(d, K, T, BAND)
+    G.activate_depth_frames(depth_all, K, T_all, BAND)
     ev1.record()
     torch.cuda.synchronize()
     act_ms = ev0.elapsed_time(ev1)
@@ -468,17 +469,19 @@ def _phase_times(torch, sdg, G, batches, K, train):
 
 
 def _activate_views(sdg, torch, G, sc, poses, K, device, band):
+    """Activates the grid from the views' depth maps in one batch; returns its time in ms (maps made beforehand)."""
+    import synth
+    depth_all = torch.stack([synth.depth_map(sc, T, W, H, K, device=device) for T in poses]).contiguous()
+    T_all = np.stack([np.asarray(T, np.float64) for T in poses])
+    torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    import synth
-    ms = 0.0
-    for T in poses:
-        d = synth.depth_map(sc, T, W, H, K, device=device)
-        t0.record()
-        G.activate_depth(d, K, T, band)
-        t1.record()
-        torch.cuda.synchronize()
-        ms += t0.elapsed_time(t1)
+    t0.record()
+    G.activate_depth_frames(depth_all, K, T_all, band)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    del depth_all
     return ms
 
 

@@ -134,6 +134,16 @@ int sdg_grid_activate_points(sdg_grid g, const float* xyz_dev, int64_t n, int32_
 int sdg_grid_activate_depth(sdg_grid g, const float* depth_dev, int32_t H, int32_t W, const float K[4],
                             const float Twc[12], int32_t dilate_voxels, int64_t* n_new);
 
+/* sdg_grid_activate_depth over F depth maps as ONE activation batch: the
+ * union of their blocks is inserted at once, new blocks indexed in ascending
+ * packed-key order over the whole batch (F sequential calls give the same
+ * block set, indexed map by map).  depth_dev: [F][H][W] float z-depth.
+ * K (host): [F][4] fx, fy, cx, cy.  Twc (host): [F][12] row-major 3x4
+ * camera-to-world.  The per-map unprojection is sdg_grid_activate_depth's.
+ * F = 0 adds nothing.  Synchronises once; all-or-nothing over the batch. */
+int sdg_grid_activate_depth_frames(sdg_grid g, const float* depth_dev, int32_t F, int32_t H, int32_t W,
+                                   const float* K, const float* Twc, int32_t dilate_voxels, int64_t* n_new);
+
 /* Activates an explicit list of block keys keys_dev [n][3] int32 (duplicates
  * and already active keys allowed).  Synchronises; all-or-nothing. */
 int sdg_grid_activate_keys(sdg_grid g, const int32_t* keys_dev, int64_t n, int64_t* n_new);

@@ -79,6 +79,7 @@ SIGNATURES = {
     "sdg_grid_destroy": [_p],
     "sdg_grid_activate_points": [_p, _p, _i64, _i32, _P(_i64)],
     "sdg_grid_activate_depth": [_p, _p, _i32, _i32, _P(C.c_float), _P(C.c_float), _i32, _P(_i64)],
+    "sdg_grid_activate_depth_frames": [_p, _p, _i32, _i32, _i32, _P(C.c_float), _P(C.c_float), _i32, _P(_i64)],
     "sdg_grid_activate_keys": [_p, _p, _i64, _P(_i64)],
     "sdg_grid_num_blocks": [_p, _P(_i64)],
     "sdg_grid_keys": [_p, _p],

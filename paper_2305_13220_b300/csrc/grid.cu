@@ -467,6 +467,16 @@ int finish_activation(sdg_grid g, int64_t* n_new) {
     return rebuild_derived(g);
 }
 
+Cam make_cam(const float K[4], const float T[12]) {
+    Cam cam;
+    cam.fx_inv = 1.0f / K[0];
+    cam.fy_inv = 1.0f / K[1];
+    cam.cx = K[2];
+    cam.cy = K[3];
+    for (int i = 0; i < 12; ++i) cam.T[i] = T[i];
+    return cam;
+}
+
 int begin_activation(sdg_grid g) {
     if (!g) return fail(SDG_ERR_ARG, "null grid");
     int rc = use_device(g);
@@ -580,16 +590,33 @@ extern "C" int sdg_grid_activate_depth(sdg_grid g, const float* depth, int32_t H
     std::lock_guard<std::mutex> lk(g->mu);
     int rc = begin_activation(g);
     if (rc) return rc;
-    Cam cam;
-    cam.fx_inv = 1.0f / K[0];
-    cam.fy_inv = 1.0f / K[1];
-    cam.cx = K[2];
-    cam.cy = K[3];
-    for (int i = 0; i < 12; ++i) cam.T[i] = T[i];
     const float inv_vs = 1.0f / g->desc.voxel_size;
     k_candidates_depth<<<grid_blocks((int64_t)H * W), kThreads, 0, g->stream>>>(
-        depth, H, W, cam, inv_vs, r, g->table, g->mask, g->tmp_table, g->counters,
+        depth, H, W, make_cam(K, T), inv_vs, r, g->table, g->mask, g->tmp_table, g->counters,
         (unsigned long long)(g->max_blocks - g->n_blocks));
+    return finish_activation(g, n_new);
+}
+
+// All frames' candidates go into the one de-duplication set, then a single compaction, sort and insertion: one
+// activation batch (new blocks indexed in ascending packed-key order over the whole batch), one synchronisation.
+extern "C" int sdg_grid_activate_depth_frames(sdg_grid g, const float* depth, int32_t F, int32_t H, int32_t W,
+                                              const float* K, const float* T, int32_t r, int64_t* n_new) {
+    if (n_new) *n_new = 0;
+    if (!g || F < 0 || (F > 0 && (!depth || !K || !T)) || H <= 0 || W <= 0 || r < 0 || r > 64)
+        return fail(SDG_ERR_ARG, "sdg_grid_activate_depth_frames");
+    for (int32_t f = 0; f < F; ++f)
+        if (!(K[4 * f] != 0.f) || !(K[4 * f + 1] != 0.f))
+            return fail(SDG_ERR_ARG, "sdg_grid_activate_depth_frames: fx and fy must be non-zero");
+    std::lock_guard<std::mutex> lk(g->mu);
+    int rc = begin_activation(g);
+    if (rc) return rc;
+    const float inv_vs = 1.0f / g->desc.voxel_size;
+    const unsigned long long room = (unsigned long long)(g->max_blocks - g->n_blocks);
+    const int64_t HW = (int64_t)H * W;
+    for (int32_t f = 0; f < F; ++f)
+        k_candidates_depth<<<grid_blocks(HW), kThreads, 0, g->stream>>>(
+            depth + f * HW, H, W, make_cam(K + 4 * f, T + 12 * f), inv_vs, r, g->table, g->mask, g->tmp_table,
+            g->counters, room);
     return finish_activation(g, n_new);
 }
 

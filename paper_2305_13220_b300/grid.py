@@ -101,6 +101,19 @@ class Grid:
                int(dilate_voxels), C.byref(n))
         return n.value
 
+    def activate_depth_frames(self, depth: torch.Tensor, K, Twc, dilate_voxels: int) -> int:
+        """activate_depth over F maps as one activation batch: depth [F,H,W] on the grid's device, K [4] or [F,4],
+        Twc [3,4] or [F,3,4] camera-to-world.  Returns the number of blocks added."""
+        F, H, W = depth.shape
+        Kt = torch.as_tensor(K, dtype=torch.float64).reshape(-1, 4).expand(F, 4)
+        Tt = torch.as_tensor(Twc, dtype=torch.float64).reshape(-1, 12).expand(F, 12)
+        Kc = (C.c_float * max(4 * F, 1))(*[float(v) for v in Kt.reshape(-1).tolist()])
+        Tc = (C.c_float * max(12 * F, 1))(*[float(v) for v in Tt.reshape(-1).tolist()])
+        n = C.c_int64()
+        A.call("sdg_grid_activate_depth_frames", self._h, _ptr(depth, torch.float32, "depth"), F, H, W, Kc, Tc,
+               int(dilate_voxels), C.byref(n))
+        return n.value
+
     def fuse(self, depth: torch.Tensor, K, Twc, mu: float, rgb: Optional[torch.Tensor] = None,
              sem: Optional[torch.Tensor] = None):
         """Volumetric fusion (Eq. 9-11) of F frames: depth [F,H,W] or [H,W] (z-depth), optional rgb [F,H,W,3] and

@@ -59,6 +59,43 @@ def test_activate_depth_bit_exact(sdg, which):
     np.testing.assert_array_equal(G.keys().cpu().numpy(), want)
 
 
+def test_activate_depth_frames_is_one_batch(sdg):
+    """F depth maps in one call: the union of their blocks, indexed in ascending (z, y, x) order over the whole
+    batch (the oracle's key set), the same block set as map-by-map calls, all-or-nothing on capacity."""
+    sc, vs, r, W, H = synth.scene_tiny_room(0), 0.04, 3, 64, 48
+    K = synth.intrinsics(W, H)
+    poses = synth.random_poses(sc, 6, seed=5)
+    views = [(T, synth.depth_map(sc, T, W, H, K)) for T in poses]
+    depth = torch.stack([d for _, d in views]).cuda()
+    Tw = np.stack([np.asarray(T, np.float64) for T, _ in views])
+    ks = oracle.KeySet()
+    for T, d in views[:4]:
+        ks.add_depth(d, K, T, vs, r)
+    first = ks.keys()
+    G = sdg.Grid(vs, 4096)
+    n = G.activate_depth_frames(depth[:4].contiguous(), K, Tw[:4], r)
+    assert n == len(first) == G.num_blocks
+    np.testing.assert_array_equal(G.keys().cpu().numpy(), first)
+    # a second batch appends its new blocks, again in ascending order; zero maps add nothing
+    for T, d in views[4:]:
+        ks.add_depth(d, K, T, vs, r)
+    old = set(map(tuple, first.tolist()))
+    second = np.array([k for k in ks.keys().tolist() if tuple(k) not in old], np.int32).reshape(-1, 3)
+    assert G.activate_depth_frames(depth[4:].contiguous(), K, Tw[4:], r) == len(second)
+    np.testing.assert_array_equal(G.keys().cpu().numpy(), np.concatenate([first, second]))
+    assert G.activate_depth_frames(depth[:0], K, Tw[:0], r) == 0
+    # map by map: the same set
+    G2 = sdg.Grid(vs, 4096)
+    for T, d in views:
+        G2.activate_depth(d.cuda(), K, T, r)
+    assert set(map(tuple, G2.keys().cpu().numpy().tolist())) == set(map(tuple, ks.keys().tolist()))
+    # one block short of the batch: nothing is added
+    G3 = sdg.Grid(vs, len(first) - 1)
+    with pytest.raises(sdg.SdgError):
+        G3.activate_depth_frames(depth[:4].contiguous(), K, Tw[:4], r)
+    assert G3.num_blocks == 0
+
+
 def test_lookup_present_and_absent(sdg):
     sc = synth.scene_tiny_room(0)
     keys = synth.band_blocks(sc, 0.04, 3)
