@@ -38,3 +38,4 @@ def test_errors_without_gpu_work_are_reported():
     assert L.sdg_ctx_release(None) == A.OK
     assert L.sdg_server_destroy(None) == A.OK
     assert L.sdg_version().startswith(b"sdg")
+    assert L.sdg_grid_activate_depth_frames(None, None, 1, 4, 4, None, None, 1, None) == A.ERR_ARG

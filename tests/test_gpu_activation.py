@@ -94,6 +94,12 @@ def test_activate_depth_frames_is_one_batch(sdg):
     with pytest.raises(sdg.SdgError):
         G3.activate_depth_frames(depth[:4].contiguous(), K, Tw[:4], r)
     assert G3.num_blocks == 0
+    # a zero focal length in any frame is rejected before any work
+    Kb = np.tile(np.asarray(K, np.float64), (4, 1))
+    Kb[2, 0] = 0.0
+    with pytest.raises(sdg.SdgError):
+        G3.activate_depth_frames(depth[:4].contiguous(), Kb, Tw[:4], r)
+    assert G3.num_blocks == 0
 
 
 def test_lookup_present_and_absent(sdg):
