@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(kFuseThreads) k_fuse(FuseArgs a) {
         const float pv = __fadd_rn(__fmul_rn(c.fy, __fmul_rn(c1, rz)), c.cy);
         const float fu = floorf(pu), fv = floorf(pv);
         if (!(fu >= 0.f && fu < (float)a.W && fv >= 0.f && fv < (float)a.H)) continue;
-        const int64_t pix = (int64_t)i * HW + (int64_t)fv * a.W + (int64_t)fu;
+        // pixel within the frame in 32 bits (a frame holds < 2^31 pixels), frame offset in 64
+        const int64_t pix = (int64_t)i * HW + ((int)fv * a.W + (int)fu);
         const float D = __ldg(a.depth + pix);
         if (!(isfinite(D) && D > 0.f)) continue;
         const float o = __fsub_rn(D, c2);
