@@ -62,7 +62,7 @@ __device__ __forceinline__ bool lattice_simplex(const float* p, int d, Simplex& 
     for (int k = 0; k < d1; ++k) {
         const float q = __fdiv_rn(x[k], fd1);
         if (!(fabsf(q) < 5e7f)) return false;  // non-finite, or coordinates beyond the int32 lattice keys
-        const int qr = (int)llroundf(q);
+        const int qr = (int)roundf(q);  // half away from zero, exact in float for |q| < 5e7; 32-bit conversion
         S.r[k] = qr * d1;
         sum += qr;
         res[k] = __fsub_rn(x[k], (float)S.r[k]);
