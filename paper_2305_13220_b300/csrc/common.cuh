@@ -43,6 +43,19 @@ int cuda_fail(cudaError_t e, const char* what);
 #define SDG_KEY_BIAS (1 << 20)
 #define SDG_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
 
+// q = e / div and r = e - q div for 0 <= e, in 32-bit unsigned arithmetic whenever e fits (every practical
+// size; a 64-bit division is a long instruction sequence), else in 64 bits.
+__device__ __forceinline__ int64_t sdg_divmod(int64_t e, int div, int& r) {
+    if (e <= 0xFFFFFFFFll) {
+        const unsigned q = (unsigned)e / (unsigned)div;
+        r = (int)((unsigned)e - q * (unsigned)div);
+        return (int64_t)q;
+    }
+    const int64_t q = e / div;
+    r = (int)(e - q * div);
+    return q;
+}
+
 __host__ __device__ __forceinline__ uint64_t sdg_pack_key(int x, int y, int z) {
     return (uint64_t)(uint32_t)(x + SDG_KEY_BIAS) | ((uint64_t)(uint32_t)(y + SDG_KEY_BIAS) << 21) |
            ((uint64_t)(uint32_t)(z + SDG_KEY_BIAS) << 42);

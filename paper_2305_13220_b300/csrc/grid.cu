@@ -124,7 +124,8 @@ __global__ void k_candidates_depth(const float* __restrict__ depth, int H, int W
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float d = depth[i];
         if (!(isfinite(d) && d > 0.0f)) continue;
-        int u = (int)(i % W), v = (int)(i / W);
+        int u;
+        const int v = (int)sdg_divmod(i, W, u);
         float xc = __fmul_rn(__fmul_rn(__fadd_rn(__fadd_rn((float)u, 0.5f), -cam.cx), cam.fx_inv), d);
         float yc = __fmul_rn(__fmul_rn(__fadd_rn(__fadd_rn((float)v, 0.5f), -cam.cy), cam.fy_inv), d);
         float zc = d;

@@ -183,8 +183,8 @@ __global__ void __launch_bounds__(256) k_lat_insert(int64_t n, int d, Table t, c
     __syncthreads();
     const int d1 = d + 1;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * d1; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / d1;
-        const int j = (int)(e - i * d1);
+        int j;
+        const int64_t i = sdg_divmod(e, d1, j);
         if (sr[i * d1] == INT_MIN) {
             vslot[e] = -1;
             continue;
@@ -259,8 +259,8 @@ __global__ void __launch_bounds__(256, 8) k_lat_splat(const float* __restrict__ 
                             int* status) {
     const int d1 = d + 1;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * g4; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / g4;
-        const int g = (int)(e - i * g4);
+        int g;
+        const int64_t i = sdg_divmod(e, g4, g);
         float v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(256, 8) k_lat_neighbours(const int* __restrict
     }
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)M * d1;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = e / d1;
-        const int dir = (int)(e - m * d1);
+        int dir;
+        const int64_t m = sdg_divmod(e, d1, dir);
         unsigned long long lin = 0, lin2 = 0;
         for (int k = 0; k < d; ++k) {
             const unsigned long long ck = (unsigned long long)(long long)keys[m * d + k];
@@ -327,8 +327,8 @@ __global__ void k_lat_blur(const float4* __restrict__ src, float4* __restrict__ 
     const int d1 = d + 1;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)M * g4;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = e / g4;
-        const int g = (int)(e - m * g4);
+        int g;
+        const int64_t m = sdg_divmod(e, g4, g);
         const int2 pr = *reinterpret_cast<const int2*>(nb + (m * d1 + dir) * 2);
         const float4 a = src[e];
         float4 r = make_float4(2.f * a.x, 2.f * a.y, 2.f * a.z, 2.f * a.w);
@@ -358,8 +358,8 @@ __global__ void k_lat_slice(const float4* __restrict__ lat, const int* __restric
     const int d1 = d + 1;
     const int gh = c >> 2, uh = c & 3;  // group and lane of the homogeneous channel
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * g4; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / g4;
-        const int g = (int)(e - i * g4);
+        int g;
+        const int64_t i = sdg_divmod(e, g4, g);
         if (4 * g >= c) continue;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         float hom = 0.f;

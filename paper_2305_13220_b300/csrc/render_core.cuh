@@ -440,7 +440,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     }
     const float s_after = __shfl_down_sync(kFull, s_[0], 1);  // first sample of the next lane
 
-    float t_[Q], dl_[Q], d_[Q], cr_[Q], cg_[Q], cb_[Q], tau_[Q], dsig_[Q];
+    float t_[Q] = {}, dl_[Q], d_[Q], cr_[Q], cg_[Q], cb_[Q], tau_[Q], dsig_[Q];
     int blk_[Q], lc_[Q];
     float bq_[kBeta ? Q : 1];
     float gnx_[kNrm ? Q : 1], gny_[kNrm ? Q : 1], gnz_[kNrm ? Q : 1];  // grad f at the samples (Eq. 17)
