@@ -90,6 +90,29 @@ def test_bf16_grid_with_logits_matches_oracle(sdg):
     assert torch.all(G.channel(A.GROUP_SEM, A.KIND_GRAD)[:N] == 0)
 
 
+def test_misaligned_logit_frames_take_the_scalar_path(sdg):
+    """Logit frames that are not 16-byte aligned (a view at a 4-byte offset) are read channel by channel; the
+    result is bit-identical to the float4 path on an aligned copy (same per-channel summation order)."""
+    sc = synth.scene_tiny_room(1)
+    ns = 8
+    keys = synth.band_blocks(sc, VS, BAND)
+    fr, P, K = frames(sc, 3, seed=11, n_sem=ns)
+    sem = fr["sem"]
+    buf = torch.empty(sem.numel() + 1, device="cuda")
+    mis = buf[1:].view(sem.shape)
+    mis.copy_(sem)
+    assert mis.data_ptr() % 16 != 0 and mis.is_contiguous()
+    out = []
+    for s_in in (sem, mis):
+        G, gk = fresh_grid(sdg, keys, rgb_dtype="bf16", n_sem=ns)
+        G.fuse(fr["depth"], K, P, MU, rgb=fr["rgb"], sem=s_in)
+        G.fuse_finalize()
+        torch.cuda.synchronize()
+        out.append(G.channel(sdg._abi.GROUP_SEM)[:len(gk)].float().cpu())
+    assert torch.equal(out[0], out[1])
+    assert out[0].abs().sum() > 0
+
+
 def test_more_frames_than_one_launch_holds(sdg):
     """1100 small frames: the call is split into launches of at most 1024 frames."""
     sc = synth.scene_tiny_room(2)
