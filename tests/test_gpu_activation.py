@@ -84,6 +84,16 @@ def test_activate_depth_frames_is_one_batch(sdg):
     assert G.activate_depth_frames(depth[4:].contiguous(), K, Tw[4:], r) == len(second)
     np.testing.assert_array_equal(G.keys().cpu().numpy(), np.concatenate([first, second]))
     assert G.activate_depth_frames(depth[:0], K, Tw[:0], r) == 0
+    # per-frame intrinsics: each frame unprojected with its own K, as map-by-map calls do
+    Kf = np.tile(np.asarray(K, np.float64), (6, 1))
+    Kf[1, 0] *= 1.25
+    Kf[3, 1] *= 0.8
+    Kf[4, 2] += 3.0
+    Ga, Gb = sdg.Grid(vs, 4096), sdg.Grid(vs, 4096)
+    Ga.activate_depth_frames(depth, Kf, Tw, r)
+    for f, (T, d) in enumerate(views):
+        Gb.activate_depth(d.cuda(), Kf[f], T, r)
+    assert set(map(tuple, Ga.keys().cpu().numpy().tolist())) == set(map(tuple, Gb.keys().cpu().numpy().tolist()))
     # map by map: the same set
     G2 = sdg.Grid(vs, 4096)
     for T, d in views:

@@ -84,6 +84,19 @@ def test_eikonal_matches_oracle(room):
     assert total2.item() == total.item()
 
 
+def test_ragged_sizes_match_the_large_batch(room):
+    """One point and 300 points (less than one wave of CTAs) give exactly what the same points give inside a batch
+    of 20,000 (a grid of one resident wave, each thread looping)."""
+    sdg, G, O, gk = room
+    x = torch.as_tensor(points(gk, 20000, 4)[:-3], device="cuda")
+    f_all, g_all = G.query(x)
+    for m in (1, 300):
+        f, g = G.query(x[:m].contiguous())
+        torch.cuda.synchronize()
+        assert torch.equal(torch.nan_to_num(f, nan=-7.0), torch.nan_to_num(f_all[:m], nan=-7.0))
+        assert torch.equal(torch.nan_to_num(g, nan=-7.0), torch.nan_to_num(g_all[:m], nan=-7.0))
+
+
 def test_empty_and_rejected_calls(room):
     sdg, G, O, gk = room
     empty = torch.zeros((0, 3), device="cuda")
