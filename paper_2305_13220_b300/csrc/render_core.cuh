@@ -554,10 +554,10 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             rec[5 * CS] = __int_as_float(blk_[i]);
         }
     };
-    // The fused training modes, and the forward modes with 6 or more samples per lane, place all samples first
-    // and then reuse a cell's corners for the lane's next sample in it (about half of the samples); elsewhere
-    // holding the corners costs more registers than the loads it saves.
-    if constexpr (kTrain || (kFwdOut && Q >= 6)) {
+    // The fused training and the forward modes place all samples first and then reuse a cell's corners for the
+    // lane's next sample in it (about half of the samples); the separate backward passes keep the single
+    // place-and-fetch loop, where holding the corners costs more registers than the loads it saves.
+    if constexpr (kTrain || kFwdOut) {
         unsigned pmask = 0;  // samples placed
 #pragma unroll
         for (int i = 0; i < Q; ++i)

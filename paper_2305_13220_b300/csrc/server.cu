@@ -44,9 +44,10 @@ struct ChunkDesc {
     int32_t strat;
 };
 
+// 3 CTAs per SM at 4 samples per lane (80 registers), 2 above
 template <bool BF16, int Q>
-__global__ void __launch_bounds__(256) k_serve(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks,
-                                               int chunk_rays) {
+__global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
+    k_serve(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks, int chunk_rays) {
     __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
