@@ -96,7 +96,8 @@ typedef struct {
     float voxel_size;   /* metres, > 0 */
     float beta;         /* Laplace scale of the SDF-to-density transform (Sec. 3.5.1), metres;
                            <= 0 selects voxel_size / 2 */
-    int64_t max_blocks; /* block capacity; every per-block array is allocated for it up front */
+    int64_t max_blocks; /* block capacity, at most 2^22 (voxel addresses are 32-bit in the kernels); every
+                           per-block array is allocated for it up front */
     int32_t rgb_dtype;  /* SDG_F32 or SDG_BF16 */
     int32_t n_sem;      /* semantic channels per voxel: 0 or a multiple of 4, at most 32 */
     int32_t device;     /* CUDA device ordinal */

@@ -61,6 +61,8 @@ extern "C" const char* sdg_version(void) { return "sdg 0.1 (sm_103a)"; }
 namespace {
 
 constexpr int kThreads = 256;
+// Largest block capacity: the render and query kernels form voxel addresses (block * 512 + local) in 32 bits.
+constexpr int64_t kMaxBlocks = 1ll << 22;
 
 __device__ __forceinline__ int floordiv8(int v) { return v >> 3; }  // arithmetic shift = floor division
 
@@ -336,6 +338,7 @@ void free_grid_buffers(sdg_grid g) {
     void* ptrs[] = {g->table, g->tmp_table, g->keys, g->nbr, g->dense, g->geo, g->ggeo, g->m_geo, g->v_geo,
                     g->sdf, g->gsdf, g->m_sdf, g->v_sdf, g->rgbh, g->grgb, g->m_rgb, g->v_rgb, g->sem, g->gsem,
                     g->m_sem, g->v_sem, g->weight, g->sort_buf, g->counters, g->minmax, g->loss_buf,
+                    g->walk_hdr, g->walk_s0, g->walk_rec,
                     g->order_keys, g->order_perm, g->order_hist, g->fuse_cams, g->beta_grad, g->beta_part,
                     g->ssi_dev, g->lat.fp, g->lat.idx, g->lat.skey, g->lat.keys, g->lat.vidx, g->lat.vbary,
                     g->lat.val0, g->lat.val1, g->lat.nb, g->lat.counters, g->lat.fq, g->lat.sr, g->lat.srank,
@@ -494,7 +497,7 @@ int begin_activation(sdg_grid g) {
 extern "C" int sdg_grid_create(const sdg_grid_desc* d, sdg_grid* out) {
     if (!d || !out) return fail(SDG_ERR_ARG, "sdg_grid_create: null argument");
     *out = nullptr;
-    if (!(d->voxel_size > 0.f) || d->max_blocks <= 0 || d->max_blocks > (1ll << 30) ||
+    if (!(d->voxel_size > 0.f) || d->max_blocks <= 0 || d->max_blocks > kMaxBlocks ||
         (d->rgb_dtype != SDG_F32 && d->rgb_dtype != SDG_BF16) || d->n_sem < 0 || d->n_sem > 32 || d->n_sem % 4 ||
         d->reserved != 0)
         return fail(SDG_ERR_ARG, "sdg_grid_create: invalid descriptor");

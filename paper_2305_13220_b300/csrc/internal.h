@@ -66,6 +66,11 @@ struct sdg_grid_s {
     int* h_minmax = nullptr;                   // pinned host [6]
     float* loss_buf = nullptr;                 // per-ray loss scratch of the fused training pass
     int64_t loss_cap = 0;
+    // records of the traversal pass (k_walk) for up to walk_cap rays: header, skip-space offsets, cell records
+    int2* walk_hdr = nullptr;
+    float* walk_s0 = nullptr;
+    int4* walk_rec = nullptr;
+    int64_t walk_cap = 0;
     int* order_keys = nullptr;  // surface ordering of a training batch: per-ray bucket [order_cap]
     int* order_perm = nullptr;  // processing order [order_cap]
     int* order_hist = nullptr;  // bucket counts, then offsets [kOrderBuckets]

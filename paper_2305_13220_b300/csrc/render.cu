@@ -76,6 +76,77 @@ PassArgs base_args(const sdg_render_opts* o, int64_t n) {
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // ---------------------------------------------------------------------------
+// Traversal pass (Sec. 3.5.1: samples only where blocks are allocated): one thread walks the whole ray through
+// the dense block-index grid and writes the allocated cells it crosses, in order, with their skip-space offsets.
+// A warp of the render kernel then places its ray's samples by a binary search over these records instead of
+// walking the ray itself (a ray crossing more than kWalkCap allocated cells keeps the in-warp traversal).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_walk(GridDev g, const float* __restrict__ rays, const int* __restrict__ perm,
+                                              int64_t n, WalkBufs w) {
+    const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= n) return;
+    const int64_t r = perm ? (int64_t)__ldg(perm + slot) : slot;
+    const float4 r0 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r);
+    const float4 r1 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r + 1);
+    const float3 o = make_float3(r0.x, r0.y, r0.z), d = make_float3(r1.x, r1.y, r1.z);
+    float t0 = r0.w, t1 = r1.w;
+    int cnt = 0;
+    float S = 0.f;
+    if (clip_to_grid(g, o, d, t0, t1)) {
+        const float3 invd = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+        float* s0 = w.s0 + slot * kWalkCap;
+        int4* rec = w.rec + slot * kWalkCap;
+        walk_cells(g, o, d, invd, t0, t1, [&](float x0, float x1, int cell, int blk) {
+            if (cnt == kWalkCap) {
+                cnt = -1;  // more cells than records: the render warp walks this ray itself
+                return false;
+            }
+            const float len = x1 - x0;
+            s0[cnt] = S;
+            rec[cnt] = make_int4(__float_as_int(x0), __float_as_int(len), blk, cell);
+            S += len;
+            ++cnt;
+            return true;
+        });
+    }
+    w.hdr[slot] = make_int2(cnt, __float_as_int(S));
+}
+
+// Grows the grid-owned walk records to n rays (valid until the next call on this grid).
+int walk_scratch(sdg_grid g, int64_t n) {
+    if (g->walk_cap >= n) return SDG_OK;
+    if (g->walk_hdr || g->walk_s0 || g->walk_rec) {
+        SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));  // earlier work on the stream may still read them
+        cudaFree(g->walk_hdr);
+        cudaFree(g->walk_s0);
+        cudaFree(g->walk_rec);
+    }
+    g->walk_hdr = nullptr;
+    g->walk_s0 = nullptr;
+    g->walk_rec = nullptr;
+    g->walk_cap = 0;
+    SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_hdr, sizeof(int2) * n));
+    SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_s0, sizeof(float) * kWalkCap * n));
+    SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_rec, sizeof(int4) * kWalkCap * n));
+    g->walk_cap = n;
+    return SDG_OK;
+}
+
+// Enqueues the traversal pass of n rays (processing order perm, or the given order) and points a.walk at its
+// records.
+int walk_rays(sdg_grid g, const float* rays, const int* perm, int64_t n, PassArgs& a) {
+    a.walk = WalkBufs{nullptr, nullptr, nullptr};
+    if (n == 0) return SDG_OK;
+    int rc = walk_scratch(g, n);
+    if (rc) return rc;
+    const WalkBufs w{g->walk_hdr, g->walk_s0, g->walk_rec};
+    k_walk<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(g->dev(), rays, perm, n, w);
+    SDG_LAUNCH_CHECK("traversal pass");
+    a.walk = w;
+    return SDG_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Losses
 // ---------------------------------------------------------------------------
 __global__ void k_loss_l1(int64_t n, int ns, const float* __restrict__ rgb, const float* __restrict__ depth,
@@ -202,9 +273,11 @@ extern "C" int sdg_render_forward(sdg_grid g, const float* rays, int64_t n, cons
         }
         a.rec = rec;
         a.rec_S = rec_S;
-        rc = launch_pass<PASS_FWD_STORE>(g, rays, o->ray_id0, a);
+        rc = walk_rays(g, rays, nullptr, n, a);
+        if (!rc) rc = launch_pass<PASS_FWD_STORE>(g, rays, o->ray_id0, a);
     } else {
-        rc = launch_pass<PASS_FWD>(g, rays, o->ray_id0, a);
+        rc = walk_rays(g, rays, nullptr, n, a);
+        if (!rc) rc = launch_pass<PASS_FWD>(g, rays, o->ray_id0, a);
     }
     if (rc) {
         if (rec) cudaFreeAsync(rec, g->stream);
@@ -240,6 +313,7 @@ extern "C" int sdg_render_backward(sdg_ctx c, const float* g_rgb, const float* g
         a.rec_S = c->rec_S;
         return launch_pass<PASS_BWD_STORE>(g, c->rays, c->opts.ray_id0, a);
     }
+    if ((rc = walk_rays(g, c->rays, nullptr, c->n, a))) return rc;  // the forward's records, recomputed
     return launch_pass<PASS_BWD>(g, c->rays, c->opts.ray_id0, a);
 }
 
@@ -300,6 +374,7 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
     if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
         if ((rc = order_rays_by_surface(g, rays, tdepth, n, &a.perm))) return rc;
     }
+    if ((rc = walk_rays(g, rays, a.perm, n, a))) return rc;
     if (lo->learn_beta) {
         if (g->beta_part_cap < n) {
             if (g->beta_part) {
@@ -361,6 +436,7 @@ extern "C" int sdg_train_step_rays_normal(sdg_grid g, const float* rays, int64_t
     if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
         if ((rc = order_rays_by_surface(g, rays, tdepth, n, &a.perm))) return rc;
     }
+    if ((rc = walk_rays(g, rays, a.perm, n, a))) return rc;
     rc = launch_pass_nosem<PASS_TRAIN_NRM>(g, rays, o->ray_id0, a);
     if (rc) return rc;
     if (loss_sum) {

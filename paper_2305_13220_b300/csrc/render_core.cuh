@@ -45,6 +45,19 @@ enum PassMode {
     PASS_TRAIN_NRM = 6  // PASS_TRAIN plus the normal loss of Eq. 14 on the rendered normal sum_k w_k grad f(x_k)
 };
 
+// Allocated block cells of a ray kept in the walk records; a ray crossing more takes the in-warp traversal.
+constexpr int kWalkCap = 32;
+
+// Output of k_walk, indexed by processing slot: hdr[slot] = {number of records (-1: more than kWalkCap),
+// bits of S}; record m of the slot at [slot * kWalkCap + m]: s0 = skip-space offset of the cell (sequential FP32
+// sum of the lengths before it, so the offsets are monotone and S = s0 + len of the last), and
+// rec = {bits of t_in, bits of len, block index, dense-grid cell}.
+struct WalkBufs {
+    int2* hdr;
+    float* s0;
+    int4* rec;
+};
+
 // Store-mode record channels per sample: t, sdf (NaN if invalid), r, g, b, block index (int bits).
 constexpr int kRecChannels = 6;
 
@@ -65,13 +78,15 @@ struct PassArgs {
     float* beta_part;  // PASS_TRAIN_BETA: dL/dbeta of each ray [n]
     const float* t_normal;  // PASS_TRAIN_NRM: target normals [n][3] (world frame)
     float lam_n;
+    WalkBufs walk;  // records of the traversal pass (hdr NULL: every warp walks its ray itself)
 };
 
 struct RayJob {
     float3 o, d;
     float tn, tf;
     uint32_t ray_id;
-    int64_t idx;  // row of this ray in per-ray arrays
+    int64_t idx;   // row of this ray in per-ray arrays
+    int64_t slot;  // processing slot (row of the walk records)
 };
 
 // Per-warp shared memory: the allocated cells of each lane piece (m-major so a
@@ -80,7 +95,7 @@ struct WarpSmem {
     float tin[kSegs][32];
     float len[kSegs][32];
     int blk[kSegs][32];
-    unsigned long long key[kSegs][32];
+    int cell[kSegs][32];  // dense block-index grid cell of the record's block
     float P[33];
     int cnt[32];
 };
@@ -118,7 +133,9 @@ __device__ __forceinline__ bool clip_to_grid(const GridDev& g, const float3& o, 
     const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float lo = (float)g.bmin[a] * g.L, hi = (float)(g.bmin[a] + g.bdim[a]) * g.L;
+        // products rounded on their own (no contraction into the subtraction below), so that every kernel that
+        // walks a ray gets the same bits
+        const float lo = __fmul_rn((float)g.bmin[a], g.L), hi = __fmul_rn((float)(g.bmin[a] + g.bdim[a]), g.L);
         if (dd[a] == 0.0f) {
             if (oo[a] < lo || oo[a] > hi) return false;
             continue;
@@ -132,8 +149,23 @@ __device__ __forceinline__ bool clip_to_grid(const GridDev& g, const float3& o, 
 }
 
 
-// Calls f(a, b, key, blk) for every allocated block cell the ray crosses inside
-// [ta, tb), in order of increasing t, with [a, b) its stretch of the ray.
+// Cell of the dense block-index grid holding block (bx, by, bz), -1 if it lies outside the AABB.
+__device__ __forceinline__ int dense_cell(const GridDev& g, int bx, int by, int bz) {
+    const unsigned x = (unsigned)(bx - g.bmin[0]), y = (unsigned)(by - g.bmin[1]), z = (unsigned)(bz - g.bmin[2]);
+    if (x >= (unsigned)g.bdim[0] || y >= (unsigned)g.bdim[1] || z >= (unsigned)g.bdim[2]) return -1;
+    return (int)((z * (unsigned)g.bdim[1] + y) * (unsigned)g.bdim[0] + x);  // < 2^31 cells
+}
+
+// Index of the block at block coordinates (bx, by, bz), -1 if it is not allocated (or outside the AABB).
+__device__ __forceinline__ int block_at(const GridDev& g, int bx, int by, int bz) {
+    const int c = dense_cell(g, bx, by, bz);
+    return c < 0 ? -1 : __ldg(g.dense + c);
+}
+
+// Calls f(a, b, cell, blk) for every allocated block cell the ray crosses inside [ta, tb), in order of
+// increasing t, with [a, b) its stretch of the ray and cell its index in the dense block-index grid; the walk
+// stops early when f returns false.  Block-level Amanatides-Woo: the exit time of a cell is the smallest of its
+// three face-plane times, each formed as one fused multiply-add and a product (the same bits in every kernel).
 template <class F>
 __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, const float3& d, const float3& invd,
                                            float ta, float tb, F&& f) {
@@ -148,36 +180,36 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
     const int sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
     const int sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
     const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
+    // index steps of the dense grid (x fastest)
+    const int stx = sx, sty = sy * g.bdim[0], stz = sz * (int)((unsigned)g.bdim[0] * (unsigned)g.bdim[1]);
     float tcur = ta;
     const int maxit = g.bdim[0] + g.bdim[1] + g.bdim[2] + 3;
+    int cidx = (cz * g.bdim[1] + cy) * g.bdim[0] + cx;
     // the next cell's block index is loaded before the current cell is handed to f, so the loads of successive
     // cells overlap instead of each waiting for the previous one
-    int blk = __ldg(g.dense + ((int64_t)cz * g.bdim[1] + cy) * (int64_t)g.bdim[0] + cx);
+    int blk = __ldg(g.dense + cidx);
     for (int it = 0; it < maxit; ++it) {
-        const float tx = sx ? ((float)(g.bmin[0] + cx + (sx > 0)) * g.L - o.x) * invd.x : INF;
-        const float ty = sy ? ((float)(g.bmin[1] + cy + (sy > 0)) * g.L - o.y) * invd.y : INF;
-        const float tz = sz ? ((float)(g.bmin[2] + cz + (sz > 0)) * g.L - o.z) * invd.z : INF;
+        const float tx = sx ? fmaf((float)(g.bmin[0] + cx + (sx > 0)), g.L, -o.x) * invd.x : INF;
+        const float ty = sy ? fmaf((float)(g.bmin[1] + cy + (sy > 0)), g.L, -o.y) * invd.y : INF;
+        const float tz = sz ? fmaf((float)(g.bmin[2] + cz + (sz > 0)), g.L, -o.z) * invd.z : INF;
         const float te = fminf(tx, fminf(ty, tz));
         const float b = fminf(te, tb);
-        const int nx = cx + (tx == te ? sx : 0), ny = cy + (ty == te ? sy : 0), nz = cz + (tz == te ? sz : 0);
+        const bool mx = tx == te, my = ty == te, mz = tz == te;
+        const int nx = cx + (mx ? sx : 0), ny = cy + (my ? sy : 0), nz = cz + (mz ? sz : 0);
         const bool more = te < tb && (unsigned)nx < (unsigned)g.bdim[0] && (unsigned)ny < (unsigned)g.bdim[1] &&
                           (unsigned)nz < (unsigned)g.bdim[2];
-        const int nblk = more ? __ldg(g.dense + ((int64_t)nz * g.bdim[1] + ny) * (int64_t)g.bdim[0] + nx) : -1;
-        if (b > tcur && blk >= 0) f(tcur, b, sdg_pack_key(g.bmin[0] + cx, g.bmin[1] + cy, g.bmin[2] + cz), blk);
+        const int nidx = cidx + (mx ? stx : 0) + (my ? sty : 0) + (mz ? stz : 0);
+        const int nblk = more ? __ldg(g.dense + nidx) : -1;
+        if (b > tcur && blk >= 0)
+            if (!f(tcur, b, cidx, blk)) break;
         if (!more) break;
         cx = nx;
         cy = ny;
         cz = nz;
+        cidx = nidx;
         blk = nblk;
         tcur = fmaxf(te, ta);
     }
-}
-
-// Index of the block at block coordinates (bx, by, bz), -1 if it is not allocated (or outside the AABB).
-__device__ __forceinline__ int block_at(const GridDev& g, int bx, int by, int bz) {
-    const unsigned x = (unsigned)(bx - g.bmin[0]), y = (unsigned)(by - g.bmin[1]), z = (unsigned)(bz - g.bmin[2]);
-    if (x >= (unsigned)g.bdim[0] || y >= (unsigned)g.bdim[1] || z >= (unsigned)g.bdim[2]) return -1;
-    return __ldg(g.dense + ((int64_t)z * g.bdim[1] + y) * (int64_t)g.bdim[0] + x);
 }
 
 struct Pieces {
@@ -205,15 +237,16 @@ __device__ __forceinline__ float walk_pieces(const GridDev& g, const RayJob& j, 
         pc.t0 = t0;
         pc.dt = (t1 - t0) * (1.0f / 32.0f);
         const float ta = piece_start(pc, lane), tb = piece_end(pc, t1, lane);
-        walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, uint64_t key, int blk) {
+        walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, int cell, int blk) {
             if (cnt < kSegs) {
                 sm.tin[cnt][lane] = x0;
                 sm.len[cnt][lane] = x1 - x0;
                 sm.blk[cnt][lane] = blk;
-                sm.key[cnt][lane] = key;
+                sm.cell[cnt][lane] = cell;
             }
             ++cnt;
             S_j += x1 - x0;
+            return true;
         });
     }
     t1_out = t1;
@@ -233,9 +266,9 @@ __device__ __forceinline__ float walk_pieces(const GridDev& g, const RayJob& j, 
     return S;
 }
 
-// t, block index and block key of skip-space position s (0 <= s < S).
+// t, block index and dense-grid cell of skip-space position s (0 <= s < S), from the lane pieces' records.
 __device__ __forceinline__ float locate(const GridDev& g, const RayJob& j, const WarpSmem& sm, const Pieces& pc,
-                                        float t1, float s, int& blk, uint64_t& key) {
+                                        float t1, float s, int& blk, int& cell) {
     int jp = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1)
@@ -250,31 +283,46 @@ __device__ __forceinline__ float locate(const GridDev& g, const RayJob& j, const
             local -= l;
         }
         blk = sm.blk[m][jp];
-        key = sm.key[m][jp];
+        cell = sm.cell[m][jp];
         return sm.tin[m][jp] + fminf(local, sm.len[m][jp]);
     }
     // the piece had more allocated cells than were recorded: walk it again
     float ta = piece_start(pc, jp), tb = piece_end(pc, t1, jp);
-    float t = ta, best_a = ta, best_len = 0.f;
-    uint64_t best_key = SDG_EMPTY_KEY;
-    bool found = false;
-    int best_blk = -1;
-    walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, uint64_t k, int kb) {
-        if (found) return;
+    float best_a = ta, best_len = 0.f;
+    int best_cell = -1, best_blk = -1;
+    walk_cells(g, j.o, j.d, pc.invd, ta, tb, [&](float x0, float x1, int c, int kb) {
         best_a = x0;
         best_len = x1 - x0;
-        best_key = k;
+        best_cell = c;
         best_blk = kb;
-        if (local < best_len) {
-            found = true;
-            return;
-        }
+        if (local < best_len) return false;
         local -= best_len;
+        return true;
     });
-    t = best_a + fminf(local, best_len);
-    key = best_key;
+    cell = best_cell;
     blk = best_blk;
-    return t;
+    return best_a + fminf(local, best_len);
+}
+
+// ---------------------------------------------------------------------------
+// Traversal as its own pass: one thread walks a whole ray
+// ---------------------------------------------------------------------------
+// Record m of the lane-distributed walk records (lane m holds record m): the largest m with s0[m] <= s, found by
+// a binary search over the lanes' offsets.  Every lane of the warp must call it (it shuffles).
+__device__ __forceinline__ float locate_rec(int n_rec, float my_s0, const int4& my_rec, float s, int& blk,
+                                            int& cell) {
+    int m = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const float v = __shfl_sync(kFull, my_s0, m + step);
+        if (m + step < n_rec && v <= s) m += step;
+    }
+    const float s0 = __shfl_sync(kFull, my_s0, m);
+    const float tin = __int_as_float(__shfl_sync(kFull, my_rec.x, m));
+    const float len = __int_as_float(__shfl_sync(kFull, my_rec.y, m));
+    blk = __shfl_sync(kFull, my_rec.z, m);
+    cell = __shfl_sync(kFull, my_rec.w, m);
+    return tin + fminf(s - s0, len);
 }
 
 // ---------------------------------------------------------------------------
@@ -419,10 +467,27 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     Pieces pc;
     float t1 = 0.f;
     float S;
+    // walk records of this ray (lane m holds record m), when the traversal ran as its own pass
+    bool by_rec = false;
+    int n_rec = 0;
+    float my_s0 = 0.f;
+    int4 my_rec = make_int4(0, 0, -1, -1);
     if constexpr (kStoreIn) {
         S = a.rec_S[j.idx];
     } else {
-        S = walk_pieces(g, j, sm, lane, pc, t1);
+        if (a.walk.hdr) {
+            const int2 h = __ldg(a.walk.hdr + j.slot);
+            if (h.x >= 0) {  // warp-uniform
+                by_rec = true;
+                n_rec = h.x;
+                S = __int_as_float(h.y);
+                if (lane < n_rec) {
+                    my_s0 = __ldg(a.walk.s0 + j.slot * kWalkCap + lane);
+                    my_rec = __ldg(a.walk.rec + j.slot * kWalkCap + lane);
+                }
+            }
+        }
+        if (!by_rec) S = walk_pieces(g, j, sm, lane, pc, t1);
     }
     if constexpr (kStoreOut) {
         if (lane == 0) a.rec_S[j.idx] = S;
@@ -464,14 +529,19 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         if constexpr (kBeta) bq_[i] = 0.f;
         if constexpr (kNrm) gnx_[i] = gny_[i] = gnz_[i] = 0.f;
         blk_[i] = -1; lc_[i] = 0;
-        if (!any || k >= N) return false;
+        if (!any) return false;  // warp-uniform
+        int blk = -1, cell = -1;
+        float t_rec = 0.f;
+        if constexpr (!kStoreIn) {
+            // every lane takes part in the record search (it shuffles), with or without a sample i
+            if (by_rec) t_rec = locate_rec(n_rec, my_s0, my_rec, k < N ? s_[i] : 0.f, blk, cell);
+        }
+        if (k >= N) return false;
         float sn;
         if (k + 1 >= N) sn = S;
         else if (i + 1 < Q) sn = s_[i + 1 < Q ? i + 1 : i];
         else sn = s_after;
         dl_[i] = sn - s_[i];
-        int blk = -1;
-        uint64_t key = SDG_EMPTY_KEY;
         if constexpr (kStoreIn) {
             const float* rec = a.rec + j.idx * RS + i * 32 + lane;
             const int64_t CS = a.n * RS;
@@ -483,7 +553,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             blk = __float_as_int(rec[5 * CS]);
             if (!isnan(d_[i])) smask |= 1u << i;
         } else {
-            t_[i] = locate(g, j, sm, pc, t1, s_[i], blk, key);
+            t_[i] = by_rec ? t_rec : locate(g, j, sm, pc, t1, s_[i], blk, cell);
         }
         const float px = fmaf(t_[i], j.d.x, j.o.x) * g.inv_vs;
         const float py = fmaf(t_[i], j.d.y, j.o.y) * g.inv_vs;
@@ -493,8 +563,8 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         lc_[i] = (cx & 7) | ((cy & 7) << 3) | ((cz & 7) << 6);
         if constexpr (!kStoreIn) {
             // the sample's own block: the traversal cell's, unless rounding put it across a block face
-            const uint64_t own = sdg_pack_key(cx >> 3, cy >> 3, cz >> 3);
-            if (own != key) blk = block_at(g, cx >> 3, cy >> 3, cz >> 3);
+            const int own = dense_cell(g, cx >> 3, cy >> 3, cz >> 3);
+            if (own != cell) blk = own < 0 ? -1 : __ldg(g.dense + own);
         }
         blk_[i] = blk;
         return true;

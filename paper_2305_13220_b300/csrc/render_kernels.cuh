@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>()))
     j.tf = r1.w;
     j.ray_id = ray_id0 + (uint32_t)r;
     j.idx = r;
+    j.slot = slot;
     ray_program<MODE, BF16, SEM, Q>(g, a, j, smem[warp], lane);
 }
 

@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
     j.tf = ch.tfar;
     j.ray_id = (uint32_t)pix;
     j.idx = pix;
+    j.slot = 0;  // no walk records: the warp walks its ray
     PassArgs a{};
     a.N = ch.N;
     a.seed = ch.seed;
