@@ -235,6 +235,54 @@ int sdg_render_forward(sdg_grid g, const float* rays_dev, int64_t n, const sdg_r
 int sdg_render_backward(sdg_ctx ctx, const float* g_rgb_dev, const float* g_depth_dev, const float* g_opac_dev,
                         const float* g_sem_dev);
 
+/* Debug export of where a render placed every sample (Sec. 3.5.1: the
+ * allocated stretches, S, and the samples t_k mapped back from skip space;
+ * Eq. 17: the trilinear cell of each sample).  It runs the forward pass with
+ * the same traversal and placement code as the other passes and writes, for
+ * each ray i (row i of rays_dev) and sample k, to device buffers:
+ *   n_cells [n]      allocated block cells in the ray's traversal record, or -1
+ *                    when the ray crossed more than SDG_TRACE_CELLS of them and
+ *                    its warp walked it itself (or walk = SDG_WALK_IN_WARP);
+ *   S [n]            total allocated length (0: the ray meets no block);
+ *   t [n][N]         ray parameter t_k of sample k;
+ *   cell [n][N][3]   voxel coordinates of the base corner of the sample's cell
+ *                    (floor of x / voxel_size, decided in FP32);
+ *   block [n][N]     index of the block holding that corner, -1 if none;
+ *   valid [n][N]     1 if all 8 corners of the cell are allocated;
+ *   seg [n][SDG_TRACE_CELLS][2]  (may be NULL) t_in and length of each
+ *                    recorded cell, in order (first n_cells[i] entries);
+ *   rgb, depth, opac forward outputs, as sdg_render_forward.
+ * Samples of a ray with S = 0 read t = 0, cell = 0, block = -1, valid = 0.
+ * walk: SDG_WALK_PASS (the traversal pass used by sdg_render_forward,
+ * sdg_render_backward and the training passes) or SDG_WALK_IN_WARP (the
+ * in-warp traversal used by the serving loop and the allocation-free pass).
+ * Asynchronous on the grid's stream.  Errors: SDG_ERR_ARG (null or
+ * misaligned buffer, bad walk), SDG_ERR_OOM, SDG_ERR_CUDA. */
+#define SDG_TRACE_CELLS 32
+#define SDG_WALK_PASS 0
+#define SDG_WALK_IN_WARP 1
+typedef struct {
+    int32_t* n_cells;
+    float* S;
+    float* t;
+    int32_t* cell;
+    int32_t* block;
+    uint8_t* valid;
+    float* seg;
+    float *rgb, *depth, *opac;
+} sdg_trace_out;
+int sdg_debug_trace(sdg_grid g, const float* rays_dev, int64_t n, const sdg_render_opts* opts, int32_t walk,
+                    const sdg_trace_out* out);
+
+/* Same export for the H x W pinhole view that the serving loop renders for a
+ * request (K = {fx, fy, cx, cy}, T row-major 3x4 camera-to-world, host
+ * arrays; pixel (u, v) is ray v * W + u, its direction normalised): the rays
+ * are formed by the serving kernel's own code and walked in-warp as it walks
+ * them, so the outputs equal the served request's bit for bit.  rays_out
+ * [H*W][8] (device) receives the rays {o, tnear, d, tfar}. */
+int sdg_debug_trace_view(sdg_grid g, int32_t H, int32_t W, const float K[4], const float T[12], float tnear,
+                         float tfar, const sdg_render_opts* opts, float* rays_out_dev, const sdg_trace_out* out);
+
 /* Releases a context (enqueues the release of its device memory).  Safe on NULL. */
 int sdg_ctx_release(sdg_ctx ctx);
 

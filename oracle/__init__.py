@@ -91,14 +91,14 @@ def _declare(L):
         "orc_query_grad": (None, [_p, _p, _i64, _p, _p, _p]),
         "orc_eikonal": (_d, [_p, _p, _i64, _d, _p, _p]),
         "orc_crf_loss": (_d, [_p, C.c_int, _p, _i64, _p, _d, _p, _p]),
-        "orc_render": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p]),
+        "orc_render": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p]),
         "orc_loss_normal": (_d, [_i64, _p, _p, _d, _p]),
         "orc_lattice_simplex": (None, [_p, C.c_int, _p, _p]),
         "orc_lattice_filter": (_i64, [_i64, C.c_int, _p, C.c_int, _p, _p, C.c_int]),
         "orc_crf_meanfield": (None, [_i64, C.c_int, _p, C.c_int, _p, _p, _d, _p]),
         "orc_trace": (C.c_int, [_p, _p, C.c_int, _u32, _u32, C.c_int, _p]),
         "orc_render_backward": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p, _p, _p, _p, _p, _p,
-                                       _p, _p, _p]),
+                                       _p, _p, _p, _p, _p, _p]),
         "orc_depth_ssi": (_d, [_i64, _p, _p, _d, _p, _p]),
         "orc_count_touched": (None, [_p, _p, _i64, C.c_int, _u32, _u32, C.c_int, _p, _p]),
         "orc_loss": (_d, [_i64, C.c_int, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p]),
@@ -260,9 +260,14 @@ class Grid:
                                terms.ctypes.data)
         return L, terms, g
 
-    def render(self, rays, n_samples: int, seed: int = 0, ray_id0: int = 0, stratified: bool = True, bg=(0, 0, 0)):
+    def render(self, rays, n_samples: int, seed: int = 0, ray_id0: int = 0, stratified: bool = True, bg=(0, 0, 0),
+               given=None):
+        """Forward render.  given: None, or a dict with the samples of every ray fixed by the caller -- "S" [n],
+        "t" [n, N] (float32) and "cell" [n, N, 3] (int32, base corner of each sample's trilinear cell); then s_k,
+        delta_k and everything after the placement are computed here, in FP64, from those samples."""
         rays = _np(rays, np.float32).reshape(-1, 8)
         n = rays.shape[0]
+        gS, gt, gc = _given(given, n, n_samples)
         bgv = np.asarray(bg, np.float64)
         out = {"rgb": np.empty((n, 3)), "depth": np.empty(n), "opac": np.empty(n), "diag": np.empty((n, 4)),
                "normal": np.empty((n, 3))}
@@ -272,7 +277,8 @@ class Grid:
             semp = out["sem"].ctypes.data
         lib().orc_render(self._h, rays.ctypes.data, n, int(n_samples), _u32(seed), _u32(ray_id0), int(stratified),
                          bgv.ctypes.data, out["rgb"].ctypes.data, out["depth"].ctypes.data, out["opac"].ctypes.data,
-                         semp, out["diag"].ctypes.data, out["normal"].ctypes.data)
+                         semp, out["diag"].ctypes.data, out["normal"].ctypes.data, _ptr_or_none(gS),
+                         _ptr_or_none(gt), _ptr_or_none(gc))
         out["S"] = out["diag"][:, 0]
         out["n_valid"] = out["diag"][:, 1]
         out["degenerate"] = out["diag"][:, 2] > 0
@@ -289,9 +295,11 @@ class Grid:
         return {c: out[:k, i] for i, c in enumerate(cols)}
 
     def backward(self, rays, n_samples: int, g_rgb, g_depth=None, g_opac=None, g_sem=None, seed: int = 0,
-                 ray_id0: int = 0, stratified: bool = True, bg=(0, 0, 0), g_normal=None):
+                 ray_id0: int = 0, stratified: bool = True, bg=(0, 0, 0), g_normal=None, given=None):
+        """Accumulated dL/dtheta for the given seeds (see render for `given`)."""
         rays = _np(rays, np.float32).reshape(-1, 8)
         n = rays.shape[0]
+        gS, gt, gc = _given(given, n, n_samples)
         g_rgb = _np(g_rgb, np.float64).reshape(n, 3)
         gd = _np(g_depth, np.float64) if g_depth is not None else None
         go = _np(g_opac, np.float64) if g_opac is not None else None
@@ -310,7 +318,8 @@ class Grid:
                                   go.ctypes.data if go is not None else None,
                                   gs.ctypes.data if gs is not None else None,
                                   grad["sdf"].ctypes.data, grad["rgb"].ctypes.data, gsp,
-                                  grad["beta_per_ray"].ctypes.data, gn.ctypes.data if gn is not None else None)
+                                  grad["beta_per_ray"].ctypes.data, gn.ctypes.data if gn is not None else None,
+                                  _ptr_or_none(gS), _ptr_or_none(gt), _ptr_or_none(gc))
         grad["beta"] = float(grad["beta_per_ray"].sum())
         return grad
 
@@ -322,6 +331,20 @@ class Grid:
         lib().orc_count_touched(self._h, rays.ctypes.data, n, int(n_samples), _u32(seed), _u32(ray_id0),
                                 int(stratified), vx.ctypes.data, bl.ctypes.data)
         return vx, bl
+
+
+def _ptr_or_none(a):
+    return None if a is None else a.ctypes.data
+
+
+def _given(given, n, N):
+    """Contiguous (S float64 [n], t float32 [n, N], cell int32 [n, N, 3]) of a caller-fixed sample set, or Nones."""
+    if given is None:
+        return None, None, None
+    S = _np(given["S"], np.float64).reshape(n)
+    t = _np(given["t"], np.float32).reshape(n, N)
+    c = _np(given["cell"], np.int32).reshape(n, N, 3)
+    return S, t, c
 
 
 def sample_hash(seed, ray, k) -> int:

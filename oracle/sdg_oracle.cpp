@@ -87,15 +87,10 @@ struct Stencil {
     double f[3];
 };
 
-Stencil stencil_at(const Grid& g, const double x[3]) {
+// Stencil of the cell whose base corner is voxel c: f = x / vs - c per axis (in [0, 1) when c = floor(x / vs)).
+Stencil stencil_in_cell(const Grid& g, const double x[3], const int64_t c[3]) {
     Stencil s;
-    int64_t c[3];
-    for (int a = 0; a < 3; ++a) {
-        double gx = x[a] / g.vs;
-        double fl = std::floor(gx);
-        c[a] = (int64_t)fl;
-        s.f[a] = gx - fl;
-    }
+    for (int a = 0; a < 3; ++a) s.f[a] = x[a] / g.vs - (double)c[a];
     s.valid = true;
     for (int e = 0; e < 8; ++e) {
         int ex = e & 1, ey = (e >> 1) & 1, ez = (e >> 2) & 1;
@@ -107,6 +102,12 @@ Stencil stencil_at(const Grid& g, const double x[3]) {
         s.r[e] = (ex ? s.f[0] : 1.0 - s.f[0]) * (ey ? s.f[1] : 1.0 - s.f[1]) * (ez ? s.f[2] : 1.0 - s.f[2]);
     }
     return s;
+}
+
+Stencil stencil_at(const Grid& g, const double x[3]) {
+    int64_t c[3];
+    for (int a = 0; a < 3; ++a) c[a] = (int64_t)std::floor(x[a] / g.vs);
+    return stencil_in_cell(g, x, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -248,13 +249,27 @@ void corner_weight_grad(const Stencil& s, double vs, int e, double* r, double dr
 
 bool valid_at(const Grid& g, const double x[3]) { return stencil_at(g, x).valid; }
 
+// Samples fixed by the caller instead of found by traversal (the comparison of a ray whose FP32 placement differs
+// from the FP64 one only by rounding, at an interval joint or a block face): the allocated length S, and for every
+// sample its ray parameter t_k and the base corner of its trilinear cell.  Everything else -- s_k and delta_k from
+// S, the stencil's validity and weights, density, compositing, backward -- is computed here as for any ray.
+struct Given {
+    double S;
+    const float* t;       // [N]
+    const int32_t* cell;  // [N][3]
+};
+
 RayResult render_ray(const Grid& g, const float* ray, int N, uint32_t seed, uint32_t ray_id, int stratified,
-                     const double bg[3]) {
+                     const double bg[3], const Given* gv = nullptr) {
     RayResult R;
     R.sem.assign(g.n_sem, 0.0);
     double o[3] = {ray[0], ray[1], ray[2]}, d[3] = {ray[4], ray[5], ray[6]};
-    R.iv = traverse(g, o, d, ray[3], ray[7]);
-    for (auto& v : R.iv) R.S += v.t_out - v.t_in;
+    if (gv) {
+        R.S = gv->S;
+    } else {
+        R.iv = traverse(g, o, d, ray[3], ray[7]);
+        for (auto& v : R.iv) R.S += v.t_out - v.t_in;
+    }
     if (!(R.S > 0.0)) {
         for (int c = 0; c < 3; ++c) R.C[c] = bg[c];
         return R;
@@ -274,11 +289,20 @@ RayResult render_ray(const Grid& g, const float* ray, int N, uint32_t seed, uint
     for (int k = 0; k < N; ++k) {
         Sample& sm = R.smp[k];
         sm.delta = (k + 1 < N ? R.smp[k + 1].s : R.S) - sm.s;
-        size_t i = 0;
-        while (i + 1 < R.iv.size() && sm.s >= s_start[i + 1]) ++i;
-        sm.t = R.iv[i].t_in + (sm.s - s_start[i]);
+        if (gv) {
+            sm.t = gv->t[k];
+        } else {
+            size_t i = 0;
+            while (i + 1 < R.iv.size() && sm.s >= s_start[i + 1]) ++i;
+            sm.t = R.iv[i].t_in + (sm.s - s_start[i]);
+        }
         double x[3] = {o[0] + sm.t * d[0], o[1] + sm.t * d[1], o[2] + sm.t * d[2]};
-        sm.st = stencil_at(g, x);
+        if (gv) {
+            const int64_t c[3] = {gv->cell[3 * k], gv->cell[3 * k + 1], gv->cell[3 * k + 2]};
+            sm.st = stencil_in_cell(g, x, c);
+        } else {
+            sm.st = stencil_at(g, x);
+        }
         sm.valid = sm.st.valid;
         sm.d = 0.0;
         sm.c[0] = sm.c[1] = sm.c[2] = 0.0;
@@ -299,6 +323,7 @@ RayResult render_ray(const Grid& g, const float* ray, int N, uint32_t seed, uint
         sm.sigma = sm.valid ? density(sm.d, g.beta) : 0.0;
         sm.tau = sm.sigma * sm.delta;
         // degeneracy: a sample next to a skip-space joint, or whose validity flips under a tiny nudge
+        if (gv) continue;
         for (size_t j = 1; j < R.iv.size(); ++j)
             if (std::fabs(sm.s - s_start[j]) < 1e-5) R.degenerate = true;
         const double eg = 5e-4 * g.vs;
@@ -603,13 +628,26 @@ double orc_eikonal(void* gp, const double* x, int64_t n, double lambda, double* 
     return L;
 }
 
+// Samples of ray i when the caller fixes them (g_S non-NULL): S = g_S[i], t_k = g_t[i][k], cells g_cell[i][k][3].
+bool given_of(const double* g_S, const float* g_t, const int32_t* g_cell, int64_t i, int N, Given* gv) {
+    if (!g_S) return false;
+    gv->S = g_S[i];
+    gv->t = g_t + i * N;
+    gv->cell = g_cell + i * N * 3;
+    return true;
+}
+
 // Forward render of n rays (ray i uses hash id ray_id0 + i).  diag[i] = {S, n_valid, degenerate, T_N}.
+// g_S, g_t, g_cell: NULL, or the samples of every ray fixed by the caller (see Given).
 void orc_render(void* gp, const float* rays, int64_t n, int N, uint32_t seed, uint32_t ray_id0, int stratified,
                 const double* bg, double* rgb, double* depth, double* opac, double* sem, double* diag,
-                double* normal) {
+                double* normal, const double* g_S, const float* g_t, const int32_t* g_cell) {
     Grid* g = (Grid*)gp;
     for (int64_t i = 0; i < n; ++i) {
-        RayResult R = render_ray(*g, rays + 8 * i, N, seed, ray_id0 + (uint32_t)i, stratified, bg);
+        Given gv;
+        const bool given = given_of(g_S, g_t, g_cell, i, N, &gv);
+        RayResult R = render_ray(*g, rays + 8 * i, N, seed, ray_id0 + (uint32_t)i, stratified, bg,
+                                 given ? &gv : nullptr);
         for (int c = 0; c < 3; ++c) rgb[i * 3 + c] = R.C[c];
         if (normal)
             for (int a = 0; a < 3; ++a) normal[i * 3 + a] = R.Nrm[a];
@@ -653,12 +691,16 @@ int orc_trace(void* gp, const float* ray, int N, uint32_t seed, uint32_t ray_id,
 void orc_render_backward(void* gp, const float* rays, int64_t n, int N, uint32_t seed, uint32_t ray_id0,
                          int stratified, const double* bg, const double* g_rgb, const double* g_depth,
                          const double* g_opac, const double* g_sem, double* grad_sdf, double* grad_rgb,
-                         double* grad_sem, double* grad_beta, const double* g_normal) {
+                         double* grad_sem, double* grad_beta, const double* g_normal, const double* g_S,
+                         const float* g_t, const int32_t* g_cell) {
     Grid* g = (Grid*)gp;
     const int ns = g->n_sem;
     for (int64_t i = 0; i < n; ++i) {
         if (grad_beta) grad_beta[i] = 0.0;
-        RayResult R = render_ray(*g, rays + 8 * i, N, seed, ray_id0 + (uint32_t)i, stratified, bg);
+        Given gv;
+        const bool given = given_of(g_S, g_t, g_cell, i, N, &gv);
+        RayResult R = render_ray(*g, rays + 8 * i, N, seed, ray_id0 + (uint32_t)i, stratified, bg,
+                                 given ? &gv : nullptr);
         if (R.smp.empty()) continue;
         const double* gc = g_rgb + 3 * i;
         double gd = g_depth ? g_depth[i] : 0.0, go = g_opac ? g_opac[i] : 0.0;

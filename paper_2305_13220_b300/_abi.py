@@ -14,6 +14,8 @@ KIND_VALUE, KIND_GRAD, KIND_ADAM_M, KIND_ADAM_V = range(4)
 MODE_RECOMPUTE, MODE_STORE = 0, 1
 ORDER_AUTO, ORDER_GIVEN, ORDER_SURFACE = 0, 1, 2
 OPT_ADAM, OPT_RMSPROP = 0, 1
+WALK_PASS, WALK_IN_WARP = 0, 1
+TRACE_CELLS = 32
 
 ERROR_NAMES = {OK: "SDG_OK", ERR_ARG: "SDG_ERR_ARG", ERR_OOM: "SDG_ERR_OOM", ERR_CAPACITY: "SDG_ERR_CAPACITY",
                ERR_CUDA: "SDG_ERR_CUDA", ERR_TIMEOUT: "SDG_ERR_TIMEOUT", ERR_BUSY: "SDG_ERR_BUSY",
@@ -43,6 +45,12 @@ class LossOpts(C.Structure):
 class AdamOpts(C.Structure):
     _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
                 ("step", C.c_int32), ("algo", C.c_int32)]
+
+
+class TraceOut(C.Structure):
+    _fields_ = [("n_cells", C.c_void_p), ("S", C.c_void_p), ("t", C.c_void_p), ("cell", C.c_void_p),
+                ("block", C.c_void_p), ("valid", C.c_void_p), ("seg", C.c_void_p), ("rgb", C.c_void_p),
+                ("depth", C.c_void_p), ("opac", C.c_void_p)]
 
 
 class ServerOpts(C.Structure):
@@ -118,6 +126,9 @@ SIGNATURES = {
     "sdg_server_get_stats": [_p, _P(ServerStats)],
     "sdg_server_destroy": [_p],
     "sdg_debug_fail_alloc_after": [_i64],
+    "sdg_debug_trace": [_p, _p, _i64, _P(RenderOpts), _i32, _P(TraceOut)],
+    "sdg_debug_trace_view": [_p, _i32, _i32, _P(C.c_float), _P(C.c_float), C.c_float, C.c_float, _P(RenderOpts),
+                             _p, _P(TraceOut)],
 }
 
 _lib = None

@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "render_core.cuh"
 
 // Grid-owned scratch of the permutohedral lattice filter (lattice.cu), grown on demand.
 struct LatticeScratch {
@@ -126,6 +127,10 @@ int use_device(sdg_grid g);
 
 // Grid-owned per-item loss scratch of at least n floats (grown on demand; valid until the next call on g).
 int loss_scratch(sdg_grid g, int64_t n, float** out);
+
+// Enqueues the traversal pass (k_walk) of n rays, processed in order perm (NULL: as given), into the grid-owned
+// walk records and points a.walk at them (render.cu).
+int walk_rays(sdg_grid g, const float* rays, const int* perm, int64_t n, PassArgs& a);
 
 // Buckets of the surface ordering of a training batch (order.cu).
 constexpr int kOrderBuckets = 1 << 15;

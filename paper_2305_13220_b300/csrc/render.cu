@@ -112,6 +112,9 @@ __global__ void __launch_bounds__(256) k_walk(GridDev g, const float* __restrict
     w.hdr[slot] = make_int2(cnt, __float_as_int(S));
 }
 
+}  // namespace
+
+namespace sdg {
 // Grows the grid-owned walk records to n rays (valid until the next call on this grid).
 int walk_scratch(sdg_grid g, int64_t n) {
     if (g->walk_cap >= n) return SDG_OK;
@@ -145,6 +148,9 @@ int walk_rays(sdg_grid g, const float* rays, const int* perm, int64_t n, PassArg
     a.walk = w;
     return SDG_OK;
 }
+}  // namespace sdg
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // Losses

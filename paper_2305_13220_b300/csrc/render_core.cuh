@@ -42,7 +42,8 @@ enum PassMode {
     PASS_BWD_STORE = 3,
     PASS_TRAIN = 4,
     PASS_TRAIN_BETA = 5,
-    PASS_TRAIN_NRM = 6  // PASS_TRAIN plus the normal loss of Eq. 14 on the rendered normal sum_k w_k grad f(x_k)
+    PASS_TRAIN_NRM = 6,  // PASS_TRAIN plus the normal loss of Eq. 14 on the rendered normal sum_k w_k grad f(x_k)
+    PASS_FWD_TRACE = 7   // PASS_FWD that also writes where every sample was placed (debug export)
 };
 
 // Allocated block cells of a ray kept in the walk records; a ray crossing more takes the in-warp traversal.
@@ -79,6 +80,16 @@ struct PassArgs {
     const float* t_normal;  // PASS_TRAIN_NRM: target normals [n][3] (world frame)
     float lam_n;
     WalkBufs walk;  // records of the traversal pass (hdr NULL: every warp walks its ray itself)
+    // PASS_FWD_TRACE outputs, per ray [n] or per sample [n][N]: walk records used (-1: the warp walked the ray),
+    // S, t_k, the voxel coordinates of the sample's cell base corner [n][N][3], its own block index, validity;
+    // tr_seg [n][kWalkCap][2] (nullable): t_in and length of each walk record
+    int* tr_ncell;
+    float* tr_S;
+    float* tr_t;
+    int* tr_cell;
+    int* tr_blk;
+    unsigned char* tr_valid;
+    float* tr_seg;
 };
 
 struct RayJob {
@@ -123,6 +134,26 @@ struct SampleGen {
         return fminf(((float)k + u) * s_over_n, s_max);
     }
 };
+
+// Pinhole intrinsics {fx, fy, cx, cy} and row-major 3x4 camera-to-world pose, passed to kernels by value.
+struct Cam6 {
+    float K[4];
+    float T[12];
+};
+
+// Pinhole camera ray of pixel (u, v) (centre at +0.5): d = normalize(R ((u + 0.5 - cx)/fx, (v + 0.5 - cy)/fy, 1)),
+// o = t, with K = {fx, fy, cx, cy} and T the row-major 3x4 camera-to-world pose.  Every product is an explicit
+// fused multiply-add, so the serving kernel and the trace export form the same rays.
+__device__ __forceinline__ void pinhole_ray(const float K[4], const float T[12], int u, int v, float3& o, float3& d) {
+    const float xc = ((float)u + 0.5f - K[2]) / K[0];
+    const float yc = ((float)v + 0.5f - K[3]) / K[1];
+    const float dx = fmaf(T[0], xc, fmaf(T[1], yc, T[2]));
+    const float dy = fmaf(T[4], xc, fmaf(T[5], yc, T[6]));
+    const float dz = fmaf(T[8], xc, fmaf(T[9], yc, T[10]));
+    const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    o = make_float3(T[3], T[7], T[11]);
+    d = make_float3(dx * inv, dy * inv, dz * inv);
+}
 
 // ---------------------------------------------------------------------------
 // Traversal
@@ -455,7 +486,8 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     constexpr bool kBeta = MODE == PASS_TRAIN_BETA;
     constexpr bool kNrm = MODE == PASS_TRAIN_NRM;
     constexpr bool kBwd = MODE == PASS_BWD || MODE == PASS_BWD_STORE || kTrain;
-    constexpr bool kFwdOut = MODE == PASS_FWD || MODE == PASS_FWD_STORE;
+    constexpr bool kTrace = MODE == PASS_FWD_TRACE;
+    constexpr bool kFwdOut = MODE == PASS_FWD || MODE == PASS_FWD_STORE || kTrace;
     constexpr int SEMCAP = SEM ? 32 : 0;
     const int N = a.N;
     const int ns = SEM ? g.n_sem : 0;
@@ -488,6 +520,16 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             }
         }
         if (!by_rec) S = walk_pieces(g, j, sm, lane, pc, t1);
+        if constexpr (kTrace) {
+            if (lane == 0) {
+                a.tr_S[j.idx] = S;
+                a.tr_ncell[j.idx] = by_rec ? n_rec : -1;
+            }
+            if (a.tr_seg && by_rec && lane < n_rec) {
+                a.tr_seg[(j.idx * kWalkCap + lane) * 2] = __int_as_float(my_rec.x);
+                a.tr_seg[(j.idx * kWalkCap + lane) * 2 + 1] = __int_as_float(my_rec.y);
+            }
+        }
     }
     if constexpr (kStoreOut) {
         if (lane == 0) a.rec_S[j.idx] = S;
@@ -529,7 +571,18 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         if constexpr (kBeta) bq_[i] = 0.f;
         if constexpr (kNrm) gnx_[i] = gny_[i] = gnz_[i] = 0.f;
         blk_[i] = -1; lc_[i] = 0;
-        if (!any) return false;  // warp-uniform
+        if (!any) {  // warp-uniform
+            if constexpr (kTrace) {
+                if (k < N) {
+                    const int64_t q = j.idx * N + k;
+                    a.tr_t[q] = 0.f;
+                    a.tr_cell[3 * q] = a.tr_cell[3 * q + 1] = a.tr_cell[3 * q + 2] = 0;
+                    a.tr_blk[q] = -1;
+                    a.tr_valid[q] = 0;
+                }
+            }
+            return false;
+        }
         int blk = -1, cell = -1;
         float t_rec = 0.f;
         if constexpr (!kStoreIn) {
@@ -567,6 +620,14 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             if (own != cell) blk = own < 0 ? -1 : __ldg(g.dense + own);
         }
         blk_[i] = blk;
+        if constexpr (kTrace) {
+            const int64_t q = j.idx * N + k;
+            a.tr_t[q] = t_[i];
+            a.tr_cell[3 * q] = cx;
+            a.tr_cell[3 * q + 1] = cy;
+            a.tr_cell[3 * q + 2] = cz;
+            a.tr_blk[q] = blk;
+        }
         return true;
     };
     // evaluate sample i: corner fetch into cs/crr/cgg/cbb (or, with reuse, the corners already there when the
@@ -602,6 +663,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 if constexpr (kNrm) sdf_gradient(fx, fy, fz, g.inv_vs, cs, gnx_[i], gny_[i], gnz_[i]);
             }
         }
+        if constexpr (kTrace) a.tr_valid[j.idx * N + lane * Q + i] = valid ? 1 : 0;
         if (valid) {
             vmask |= 1u << i;
             // sigma = Psi_beta(-d) / beta, the Laplace CDF transform (Sec. 3.5.1)

@@ -57,16 +57,8 @@ __global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
     if (local >= ch.npix) return;  // warp-uniform
     const int64_t pix = ch.pix0 + local;
     const int u = (int)(pix % ch.W), v = (int)(pix / ch.W);
-    // pinhole ray: d = normalize(R ((u + 0.5 - cx)/fx, (v + 0.5 - cy)/fy, 1)), o = t
-    const float xc = ((float)u + 0.5f - ch.K[2]) / ch.K[0];
-    const float yc = ((float)v + 0.5f - ch.K[3]) / ch.K[1];
-    float dx = ch.T[0] * xc + ch.T[1] * yc + ch.T[2];
-    float dy = ch.T[4] * xc + ch.T[5] * yc + ch.T[6];
-    float dz = ch.T[8] * xc + ch.T[9] * yc + ch.T[10];
-    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
     RayJob j;
-    j.o = make_float3(ch.T[3], ch.T[7], ch.T[11]);
-    j.d = make_float3(dx * inv, dy * inv, dz * inv);
+    pinhole_ray(ch.K, ch.T, u, v, j.o, j.d);
     j.tn = ch.tnear;
     j.tf = ch.tfar;
     j.ray_id = (uint32_t)pix;

@@ -1,0 +1,137 @@
+// Debug export of the sample placement (Sec. 3.5.1 skip-space sampling, Eq. 17 trilinear cells): the forward
+// pass in PASS_FWD_TRACE mode writes, per sample, t_k, its cell and block and its validity, so that a test can
+// feed exactly these samples to an independent implementation of the rest of the method.
+#include "internal.h"
+#include "render_kernels.cuh"
+
+using namespace sdg;
+
+namespace {
+
+// One warp per pixel of an H x W pinhole view, rays formed by pinhole_ray as the serving kernel forms them and
+// walked in-warp as it walks them.
+template <bool BF16, bool SEM, int Q>
+__global__ void __launch_bounds__(256, (render_min_blocks<PASS_FWD_TRACE, SEM, Q>()))
+    k_trace_view(GridDev g, int H, int W, Cam6 cam, float tnear, float tfar, float* rays_out, PassArgs a) {
+    __shared__ WarpSmem smem[kWarpsPerBlock];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t pix = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (pix >= (int64_t)H * W) return;  // warp-uniform
+    const int u = (int)(pix % W), v = (int)(pix / W);
+    RayJob j;
+    pinhole_ray(cam.K, cam.T, u, v, j.o, j.d);
+    j.tn = tnear;
+    j.tf = tfar;
+    j.ray_id = (uint32_t)pix;
+    j.idx = pix;
+    j.slot = 0;
+    if (lane == 0) {
+        float4* r = reinterpret_cast<float4*>(rays_out) + 2 * pix;
+        r[0] = make_float4(j.o.x, j.o.y, j.o.z, tnear);
+        r[1] = make_float4(j.d.x, j.d.y, j.d.z, tfar);
+    }
+    ray_program<PASS_FWD_TRACE, BF16, SEM, Q>(g, a, j, smem[warp], lane);
+}
+
+template <bool BF16, bool SEM>
+int launch_view(const GridDev& gd, int H, int W, const Cam6& cam, float tn, float tf, float* rays_out,
+                const PassArgs& a, int Q, cudaStream_t s) {
+    const unsigned blocks = (unsigned)(((int64_t)H * W + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    switch (Q) {
+        case 2: k_trace_view<BF16, SEM, 2><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
+        case 4: k_trace_view<BF16, SEM, 4><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
+        case 6: k_trace_view<BF16, SEM, 6><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
+        default: k_trace_view<BF16, SEM, 8><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
+    }
+    SDG_LAUNCH_CHECK("trace view kernel");
+    return SDG_OK;
+}
+
+int pick_q(int N) { return N <= 64 ? 2 : N <= 128 ? 4 : N <= 192 ? 6 : 8; }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_out(const sdg_trace_out* out, int64_t n) {
+    if (!out) return fail(SDG_ERR_ARG, "trace: null output");
+    if (n > 0 && (!out->n_cells || !out->S || !out->t || !out->cell || !out->block || !out->valid || !out->rgb ||
+                  !out->depth || !out->opac))
+        return fail(SDG_ERR_ARG, "trace: null output buffer");
+    return SDG_OK;
+}
+
+PassArgs trace_args(const sdg_render_opts* o, int64_t n, const sdg_trace_out* out) {
+    PassArgs a{};
+    a.N = o->n_samples;
+    a.seed = o->seed;
+    a.strat = o->stratified ? 1 : 0;
+    for (int c = 0; c < 3; ++c) a.bg[c] = o->bg[c];
+    a.n = n;
+    a.out_rgb = out->rgb;
+    a.out_depth = out->depth;
+    a.out_opac = out->opac;
+    a.tr_ncell = out->n_cells;
+    a.tr_S = out->S;
+    a.tr_t = out->t;
+    a.tr_cell = out->cell;
+    a.tr_blk = out->block;
+    a.tr_valid = out->valid;
+    a.tr_seg = out->seg;
+    return a;
+}
+
+int check_opts(const sdg_render_opts* o) {
+    if (!o || o->n_samples < 1 || o->n_samples > 256) return fail(SDG_ERR_ARG, "trace: n_samples must be in [1, 256]");
+    return SDG_OK;
+}
+
+}  // namespace
+
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, false, false)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, false, true)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, true, false)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, true, true)
+
+extern "C" int sdg_debug_trace(sdg_grid g, const float* rays, int64_t n, const sdg_render_opts* o, int32_t walk,
+                               const sdg_trace_out* out) {
+    if (!g || n < 0 || (n > 0 && !rays)) return fail(SDG_ERR_ARG, "sdg_debug_trace: null argument");
+    int rc = check_opts(o);
+    if (rc || (rc = check_out(out, n))) return rc;
+    if (walk != SDG_WALK_PASS && walk != SDG_WALK_IN_WARP) return fail(SDG_ERR_ARG, "sdg_debug_trace: bad walk");
+    if (n > 0 && !aligned16(rays)) return fail(SDG_ERR_ARG, "sdg_debug_trace: rays must be 16-byte aligned");
+    if (n > (int64_t)1 << 31) return fail(SDG_ERR_ARG, "sdg_debug_trace: at most 2^31 rays per call");
+    if ((rc = use_device(g))) return rc;
+    if (n == 0) return SDG_OK;
+    PassArgs a = trace_args(o, n, out);
+    if (walk == SDG_WALK_PASS && (rc = walk_rays(g, rays, nullptr, n, a))) return rc;
+    const GridDev gd = g->dev();
+    const int Q = pick_q(o->n_samples);
+    const bool bf16 = g->desc.rgb_dtype == SDG_BF16, sem = g->desc.n_sem > 0;
+    if (!bf16 && !sem) return launch_q<PASS_FWD_TRACE, false, false>(gd, rays, o->ray_id0, a, Q, g->stream);
+    if (!bf16 && sem) return launch_q<PASS_FWD_TRACE, false, true>(gd, rays, o->ray_id0, a, Q, g->stream);
+    if (bf16 && !sem) return launch_q<PASS_FWD_TRACE, true, false>(gd, rays, o->ray_id0, a, Q, g->stream);
+    return launch_q<PASS_FWD_TRACE, true, true>(gd, rays, o->ray_id0, a, Q, g->stream);
+}
+
+extern "C" int sdg_debug_trace_view(sdg_grid g, int32_t H, int32_t W, const float K[4], const float T[12],
+                                    float tnear, float tfar, const sdg_render_opts* o, float* rays_out,
+                                    const sdg_trace_out* out) {
+    if (!g || !K || !T || H <= 0 || W <= 0 || !rays_out || !(K[0] != 0.f) || !(K[1] != 0.f))
+        return fail(SDG_ERR_ARG, "sdg_debug_trace_view: bad argument");
+    const int64_t n = (int64_t)H * W;
+    int rc = check_opts(o);
+    if (rc || (rc = check_out(out, n))) return rc;
+    if (!aligned16(rays_out)) return fail(SDG_ERR_ARG, "sdg_debug_trace_view: rays_out must be 16-byte aligned");
+    if (n > (int64_t)1 << 31) return fail(SDG_ERR_ARG, "sdg_debug_trace_view: at most 2^31 pixels");
+    if ((rc = use_device(g))) return rc;
+    PassArgs a = trace_args(o, n, out);
+    Cam6 cam;
+    for (int i = 0; i < 4; ++i) cam.K[i] = K[i];
+    for (int i = 0; i < 12; ++i) cam.T[i] = T[i];
+    const GridDev gd = g->dev();
+    const int Q = pick_q(o->n_samples);
+    const bool bf16 = g->desc.rgb_dtype == SDG_BF16, sem = g->desc.n_sem > 0;
+    if (!bf16 && !sem) return launch_view<false, false>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
+    if (!bf16 && sem) return launch_view<false, true>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
+    if (bf16 && !sem) return launch_view<true, false>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
+    return launch_view<true, true>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
+}

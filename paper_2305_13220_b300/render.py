@@ -50,6 +50,49 @@ def render(grid: Grid, rays: torch.Tensor, n_samples: int, seed: int = 0, ray_id
     return out
 
 
+def _trace_buffers(n: int, n_samples: int, dev):
+    out = {"n_cells": torch.empty(n, dtype=torch.int32, device=dev), "S": torch.empty(n, device=dev),
+           "t": torch.empty((n, n_samples), device=dev),
+           "cell": torch.empty((n, n_samples, 3), dtype=torch.int32, device=dev),
+           "block": torch.empty((n, n_samples), dtype=torch.int32, device=dev),
+           "valid": torch.empty((n, n_samples), dtype=torch.uint8, device=dev),
+           "seg": torch.zeros((n, A.TRACE_CELLS, 2), device=dev),
+           "rgb": torch.empty((n, 3), device=dev), "depth": torch.empty(n, device=dev),
+           "opac": torch.empty(n, device=dev)}
+    to = A.TraceOut(**{k: _ptr(v) for k, v in out.items()})
+    return out, to
+
+
+def trace(grid: Grid, rays: torch.Tensor, n_samples: int, seed: int = 0, ray_id0: int = 0, stratified: bool = True,
+          bg=(0.0, 0.0, 0.0), walk: str = "pass"):
+    """Debug export of the sample placement of a forward render (sdg_debug_trace): per ray n_cells, S, seg; per
+    sample t, cell [.., 3], block, valid; and the forward outputs rgb, depth, opac.  walk: "pass" (as the forward,
+    backward and training passes) or "in_warp" (as the serving loop and the allocation-free training pass)."""
+    walks = {"pass": A.WALK_PASS, "in_warp": A.WALK_IN_WARP}
+    n = rays.shape[0]
+    out, to = _trace_buffers(n, n_samples, rays.device)
+    o = render_opts(n_samples, seed, ray_id0, stratified, "recompute", bg)
+    A.call("sdg_debug_trace", grid.handle, _ptr(rays, torch.float32, "rays"), n, C.byref(o), walks[walk],
+           C.byref(to))
+    return out
+
+
+def trace_view(grid: Grid, H: int, W: int, K, Twc, n_samples: int, seed: int = 0, stratified: bool = True,
+               tnear: float = 0.05, tfar: float = 1.0e3):
+    """Debug export of a served H x W view (sdg_debug_trace_view): the trace() outputs plus the rays [H*W, 8] the
+    serving kernel forms for it."""
+    n = H * W
+    dev = f"cuda:{grid.device}"
+    out, to = _trace_buffers(n, n_samples, dev)
+    out["rays"] = torch.empty((n, 8), device=dev)
+    o = render_opts(n_samples, seed, 0, stratified, "recompute", (0.0, 0.0, 0.0))
+    Kc = (C.c_float * 4)(*[float(x) for x in K])
+    Tc = (C.c_float * 12)(*torch.as_tensor(Twc, dtype=torch.float64).reshape(12).tolist())
+    A.call("sdg_debug_trace_view", grid.handle, H, W, Kc, Tc, float(tnear), float(tfar), C.byref(o),
+           _ptr(out["rays"]), C.byref(to))
+    return out
+
+
 def backward(ctx: RenderContext, g_rgb: torch.Tensor, g_depth: Optional[torch.Tensor] = None,
              g_opac: Optional[torch.Tensor] = None, g_sem: Optional[torch.Tensor] = None):
     """Accumulates dL/dtheta into the grid's gradient channels."""

@@ -2,7 +2,7 @@
 
 dL/dbeta: the fused pass takes it through the identity dsigma/dbeta = -sigma/beta - (d/beta) dsigma/dd, the
 oracle differentiates the two branches of sigma directly (and is pinned by finite differences in beta); both
-must agree on the same non-degenerate rays.  The optimiser then moves beta by the Adam step-1 closed form.
+must agree over every ray of the batch (the oracle fed the GPU's samples).  The optimiser then moves beta by the Adam step-1 closed form.
 The SSI depth loss must match the oracle's FP64 least squares."""
 import numpy as np
 import pytest
@@ -10,7 +10,7 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import assert_grad_close, grad_arrays, tiny_room
+from tests.gpu_util import assert_grad_close, check_placement, gpu_samples, grad_arrays, tiny_room
 
 pytestmark = pytest.mark.gpu
 
@@ -21,13 +21,19 @@ def sdg():
     return m
 
 
-def _batch(O, sc, seed, n_samples=64):
+def _batch(O, sc, seed, n_samples=64, G=None):
+    """A whole view; with G, the oracle's render runs on the GPU's own samples (returned as ref["given"])."""
+    import paper_2305_13220_b300 as sdg
     P = synth.random_poses(sc, 1, seed=seed)
     K = synth.intrinsics(64, 48)
     rays = synth.view_rays(P[0], 64, 48, K)
-    ref = O.render(rays, n_samples, stratified=False)
-    rays = rays[torch.as_tensor(~ref["degenerate"])]
-    ref = O.render(rays, n_samples, stratified=False)
+    gv = None
+    if G is not None:
+        tr = sdg.trace(G, rays.cuda(), n_samples, stratified=False)
+        check_placement(O, rays, tr, n_samples, stratified=False)
+        gv = gpu_samples(tr)
+    ref = O.render(rays, n_samples, stratified=False, given=gv)
+    ref["given"] = gv
     n = rays.shape[0]
     rng = np.random.default_rng(seed)
     t_rgb = ref["rgb"] + rng.choice([-0.05, 0.05], size=(n, 3))
@@ -41,9 +47,9 @@ def _dev(x):
 
 def test_beta_gradient_matches_oracle_and_voxel_gradients_are_unchanged(sdg):
     sc, G, O, _, _ = tiny_room()
-    rays, ref, t_rgb, t_depth = _batch(O, sc, seed=6)
+    rays, ref, t_rgb, t_depth = _batch(O, sc, seed=6, G=G)
     L, seeds = oracle.loss(ref["rgb"], ref["depth"], t_rgb, t_depth, 0.1)
-    want = O.backward(rays, 64, seeds["rgb"], seeds["depth"], stratified=False)
+    want = O.backward(rays, 64, seeds["rgb"], seeds["depth"], stratified=False, given=ref["given"])
     assert abs(want["beta"]) > 0
     G.zero_grad()
     sdg.train_step_rays(G, rays.cuda(), _dev(t_rgb), _dev(t_depth), n_samples=64, stratified=False)

@@ -2,15 +2,17 @@
 
 The room-scale grid (6x6x3 m, 1 cm voxels, 4-voxel band) is activated on the GPU from all 50 synthetic 640x480
 depth maps and compared bit-exactly with the oracle's key set; then the fused training pass runs on a full
-2^18-ray batch with 128 samples per ray, and sampled rays' losses, a subset's gradients and sampled Adam updates
-are checked against the oracle one by one."""
+2^18-ray batch with 128 samples per ray (surface-ordered, as timed), and sampled rays' losses and rendered
+colour / depth / opacity, a subset's gradients (through the surface-ordered path and in the given order) and
+sampled Adam updates are checked against the oracle one by one.  No ray is skipped: the oracle runs on the GPU's
+own samples (sdg_debug_trace), whose placement is first checked against the oracle's FP64 traversal."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import synth
-from tests.gpu_util import assert_grad_close
+from tests.gpu_util import assert_grad_close, check_placement, gpu_samples
 
 pytestmark = pytest.mark.gpu
 
@@ -57,51 +59,59 @@ def test_full_activation_is_bit_exact(room):
 
 
 def test_full_batch_sampled_rays_match_oracle(room):
+    """The timed launch: 2^18 rays in surface order.  256 sampled rays' loss terms from that launch, and their
+    rendered colour / depth / opacity from a full-batch forward, against the oracle over the GPU's samples."""
     sdg, sc, poses, K, depths, G, O, gk = room
     b = synth.training_batch(sc, poses, W, H, K, 1 << 18, seed=7, device="cuda", order="pixel")
     n = b["rays"].shape[0]
     loss = torch.empty(n, device="cuda")
     G.zero_grad()
     sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N, seed=3, loss=loss)
+    tr = sdg.trace(G, b["rays"], N, seed=3)
     torch.cuda.synchronize()
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(n, 256, replace=False))
+    sel = torch.as_tensor(idx, device="cuda")
     rays = b["rays"].cpu().numpy()
     t_rgb = b["rgb"].double().cpu().numpy()
     t_d = b["depth"].double().cpu().numpy()
     got = loss.double().cpu().numpy()
-    checked = 0
-    for i in idx:
-        ref = O.render(rays[i:i + 1], N, seed=3, ray_id0=int(i))
-        if ref["degenerate"][0]:
-            continue
-        # per-ray loss term: (sum |C - C^| / 3 + 0.1 |D - D^|) / n
+    sub = {k: v[sel] for k, v in tr.items()}
+    assert (sub["n_cells"] >= 0).float().mean() > 0.9  # most rays placed from the traversal pass's records
+    for j, i in enumerate(idx):
+        one = {k: v[j:j + 1] for k, v in sub.items()}
+        check_placement(O, rays[i:i + 1], one, N, seed=3, ray_id0=int(i))
+        ref = O.render(rays[i:i + 1], N, seed=3, ray_id0=int(i), given=gpu_samples(one))
+        for k in ("rgb", "depth", "opac"):
+            assert np.abs(one[k].double().cpu().numpy() - ref[k]).max() <= 1e-4, (i, k)
+        # per-ray loss term: (sum |C - C^| / 3 + 0.1 |D - D^|) / n, |dL_i| <= (|dC| + 0.1 |dD|) / n
         e = np.abs(ref["rgb"][0] - t_rgb[i]).sum() / 3 + 0.1 * abs(ref["depth"][0] - t_d[i])
-        # |dL_i| <= (|dC| + 0.1 |dD|) / n with |dC|, |dD| <= 1e-4
         assert abs(got[i] * n - e) <= 2e-4, (i, got[i] * n, e)
-        checked += 1
-    assert checked > 240
 
 
-def test_subset_gradients_match_oracle(room):
-    """Gradients of a 2048-ray subset of the full batch (same kernel, same launch shape per ray)."""
+@pytest.mark.parametrize("order", ["surface", "given"])
+def test_subset_gradients_match_oracle(room, order):
+    """Gradients of a 2048-ray subset of the full batch, through the surface-ordered path the timed launch takes
+    (ray_order = surface) and in the given order, against the oracle over the GPU's samples."""
     sdg, sc, poses, K, depths, G, O, gk = room
     b = synth.training_batch(sc, poses, W, H, K, 1 << 18, seed=8, device="cuda", order="pixel")
     rng = np.random.default_rng(1)
     idx = np.sort(rng.choice(1 << 18, 2048, replace=False))
     rays = b["rays"].cpu().numpy()[idx]
-    ref = O.render(rays, N, stratified=False)
-    keep = ~ref["degenerate"]
-    rays, ref = rays[keep], {k: v[keep] for k, v in ref.items() if hasattr(v, "shape") and len(v) == len(keep)}
+    rd = torch.as_tensor(rays, device="cuda")
+    tr = sdg.trace(G, rd, N, stratified=False)
+    check_placement(O, rays, tr, N, stratified=False)
+    gv = gpu_samples(tr)
+    ref = O.render(rays, N, stratified=False, given=gv)
     n = len(rays)
     t_rgb = ref["rgb"] + rng.choice([-0.05, 0.05], size=(n, 3))
     t_depth = ref["depth"] + rng.choice([-0.1, 0.1], size=n)
     _, seeds = oracle.loss(ref["rgb"], ref["depth"], t_rgb, t_depth, 0.1)
-    want = O.backward(rays, N, seeds["rgb"], seeds["depth"], stratified=False)
+    want = O.backward(rays, N, seeds["rgb"], seeds["depth"], stratified=False, given=gv)
     G.zero_grad()
-    sdg.train_step_rays(G, torch.as_tensor(rays, device="cuda"),
-                        torch.as_tensor(t_rgb, dtype=torch.float32, device="cuda"),
-                        torch.as_tensor(t_depth, dtype=torch.float32, device="cuda"), n_samples=N, stratified=False)
+    sdg.train_step_rays(G, rd, torch.as_tensor(t_rgb, dtype=torch.float32, device="cuda"),
+                        torch.as_tensor(t_depth, dtype=torch.float32, device="cuda"), n_samples=N, stratified=False,
+                        ray_order=order)
     torch.cuda.synchronize()
     A = sdg._abi
     got = G.channel(A.GROUP_GEO, A.KIND_GRAD)[:len(gk)].double().cpu().numpy()

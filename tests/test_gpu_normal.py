@@ -6,7 +6,7 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import assert_grad_close, grad_arrays, tiny_room
+from tests.gpu_util import assert_grad_close, check_placement, gpu_samples, grad_arrays, tiny_room
 
 pytestmark = pytest.mark.gpu
 
@@ -26,9 +26,11 @@ def test_normal_loss_matches_oracle(sdg, rgb_dtype):
     sc, G, O, _, _ = tiny_room(rgb_dtype=rgb_dtype)
     P = synth.random_poses(sc, 1, seed=12)
     rays = synth.view_rays(P[0], 64, 48, synth.intrinsics(64, 48))
-    ref = O.render(rays, 64, stratified=False)
-    rays = rays[torch.as_tensor(~ref["degenerate"])]
-    ref = O.render(rays, 64, stratified=False)
+    # every ray: the oracle runs on the GPU's own samples (placement checked against the oracle's first)
+    tr = sdg.trace(G, rays.cuda(), 64, stratified=False)
+    check_placement(O, rays, tr, 64, stratified=False)
+    gv = gpu_samples(tr)
+    ref = O.render(rays, 64, stratified=False, given=gv)
     n = rays.shape[0]
     rng = np.random.default_rng(1)
     t_rgb = ref["rgb"] + rng.choice([-0.05, 0.05], size=(n, 3))
@@ -36,7 +38,7 @@ def test_normal_loss_matches_oracle(sdg, rgb_dtype):
     t_normal = ref["normal"] + rng.choice([-0.05, 0.05], size=(n, 3))
     L1, seeds = oracle.loss(ref["rgb"], ref["depth"], t_rgb, t_depth, 0.1)
     Ln, gN = oracle.loss_normal(ref["normal"], t_normal, 0.05)
-    want = O.backward(rays, 64, seeds["rgb"], seeds["depth"], stratified=False, g_normal=gN)
+    want = O.backward(rays, 64, seeds["rgb"], seeds["depth"], stratified=False, g_normal=gN, given=gv)
     assert np.abs(gN).max() > 0 and np.abs(ref["normal"]).max() > 0.5
     G.zero_grad()
     loss = torch.empty(n, device="cuda")

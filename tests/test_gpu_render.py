@@ -1,16 +1,21 @@
 """GPU parity of the rendering path (Sec. 3.5.1, Eq. 12-15; trilinear Eq. 17) against the FP64 oracle.
 
 Tolerances (FP32 on the GPU vs FP64): rendered colour / depth / opacity max-abs 1e-4; gradients relative 1e-3
-elementwise with a floor of 1e-5 of the channel's largest entry (FP32 atomics sum in arbitrary order).  Rays the
-oracle flags degenerate (a sample within rounding of a skip-space joint or of a plane where its stencil's
-validity flips) are excluded from the element-wise comparison and counted."""
+elementwise with a floor of 1e-5 of the channel's largest entry (FP32 atomics sum in arbitrary order).
+
+Every ray is compared.  The GPU exports where it placed each sample (sdg_debug_trace); check_placement asserts
+that this placement is the oracle's own up to FP32 rounding (a sample on a joint between allocated stretches may
+sit at either end of the joint, a cell at either side of a face within rounding), and the oracle, fed those
+samples, computes everything after the placement for every ray: forward outputs and the whole batch's gradients.
+Rays the oracle's own placement reproduces are also compared with the plain oracle."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import synth
-from tests.gpu_util import assert_grad_close, grad_arrays, tiny_room
+from tests.gpu_util import (assert_forward_all_rays, assert_grad_close, assert_trace_equals_render,
+                            check_placement, gpu_samples, grad_arrays, tiny_room)
 
 pytestmark = pytest.mark.gpu
 
@@ -34,37 +39,55 @@ def _view(sc, W=64, H=48, seed=0):
 
 
 def _cmp_forward(out, ref, nd, ns=0):
-    for k in ("rgb", "depth", "opac"):
+    """Rays the oracle's own placement reproduces (not flagged degenerate) against the plain oracle."""
+    for k in ("rgb", "depth", "opac") + (("sem",) if ns else ()):
         got = out[k].double().cpu().numpy()
         d = np.abs(got - ref[k])[nd]
-        assert d.max() <= TOL, (k, d.max())
-    if ns:
-        got = out["sem"].double().cpu().numpy()
-        d = np.abs(got - ref["sem"])[nd]
-        assert d.max() <= TOL * 10, ("sem", d.max())   # logits reach ~5 in magnitude
+        lim = TOL * 10 if k == "sem" else TOL   # logits reach ~5 in magnitude
+        assert d.size == 0 or d.max() <= lim, (k, d.max())
+
+
+def _all_rays(sdg, G, O, rays, N, seed=0, stratified=True, bg=(0, 0, 0), ns=0, ray_id0=0):
+    """Forward of every ray against the oracle fed the GPU's samples, after checking the placement; returns the
+    trace and the oracle's plain render (for the non-degenerate comparison)."""
+    out = sdg.render(G, rays.cuda(), N, seed=seed, stratified=stratified, bg=bg, ray_id0=ray_id0)
+    tr = sdg.trace(G, rays.cuda(), N, seed=seed, stratified=stratified, bg=bg, ray_id0=ray_id0)
+    assert_trace_equals_render(tr, out)
+    n_joint, n_tie = check_placement(O, rays, tr, N, seed=seed, ray_id0=ray_id0, stratified=stratified)
+    given = O.render(rays, N, seed=seed, stratified=stratified, bg=bg, ray_id0=ray_id0, given=gpu_samples(tr))
+    assert np.array_equal(given["n_valid"], tr["valid"].sum(1).double().cpu().numpy())  # same validity decisions
+    assert_forward_all_rays(out, given, TOL, ns)
+    ref = O.render(rays, N, seed=seed, stratified=stratified, bg=bg, ray_id0=ray_id0)
+    _cmp_forward(out, ref, ~ref["degenerate"], ns)
+    print(f"rays {len(rays)}: oracle-degenerate {ref['degenerate'].mean():.4f}, joint samples in {n_joint}, "
+          f"cell ties in {n_tie}")
+    return tr, ref
 
 
 @pytest.mark.parametrize("stratified,bg", [(True, (0, 0, 0)), (False, (0.2, 0.5, 0.9)), (True, (1, 1, 1))])
 def test_forward_matches_oracle(sdg, room, stratified, bg):
     sc, G, O, _, _ = room
     rays = _view(sc)
-    out = sdg.render(G, rays.cuda(), 64, seed=5, stratified=stratified, bg=bg)
-    ref = O.render(rays, 64, seed=5, stratified=stratified, bg=bg)
-    nd = ~ref["degenerate"]
-    assert nd.mean() > 0.97, nd.mean()
+    tr, ref = _all_rays(sdg, G, O, rays, 64, seed=5, stratified=stratified, bg=bg)
     assert ref["opac"].max() > 0.99 and ref["n_valid"].mean() > 30
-    _cmp_forward(out, ref, nd)
 
 
 @pytest.mark.parametrize("N", [1, 17, 48, 100, 128, 192, 256])
 def test_forward_sample_counts(sdg, room, N):
     sc, G, O, _, _ = room
     rays = _view(sc, 24, 16, seed=1)
-    out = sdg.render(G, rays.cuda(), N, seed=9)
-    ref = O.render(rays, N, seed=9)
-    nd = ~ref["degenerate"]
-    assert nd.mean() > 0.9
-    _cmp_forward(out, ref, nd)
+    _all_rays(sdg, G, O, rays, N, seed=9)
+
+
+def test_in_warp_traversal_matches_oracle(sdg, room):
+    """The in-warp traversal (serving loop, allocation-free pass): every ray against the oracle fed its samples."""
+    sc, G, O, _, _ = room
+    rays = _view(sc, 48, 32, seed=3)
+    tr = sdg.trace(G, rays.cuda(), 128, seed=2, walk="in_warp")
+    assert (tr["n_cells"] == -1).all()
+    check_placement(O, rays, tr, 128, seed=2)
+    given = O.render(rays, 128, seed=2, given=gpu_samples(tr))
+    assert_forward_all_rays(tr, given, TOL)
 
 
 def test_rays_missing_the_grid_and_empty_batches(sdg, room):
@@ -81,55 +104,27 @@ def test_rays_missing_the_grid_and_empty_batches(sdg, room):
     assert torch.all(oute["opac"] == 0)
 
 
-def _runs(mask):
-    """Contiguous runs [a, b) of True in mask."""
-    runs, a = [], None
-    for i, m in enumerate(list(mask) + [False]):
-        if m and a is None:
-            a = i
-        if not m and a is not None:
-            runs.append((a, i))
-            a = None
-    return runs
-
-
-def _gpu_backward_runs(sdg, G, rays, runs, N, seed, stratified, bg, seeds, mode):
-    G.zero_grad()
-    gc, gd, go, gs = seeds
-    for a, b in runs:
-        sl = slice(a, b)
-        o = sdg.render(G, rays[sl], N, seed=seed, ray_id0=a, stratified=stratified, bg=bg, want_ctx=True, mode=mode)
-        sdg.backward(o["ctx"], gc[sl], gd[sl], go[sl], None if gs is None else gs[sl])
-        o["ctx"].release()
-    torch.cuda.synchronize()
-    return grad_arrays(G, G.num_blocks)
-
-
-def _oracle_backward_runs(O, rays, runs, N, seed, stratified, bg, seeds):
-    gc, gd, go, gs = (None if s is None else s.double().cpu().numpy() for s in seeds)
-    tot = None
-    for a, b in runs:
-        g = O.backward(rays[a:b], N, gc[a:b], gd[a:b], go[a:b], None if gs is None else gs[a:b], seed=seed,
-                       ray_id0=a, stratified=stratified, bg=bg)
-        g = {k: g[k] for k in ("sdf", "rgb", "sem", "beta") if k in g}  # per-voxel arrays and the scalar beta
-        tot = g if tot is None else {k: tot[k] + g[k] for k in g}
-    return tot
-
-
 @pytest.mark.parametrize("mode", ["recompute", "store"])
 @pytest.mark.parametrize("stratified", [True, False])
 @pytest.mark.parametrize("N", [64, 192])  # 192: 6 samples per lane, where the forward reuses a cell's corners
 def test_backward_matches_oracle(sdg, room, mode, stratified, N):
+    """The whole batch's gradients against the oracle's backward over the GPU's samples (no ray left out)."""
     sc, G, O, _, _ = room
     rays = _view(sc, seed=2)
     bg = (0.3, 0.1, 0.7)
-    ref = O.render(rays, N, seed=3, stratified=stratified, bg=bg)
-    runs = _runs(~ref["degenerate"])
     n = len(rays)
     gen = torch.Generator().manual_seed(0)
-    seeds = tuple(torch.randn(s, generator=gen).cuda() for s in ((n, 3), (n,), (n,))) + (None,)
-    got = _gpu_backward_runs(sdg, G, rays.cuda(), runs, N, 3, stratified, bg, seeds, mode)
-    want = _oracle_backward_runs(O, rays.numpy(), runs, N, 3, stratified, bg, seeds)
+    gc, gd, go = (torch.randn(s, generator=gen) for s in ((n, 3), (n,), (n,)))
+    tr = sdg.trace(G, rays.cuda(), N, seed=3, stratified=stratified, bg=bg)
+    check_placement(O, rays, tr, N, seed=3, stratified=stratified)
+    G.zero_grad()
+    o = sdg.render(G, rays.cuda(), N, seed=3, stratified=stratified, bg=bg, want_ctx=True, mode=mode)
+    sdg.backward(o["ctx"], gc.cuda(), gd.cuda(), go.cuda())
+    o["ctx"].release()
+    torch.cuda.synchronize()
+    got = grad_arrays(G, G.num_blocks)
+    want = O.backward(rays.numpy(), N, gc.double().numpy(), gd.double().numpy(), go.double().numpy(), seed=3,
+                      stratified=stratified, bg=bg, given=gpu_samples(tr))
     assert_grad_close(got["sdf"], want["sdf"], what="sdf")
     assert_grad_close(got["rgb"], want["rgb"], what="rgb")
 
@@ -175,18 +170,19 @@ def test_autograd_function_accumulates_same_gradients(sdg, room):
 
 
 def test_fused_train_step_matches_oracle(sdg, room):
+    """Fused forward + L1 losses + backward over every ray of a view, against the oracle over the GPU's samples."""
     sc, G, O, _, _ = room
     rays = _view(sc, seed=6)
-    ref = O.render(rays, 64, stratified=False)
-    nd = ~ref["degenerate"]
-    rays = rays[torch.as_tensor(nd)]
-    ref = O.render(rays, 64, stratified=False)
+    tr = sdg.trace(G, rays.cuda(), 64, stratified=False)
+    check_placement(O, rays, tr, 64, stratified=False)
+    gv = gpu_samples(tr)
+    ref = O.render(rays, 64, stratified=False, given=gv)
     n = rays.shape[0]
     rng = np.random.default_rng(0)
     t_rgb = ref["rgb"] + rng.choice([-0.05, 0.05], size=(n, 3))
     t_depth = ref["depth"] + rng.choice([-0.1, 0.1], size=n)
     L, seeds = oracle.loss(ref["rgb"], ref["depth"], t_rgb, t_depth, 0.1)
-    want = O.backward(rays, 64, seeds["rgb"], seeds["depth"], stratified=False)
+    want = O.backward(rays, 64, seeds["rgb"], seeds["depth"], stratified=False, given=gv)
     G.zero_grad()
     loss = torch.empty(n, device="cuda")
     lsum = torch.empty(1, device="cuda")
@@ -214,31 +210,32 @@ def test_fused_train_step_matches_oracle(sdg, room):
 def test_bf16_and_semantics_match_oracle(sdg, n_sem):
     sc, G, O, stored, vals = tiny_room("bf16", n_sem)
     rays = _view(sc, 48, 32, seed=7)
-    out = sdg.render(G, rays.cuda(), 64, seed=4)
-    ref = O.render(rays, 64, seed=4)
-    nd = ~ref["degenerate"]
-    _cmp_forward(out, ref, nd, n_sem)
-    runs = _runs(nd)
+    tr, _ = _all_rays(sdg, G, O, rays, 64, seed=4, ns=n_sem)
     n = len(rays)
     gen = torch.Generator().manual_seed(1)
-    seeds = tuple(torch.randn(s, generator=gen).cuda() for s in ((n, 3), (n,), (n,), (n, n_sem)))
-    got = _gpu_backward_runs(sdg, G, rays.cuda(), runs, 64, 4, True, (0, 0, 0), seeds, "recompute")
-    want = _oracle_backward_runs(O, rays.numpy(), runs, 64, 4, True, (0, 0, 0), seeds)
+    seeds = tuple(torch.randn(s, generator=gen) for s in ((n, 3), (n,), (n,), (n, n_sem)))
+    G.zero_grad()
+    o = sdg.render(G, rays.cuda(), 64, seed=4, want_ctx=True)
+    sdg.backward(o["ctx"], *(x.cuda() for x in seeds))
+    o["ctx"].release()
+    torch.cuda.synchronize()
+    got = grad_arrays(G, G.num_blocks)
+    want = O.backward(rays.numpy(), 64, *(x.double().numpy() for x in seeds), seed=4, given=gpu_samples(tr))
     for k in ("sdf", "rgb", "sem"):
         assert_grad_close(got[k], want[k], what=k)
 
 
 def test_bf16_precision_vs_unrounded_fp64(sdg):
-    """Precision variant: BF16 colour/logit storage against the FP64 oracle on the unrounded values (errors
-    reported; bounded by the BF16 quantisation of the inputs, ~2^-9 relative)."""
+    """Precision variant: BF16 colour/logit storage against the FP64 oracle on the unrounded values, every ray fed
+    the GPU's samples (errors bounded by the BF16 quantisation of the inputs, ~2^-9 relative)."""
     sc, G, O, stored, vals = tiny_room("bf16", 20)
     Ofull = oracle.Grid(0.04, 0.02, 20).set(O.keys, vals["sdf"].astype(np.float32).astype(np.float64),
                                              vals["rgb"], vals["sem"])
     rays = _view(sc, 32, 24, seed=8)
     out = sdg.render(G, rays.cuda(), 64, seed=2)
-    ref = Ofull.render(rays, 64, seed=2)
-    nd = ~ref["degenerate"]
-    e_rgb = np.abs(out["rgb"].double().cpu().numpy() - ref["rgb"])[nd].max()
-    e_sem = np.abs(out["sem"].double().cpu().numpy() - ref["sem"])[nd].max()
-    e_d = np.abs(out["depth"].double().cpu().numpy() - ref["depth"])[nd].max()
+    tr = sdg.trace(G, rays.cuda(), 64, seed=2)
+    ref = Ofull.render(rays, 64, seed=2, given=gpu_samples(tr))
+    e_rgb = np.abs(out["rgb"].double().cpu().numpy() - ref["rgb"]).max()
+    e_sem = np.abs(out["sem"].double().cpu().numpy() - ref["sem"]).max()
+    e_d = np.abs(out["depth"].double().cpu().numpy() - ref["depth"]).max()
     assert e_rgb < 2 ** -8 and e_sem < 5 * 2 ** -8 and e_d < TOL

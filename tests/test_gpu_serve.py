@@ -1,5 +1,8 @@
 """Serving loop: continuous batching across scenes and resolutions; each result must equal the same request
-rendered alone (bit-for-bit: rays are computed independently of their batch mates) and match the oracle."""
+rendered alone (bit-for-bit: rays are computed independently of their batch mates) and match the oracle on every
+pixel: the served view's rays and sample placement are exported by sdg_debug_trace_view (the serving kernel's own
+ray and traversal code; its outputs equal the served result bit for bit), the placement is checked against the
+oracle's FP64 traversal, and the oracle renders every pixel from those samples."""
 import time
 
 import numpy as np
@@ -8,7 +11,7 @@ import torch
 
 import oracle
 import synth
-from tests.gpu_util import make_pair
+from tests.gpu_util import check_placement, gpu_samples, make_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -63,16 +66,20 @@ def test_mix_equals_alone_and_oracle(sdg, scenes):
         srv.release(t)
     st = srv.stats()
     assert st.completed == 24 and st.bytes_in_use == 0 and st.peak_bytes_in_use <= 64 << 20
-    # oracle parity for two of the requests
+    # oracle parity, every pixel, for two of the requests
     for i in (0, 7):
         s, W, H, T, K, N, seed = reqs[i]
-        rays = oracle.view_rays(H, W, K, T)
-        ref = scenes[s][2].render(rays, N, seed=seed)
-        nd = ~ref["degenerate"]
-        assert nd.mean() > 0.95
+        tr = sdg.trace_view(scenes[s][1], H, W, K, T, N, seed=seed)
         rgb, depth, opac = alone[i]
-        assert np.abs(rgb.double().cpu().numpy() - ref["rgb"])[nd].max() < 1e-4
-        assert np.abs(depth.double().cpu().numpy() - ref["depth"])[nd].max() < 1e-4
+        assert torch.equal(tr["rgb"].reshape(rgb.shape), rgb) and torch.equal(tr["depth"].reshape(depth.shape), depth)
+        assert torch.equal(tr["opac"].reshape(opac.shape), opac)
+        rays = tr["rays"].cpu().numpy()
+        np.testing.assert_allclose(rays, oracle.view_rays(H, W, K, T), atol=2e-6)  # the pinhole model itself
+        check_placement(scenes[s][2], rays, tr, N, seed=seed)
+        ref = scenes[s][2].render(rays, N, seed=seed, given=gpu_samples(tr))
+        assert np.abs(rgb.double().cpu().numpy().reshape(-1, 3) - ref["rgb"]).max() < 1e-4
+        assert np.abs(depth.double().cpu().numpy().reshape(-1) - ref["depth"]).max() < 1e-4
+        assert np.abs(opac.double().cpu().numpy().reshape(-1) - ref["opac"]).max() < 1e-4
     srv.close()
 
 
