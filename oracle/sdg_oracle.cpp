@@ -942,7 +942,9 @@ void orc_fuse(const int32_t* keys, int64_t N, float vs, int F, int H, int W, con
 //    the nearest remainder-0 lattice point r (coordinates multiples of d + 1, sum 0) found by
 //    rounding each coordinate and then moving the coordinates with the most extreme residuals by d + 1 until the
 //    sum is 0; the residual x - r ranked in decreasing order gives the simplex vertices r + c_j, j = 0..d, with
-//    c_j = j on the coordinates of rank < d + 1 - j and j - (d + 1) on the others, and the barycentric weights;
+//    c_j = j on the coordinates of rank < d + 1 - j and j - (d + 1) on the others;
+//  * barycentric weights (real-valued, FP64): the affine combination of the d + 1 vertices equal to the point
+//    elevated in FP64, by a dense linear solve;
 //  * splat: every point adds weight x value to its d + 1 vertices;
 //  * blur: along each of the d + 1 lattice directions o_k (d on coordinate k, -1 on the others), in order,
 //    v <- (v[- o_k] + 2 v + v[+ o_k]) / 4 over the splatted lattice points (absent neighbours are 0);
@@ -954,10 +956,36 @@ struct LatticeSimplex {
     std::vector<double> bary;                // d + 1 weights
 };
 
+// Solves the n x n system A y = b (row-major A) by Gaussian elimination with partial pivoting, in FP64.
+std::vector<double> solve_dense(std::vector<double> A, std::vector<double> b, int n) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) std::swap(A[(size_t)c * n + k], A[(size_t)piv * n + k]);
+            std::swap(b[c], b[piv]);
+        }
+        for (int r = c + 1; r < n; ++r) {
+            const double f = A[(size_t)r * n + c] / A[(size_t)c * n + c];
+            if (f == 0.0) continue;
+            for (int k = c; k < n; ++k) A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+            b[r] -= f * b[c];
+        }
+    }
+    std::vector<double> y(n);
+    for (int r = n - 1; r >= 0; --r) {
+        double acc = b[r];
+        for (int k = r + 1; k < n; ++k) acc -= A[(size_t)r * n + k] * y[k];
+        y[r] = acc / A[(size_t)r * n + r];
+    }
+    return y;
+}
+
 LatticeSimplex lattice_simplex(const double* pd, int d) {
-    // The simplex is an integer decision: it is taken in FP32 with this exact order (no fused multiply-add), so
-    // that any FP32 evaluation of the same order finds the same lattice points.
     const int d1 = d + 1;
+    // (1) Which simplex: an integer decision, taken in FP32 with this exact order (no fused multiply-add), so
+    // that any FP32 evaluation of the same order finds the same lattice points.  Elevation first.
     std::vector<float> x(d1, 0.0f);
     const float sc = (float)d1 * std::sqrt(2.0f / 3.0f);
     for (int i = 1; i <= d; ++i) {
@@ -965,42 +993,66 @@ LatticeSimplex lattice_simplex(const double* pd, int d) {
         for (int k = 0; k < i; ++k) x[k] += f;
         x[i] -= (float)i * f;
     }
+    // The nearest remainder-0 point: each coordinate rounded to the nearest multiple of d + 1 (half away from
+    // zero); if the rounded coordinates do not sum to 0, the |excess| coordinates whose residual x - r points
+    // the other way the most are moved by d + 1 towards x.  Residual order: decreasing, ties by coordinate index.
     std::vector<int64_t> r(d1);
-    int64_t sum = 0;
+    int64_t excess = 0;  // sum of r / (d + 1)
+    std::vector<float> res(d1);
     for (int k = 0; k < d1; ++k) {
         const int64_t q = (int64_t)std::llround(x[k] / (float)d1);
         r[k] = q * d1;
-        sum += q;
+        excess += q;
+        res[k] = x[k] - (float)r[k];
     }
-    std::vector<float> res(d1);
-    for (int k = 0; k < d1; ++k) res[k] = x[k] - (float)r[k];
-    std::vector<int> rank(d1, 0);
-    for (int k = 0; k < d1; ++k)
-        for (int m = 0; m < d1; ++m)
-            if (res[m] > res[k] || (res[m] == res[k] && m < k)) rank[k]++;
-    for (int k = 0; k < d1; ++k) {
-        rank[k] += (int)sum;
-        if (rank[k] >= d1) {
-            rank[k] -= d1;
-            r[k] -= d1;
-        } else if (rank[k] < 0) {
-            rank[k] += d1;
-            r[k] += d1;
+    std::vector<int> order(d1);
+    for (int k = 0; k < d1; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return res[a] > res[b]; });
+    // Moving a coordinate down by d + 1 raises its residual by d + 1, above every other residual (all lie within
+    // (d + 1) / 2 of 0), so it goes to the front of the order; moving one up sends it to the back.  Their
+    // relative order is kept.
+    std::vector<int> final_order;
+    if (excess > 0) {  // too high: lower the coordinates with the smallest residuals
+        for (int m = d1 - (int)excess; m < d1; ++m) {
+            r[order[m]] -= d1;
+            final_order.push_back(order[m]);
         }
+        for (int m = 0; m < d1 - (int)excess; ++m) final_order.push_back(order[m]);
+    } else if (excess < 0) {  // too low: raise the coordinates with the largest residuals
+        for (int m = (int)(-excess); m < d1; ++m) final_order.push_back(order[m]);
+        for (int m = 0; m < (int)(-excess); ++m) {
+            r[order[m]] += d1;
+            final_order.push_back(order[m]);
+        }
+    } else {
+        final_order = order;
     }
-    std::vector<float> b(d1 + 1, 0.0f);
-    for (int k = 0; k < d1; ++k) {
-        const float v = (x[k] - (float)r[k]) / (float)d1;
-        b[d - rank[k]] += v;
-        b[d1 - rank[k]] -= v;
-    }
-    b[0] += 1.0f + b[d1];
+    std::vector<int> rank(d1);
+    for (int m = 0; m < d1; ++m) rank[final_order[m]] = m;
+    // (2) The simplex's vertices, from the definition: v_j = r + c_j, where the canonical offset c_j is j on
+    // the d + 1 - j coordinates of highest residual rank and j - (d + 1) on the others.
     LatticeSimplex S;
-    S.bary.assign(d1, 0.0);
-    for (int j = 0; j < d1; ++j) S.bary[j] = (double)b[j];
     S.vert.assign(d1, std::vector<int64_t>(d1));
     for (int j = 0; j < d1; ++j)
         for (int k = 0; k < d1; ++k) S.vert[j][k] = r[k] + (rank[k] < d1 - j ? j : j - d1);
+    // (3) Barycentric weights, in FP64: the affine combination of the vertices that reproduces the elevated
+    // point (elevated again in FP64): sum_j b_j v_j = x, sum_j b_j = 1 (d coordinates + the affine row; the last
+    // coordinate follows, since every point involved sums to 0).
+    std::vector<double> xe(d1, 0.0);
+    const double scd = (double)d1 * std::sqrt(2.0 / 3.0);
+    for (int i = 1; i <= d; ++i) {
+        const double f = scd * pd[i - 1] / std::sqrt((double)i * (double)(i + 1));
+        for (int k = 0; k < i; ++k) xe[k] += f;
+        xe[i] -= (double)i * f;
+    }
+    std::vector<double> A((size_t)d1 * d1), rhs(d1);
+    for (int k = 0; k < d; ++k) {
+        for (int j = 0; j < d1; ++j) A[(size_t)k * d1 + j] = (double)S.vert[j][k];
+        rhs[k] = xe[k];
+    }
+    for (int j = 0; j < d1; ++j) A[(size_t)d * d1 + j] = 1.0;
+    rhs[d] = 1.0;
+    S.bary = solve_dense(A, rhs, d1);
     return S;
 }
 

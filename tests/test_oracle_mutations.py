@@ -90,10 +90,16 @@ MUTANTS = [
      [lambda: Cl.test_crf_loss_zero_at_target_and_matches_central_differences("normal")]),
     ("lattice_blur_weight", "w[(size_t)m * cc + q] = 0.25 * s2;", "w[(size_t)m * cc + q] = 0.5 * s2;",
      [La.test_d1_filter_is_the_grid_filter]),
-    ("lattice_no_rank_shift", "        rank[k] += (int)sum;\n", "",
+    ("lattice_no_excess_fix", "    if (excess > 0) {  // too high", "    if (excess > 0 && false) {  // too high",
      [lambda: La.test_simplex_is_the_enclosing_lattice_simplex(3)]),
-    ("lattice_bary_closure", "b[0] += 1.0f + b[d1];", "b[0] += 1.0f;",
+    ("lattice_canonical_offset", "S.vert[j][k] = r[k] + (rank[k] < d1 - j ? j : j - d1);",
+     "S.vert[j][k] = r[k] + (rank[k] <= d1 - j ? j : j - d1);",
      [lambda: La.test_simplex_is_the_enclosing_lattice_simplex(2)]),
+    ("lattice_affine_row", "    rhs[d] = 1.0;\n", "    rhs[d] = 0.5;\n",
+     [lambda: La.test_simplex_is_the_enclosing_lattice_simplex(2)]),
+    ("lattice_fp64_elevation", "const double f = scd * pd[i - 1] / std::sqrt((double)i * (double)(i + 1));",
+     "const double f = scd * pd[i - 1] / std::sqrt((double)i * (double)i);",
+     [lambda: La.test_simplex_is_the_enclosing_lattice_simplex(4)]),
     ("lattice_neighbour_offset", "const int64_t o = k == dir ? d : -1;", "const int64_t o = k == dir ? d + 1 : -1;",
      [La.test_d1_filter_is_the_grid_filter]),
     ("meanfield_sign", "e[l] = unary[i * L + l] + w * (tot - qt);", "e[l] = unary[i * L + l] - w * (tot - qt);",
