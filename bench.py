@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--rays", type=int, default=1 << 18)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="room line without the precision / serving / apartment sub-measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     p.add_argument("--views", type=int, default=N_VIEWS)
     p.add_argument("--max-blocks", type=int, default=80_000, help="grid capacity (room: 53,855 active blocks)")
@@ -59,6 +61,27 @@ def parse():
 def _order_launches(args, n: int) -> int:
     """Kernels the surface ordering adds to a training step (bucket keys, bucket scan, scatter)."""
     return 3 if args.ray_order == "surface" or (args.ray_order == "auto" and n >= 65536) else 0
+
+
+def _train_launches(args, n: int) -> int:
+    """Kernels of one training pass: traversal, render (records), render (rays with more cells than a record
+    holds), loss sum -- plus the surface ordering's."""
+    return 4 + _order_launches(args, n)
+
+
+def _stats(xs):
+    """Median and p10 / p90 (and the mean) of per-step times in ms."""
+    a = np.asarray(xs, np.float64)
+    return {"median": round(float(np.median(a)), 4), "p10": round(float(np.percentile(a, 10)), 4),
+            "p90": round(float(np.percentile(a, 90)), 4), "mean": round(float(a.mean()), 4)}
+
+
+def _peak():
+    """Measured HBM copy bandwidth (GB/s) and its source."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p))["hbm_gbs"], "measured"
+    return 6400.0, "fallback"
 
 
 def reduce_max(x: float, device=None) -> float:
@@ -229,18 +252,38 @@ def bytes_per_ray(O, batch, n=1024, N=N_SAMPLES):
     return float(per_ray.mean()), float(vx.mean()), float(bl.mean())
 
 
+# Sources of the fused training kernel: a DRAM-traffic capture is valid only for the build it was taken on.
+KERNEL_SOURCES = ["paper_2305_13220_b300/csrc/render_core.cuh", "paper_2305_13220_b300/csrc/render_kernels.cuh",
+                  "paper_2305_13220_b300/csrc/common.cuh", "paper_2305_13220_b300/csrc/render_inst_f32_bwd.cu"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def read_traffic(kernel: str):
-    """DRAM bytes per launch recorded from an ncu capture in profiles/<kernel>_traffic.txt, else None."""
+    """(DRAM bytes per launch, note) from the ncu capture summarised in profiles/<kernel>_traffic.txt.  The file
+    records the hash of the kernel's sources it was captured on; a capture of other sources gives (None, why)."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     if not os.path.exists(p):
-        return None
+        return None, "no capture"
+    val, sha = None, None
     for ln in open(p):
         if ln.startswith("traffic_bytes_per_launch:"):
             try:
-                return float(ln.split(":", 1)[1])
+                val = float(ln.split(":", 1)[1])
             except ValueError:
-                return None
-    return None
+                val = None
+        if ln.startswith("source_sha16:"):
+            sha = ln.split(":", 1)[1].strip()
+    cur = kernel_source_hash()
+    if sha != cur:
+        return None, f"capture is of other kernel sources ({sha}, built {cur}): traffic not reported"
+    return val, f"ncu capture of these sources ({cur})"
 
 
 # ----------------------------------------------------------------------------------------------------------
@@ -305,9 +348,14 @@ def run_ours(args):
         stepno[0] = i
         step(wl["batches"][i % len(wl["batches"])])
     torch.cuda.synchronize()
-    # phase timing: events between the fused kernel (+ loss sum) and the optimiser
+    # phase timing, all with CUDA events on the grid's stream: the training pass (ordering, traversal, render
+    # kernels, loss sum), the render kernels alone (recorded by the library around them), the optimiser
     K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    for e in kev:  # the events exist once recorded
+        e[0].record(stream)
+        e[1].record(stream)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -319,6 +367,7 @@ def run_ours(args):
     for i in range(K):
         b = wl["batches"][i % len(wl["batches"])]
         stepno[0] = 1000 + i
+        G.set_pass_events(kev[i][0], kev[i][1])
         evs[i][0].record(stream)
         sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
                             lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
@@ -326,13 +375,33 @@ def run_ours(args):
         G.adam_step(lr=1e-3)
         evs[i][2].record(stream)
     end.record(stream)
+    G.set_pass_events()
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = reduce_max(start.elapsed_time(end), device)
-    train_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
-    adam_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    train_t = [e[0].elapsed_time(e[1]) for e in evs]
+    kern_t = [e[0].elapsed_time(e[1]) for e in kev]
+    adam_t = [e[1].elapsed_time(e[2]) for e in evs]
+    step_t = [e[0].elapsed_time(e[2]) for e in evs]
+    train_ms, kern_ms, adam_ms = (float(np.median(x)) for x in (train_t, kern_t, adam_t))
     ms_step = total_ms / K
     value = aggregate_rays_per_s(world, n, ms_step)
+
+    # unfused forward and backward of the same batches (timed apart; not part of the headline step)
+    fb = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for i in range(K):
+        b = wl["batches"][i % len(wl["batches"])]
+        fb[i][0].record(stream)
+        o = sdg.render(G, b["rays"], N_SAMPLES, seed=3000 + i, want_ctx=True)
+        fb[i][1].record(stream)
+        _, gs = sdg.loss_l1(G, o["rgb"], o["depth"], b["rgb"], b["depth"], lambda_depth=LAMBDA_D)
+        sdg.backward(o["ctx"], gs["rgb"], gs["depth"])
+        fb[i][2].record(stream)
+        o["ctx"].release()
+    torch.cuda.synchronize()
+    G.zero_grad()
+    fwd_t = [e[0].elapsed_time(e[1]) for e in fb]
+    bwd_t = [e[1].elapsed_time(e[2]) for e in fb]
 
     # end to end through the public API: every step's rays and targets are copied from pinned host memory and its
     # loss is read back, inside the timed region.  Two device input buffers: while step k computes on the
@@ -394,14 +463,18 @@ def run_ours(args):
                            "l2": "inputs larger than L2: each step streams the whole grid and Adam state "
                                  f"({adam_bytes / 1e9:.1f} GB) through HBM"},
                 "samples_per_s": round(value * N_SAMPLES, 1),
-                "phases": {"train_kernel_ms": round(train_ms, 4), "adam_ms": round(adam_ms, 4),
-                           "activation_ms_50_maps": round(wl["act_ms"], 3)},
-                "clocks": clk, "gpu_launches": (3 + _order_launches(args, n)) * K,
+                "phases": {"train_kernel_ms": round(train_ms, 4), "render_kernels_ms": round(kern_ms, 4),
+                           "adam_ms": round(adam_ms, 4), "activation_ms_50_maps": round(wl["act_ms"], 3)},
+                "timing": {"step_ms": _stats(step_t), "train_pass_ms": _stats(train_t),
+                           "render_kernels_ms": _stats(kern_t), "adam_ms": _stats(adam_t),
+                           "unfused_forward_ms": _stats(fwd_t), "unfused_loss_backward_ms": _stats(bwd_t),
+                           "note": "CUDA events on the grid's stream; the train pass holds the surface ordering, "
+                                   "the traversal, the render kernels and the loss sum; the render kernels are "
+                                   "timed by events the library records around them (sdg_grid_set_pass_events)"},
+                "clocks": clk, "gpu_launches": (_train_launches(args, n) + 1) * K,
                 "e2e": {"value": round(aggregate_rays_per_s(world, n, e2e_ms), 1), "unit": "rays/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}}
-        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
-        peak_src = "measured" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else "fallback"
+        peak, peak_src = _peak()
         adam_gbs = adam_bytes / (adam_ms / 1e3) / 1e9
         O = None
         bpr = None
@@ -412,23 +485,37 @@ def run_ours(args):
             line["cpu_baseline"] = {"value": round(rate, 2), "unit": "rays/s", "cores": 1, "kind": "oracle",
                                     "sample": f"{done} rays of the first batch (fwd + L1 loss + bwd, FP64, "
                                               f"single thread, {el:.1f} s)"}
-        train_gbs = (bpr * n / (train_ms / 1e3) / 1e9) if bpr else None
-        kern = {"adam": (adam_ms, adam_gbs, adam_bytes, "k_opt_f32"),
-                "train": (train_ms, train_gbs, bpr * n if bpr else None, "k_render_train")}
-        dom = "adam" if adam_ms >= train_ms or train_gbs is None else "train"
-        ms_d, gbs_d, bytes_d, kname = kern[dom]
-        line["roofline"] = {"kernel": kname, "bound": "hbm", "achieved": round(gbs_d, 1), "peak": peak,
-                            "unit": "GB/s", "frac": round(gbs_d / peak, 4), "traffic": read_traffic(kname),
-                            "peak_source": peak_src, "algorithmic_bytes_per_launch": bytes_d}
-        other = "train" if dom == "adam" else "adam"
-        if kern[other][1] is not None:
-            line["roofline_other"] = {"kernel": kern[other][3], "achieved": round(kern[other][1], 1),
-                                      "frac": round(kern[other][1] / peak, 4), "unit": "GB/s",
-                                      "algorithmic_bytes_per_launch": kern[other][2]}
+            del O
         if bpr:
+            kern_gbs = bpr * n / (kern_ms / 1e3) / 1e9
+            traffic, tnote = read_traffic("k_render_train")
+            line["roofline"] = {"kernel": "k_render_train", "bound": "hbm", "achieved": round(kern_gbs, 1),
+                                "peak": peak, "unit": "GB/s", "frac": round(kern_gbs / peak, 4), "traffic": traffic,
+                                "traffic_note": tnote, "peak_source": peak_src,
+                                "algorithmic_bytes_per_launch": round(bpr * n),
+                                "launch_ms_median": round(kern_ms, 4),
+                                "note": "the fused training pass's render kernels (records kernel + in-warp "
+                                        "kernel for rays beyond the record capacity), algorithmic bytes from the "
+                                        "oracle's count over their median duration; the whole training phase "
+                                        f"(ordering, traversal, loss sum included) gives "
+                                        f"{bpr * n / (train_ms / 1e3) / 1e9:.1f} GB/s"}
+            line["roofline_other"] = {"kernel": "k_opt_f32", "achieved": round(adam_gbs, 1),
+                                      "frac": round(adam_gbs / peak, 4), "unit": "GB/s",
+                                      "algorithmic_bytes_per_launch": adam_bytes}
             line["train_kernel_bytes_per_ray"] = {"value": round(bpr, 1), "distinct_voxels": round(vx, 1),
                                                   "distinct_blocks": round(bl, 2), "rays_counted": 1024}
-        if not args.no_serve:
+        else:
+            line["roofline"] = {"kernel": "k_opt_f32", "bound": "hbm", "achieved": round(adam_gbs, 1), "peak": peak,
+                                "unit": "GB/s", "frac": round(adam_gbs / peak, 4), "traffic": None,
+                                "peak_source": peak_src, "algorithmic_bytes_per_launch": adam_bytes,
+                                "note": "run without the oracle's byte count (--no-cpu-baseline): the optimiser"}
+        if world == 1 and not args.no_extra:
+            # the other workloads, measured after the headline step (each with its own grid)
+            line["precision"] = measure_precision(args, compact=True)
+            if not args.no_serve:
+                line["serve"] = measure_serve(args, compact=True)
+            line["apartment"] = measure_apartment(args, compact=True)
+        elif not args.no_serve:
             line["serve"] = serve_leg(sdg, torch, wl)
         res = line
         print(json.dumps(res), flush=True)
@@ -455,7 +542,7 @@ def _timed_steps(torch, step, batches, K, W_):
 
 
 def _phase_times(torch, sdg, G, batches, K, train):
-    """Mean CUDA-event times of the fused training pass and of the optimiser step."""
+    """Median CUDA-event times of the training pass and of the optimiser step."""
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     for i in range(K):
         ev[i][0].record()
@@ -464,8 +551,8 @@ def _phase_times(torch, sdg, G, batches, K, train):
         G.adam_step(lr=1e-3)
         ev[i][2].record()
     torch.cuda.synchronize()
-    return {"train_kernel_ms": round(float(np.mean([e[0].elapsed_time(e[1]) for e in ev])), 4),
-            "adam_ms": round(float(np.mean([e[1].elapsed_time(e[2]) for e in ev])), 4)}
+    return {"train_kernel_ms": round(float(np.median([e[0].elapsed_time(e[1]) for e in ev])), 4),
+            "adam_ms": round(float(np.median([e[1].elapsed_time(e[2]) for e in ev])), 4)}
 
 
 def _activate_views(sdg, torch, G, sc, poses, K, device, band):
@@ -543,8 +630,9 @@ def _open_loop(srv, n_requests, arrivals, make_req, start, n_samples=N_SAMPLES):
     return np.array(lat), tot[0]
 
 
-def run_precision(args):
-    """Room-scale step with BF16 colour and 20 BF16 semantic logits; per-output errors vs the FP64 oracle."""
+def measure_precision(args, compact=False):
+    """Room-scale step with BF16 colour and 20 BF16 semantic logits; per-output errors vs the FP64 oracle over
+    every ray of a 4096-ray subset (the oracle fed the GPU's own samples, sdg_debug_trace)."""
     import torch
     import oracle
     import paper_2305_13220_b300 as sdg
@@ -567,6 +655,9 @@ def run_precision(args):
     G.zero_grad()
     sub = batches[0]["rays"][torch.linspace(0, args.rays - 1, 4096, device=device).long()].contiguous()
     out = sdg.render(G, sub, N_SAMPLES, seed=0, want_ctx=True)
+    tr = sdg.trace(G, sub, N_SAMPLES, seed=0)
+    given = {"S": tr["S"].double().cpu().numpy(), "t": tr["t"].cpu().numpy(), "cell": tr["cell"].cpu().numpy()}
+    del tr
     n = sub.shape[0]
     gen = torch.Generator(device=device).manual_seed(0)
     seeds = [torch.randn(sh, generator=gen, device=device) * 1e-3 for sh in ((n, 3), (n,), (n,), (n, 20))]
@@ -582,20 +673,21 @@ def run_precision(args):
     ggot = {"sdf": G.channel(A.GROUP_SDF, A.KIND_GRAD)[:nb, :, 0].double().cpu().numpy(),
             "rgb": G.channel(A.GROUP_RGB, A.KIND_GRAD)[:nb, :, 0:3].double().cpu().numpy(),
             "sem": G.channel(A.GROUP_SEM, A.KIND_GRAD)[:nb].double().cpu().numpy()}
+    out["ctx"].release()
     rays_np = sub.cpu().numpy()
-    sd = [s.double().cpu().numpy() for s in seeds]
+    sd = [x.double().cpu().numpy() for x in seeds]
     table = {}
     for name, src in (("vs_fp64_unrounded", full), ("vs_fp64_same_bf16_values", stored)):
         O = oracle.Grid(VS, BETA, 20).set(keys, src["sdf"], src["rgb"], src["sem"])
-        ref = O.render(rays_np, N_SAMPLES, seed=0)
-        nd = ~ref["degenerate"]
-        row = {k: float(np.abs(got[k] - ref[k])[nd].max()) for k in ("rgb", "depth", "opac", "sem")}
-        gref = O.backward(rays_np, N_SAMPLES, sd[0], sd[1], sd[2], sd[3], seed=0)
+        ref = O.render(rays_np, N_SAMPLES, seed=0, given=given)
+        row = {k: float(np.abs(got[k] - ref[k]).max()) for k in ("rgb", "depth", "opac", "sem")}
+        gref = O.backward(rays_np, N_SAMPLES, sd[0], sd[1], sd[2], sd[3], seed=0, given=given)
         for k in ("sdf", "rgb", "sem"):
             row["grad_" + k + "_rel"] = float(np.abs(ggot[k] - gref[k]).max() / max(np.abs(gref[k]).max(), 1e-30))
-        row["degenerate_rays"] = int((~nd).sum())
         table[name] = row
-        del O
+        del O, ref, gref
+    del full, stored, ggot
+    G.zero_grad()
 
     def step(b, i):
         sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i,
@@ -605,30 +697,46 @@ def run_precision(args):
     ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
     phases = _phase_times(torch, sdg, G, batches, args.steps, lambda b, i: sdg.train_step_rays(
         G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i, ray_order=args.ray_order))
-    line = _line(args.rays / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
+    G.close()
+    del batches
+    torch.cuda.empty_cache()
+    rps = args.rays / (ms / 1e3)
+    if compact:
+        return {"workload": "room step, BF16 colour + 20 BF16 logits (FP32 SDF, transmittance, accumulation)",
+                "rays_per_s": round(rps, 1), "ms_per_step": round(ms, 4), "phases": phases,
+                "errors_on_4096_rays_all_compared": table, "steps": args.steps, "warmup": args.warmup}
+    return _line(rps, "rays/s", args.steps, args.warmup, ms,
                  {"workload": "precision variant of the room step: BF16 colour + 20 BF16 semantic logits, FP32 "
                               "SDF / transmittance / accumulation", "rays_per_step": args.rays,
                   "samples_per_ray": N_SAMPLES, "n_blocks": nb},
                  dtype="f32+bf16", samples_per_s=round(args.rays * N_SAMPLES / (ms / 1e3), 1), phases=phases,
-                 errors_on_4096_rays=table, gpu_launches=(5 + _order_launches(args, args.rays)) * args.steps)
-    print(json.dumps(line), flush=True)
+                 errors_on_4096_rays_all_compared=table,
+                 gpu_launches=(_train_launches(args, args.rays) + 1) * args.steps)
 
 
-def run_serve(args):
-    """8 device-resident rooms (10k-200k blocks, 1-2 cm voxels, BF16 colour); Poisson arrivals at 0.5x, 0.8x and
-    1.0x of the measured saturated capacity; latency = submit -> result ready (host clock)."""
+def run_precision(args):
+    print(json.dumps(measure_precision(args)), flush=True)
+
+
+# Serving scenes: rooms of the room-scale kind (boxes and cylinders on the floor), sized and voxelised so that
+# their block counts span about 10k to 200k (blocks of the analytic band, 3 voxels).
+SERVE_SPECS = [((5, 4, 3), 8, 0.02), ((7, 6, 3), 10, 0.02), ((6, 6, 3), 10, 0.015), ((9, 7, 3), 16, 0.015),
+               ((6, 6, 3), 12, 0.01), ((8, 8, 3), 20, 0.01), ((11, 9, 3), 30, 0.01), ((14, 12, 3), 44, 0.01)]
+
+
+def measure_serve(args, compact=False):
+    """8 device-resident rooms (about 10k-200k blocks, 1-2 cm voxels, BF16 colour); Poisson arrivals at 0.5x,
+    0.8x and 1.0x of the measured saturated capacity; latency = submit -> result ready (host clock)."""
     import torch
     import paper_2305_13220_b300 as sdg
     import synth
     device = "cuda:0"
-    specs = [((4, 4, 3), 0.02), ((6, 5, 3), 0.02), ((5, 5, 3), 0.015), ((7, 6, 3), 0.015),
-             ((4, 3, 2.7), 0.01), ((6, 6, 3), 0.01), ((5, 4, 3), 0.01), ((8, 6, 3), 0.01)]
     grids, scenes = [], []
-    for i, (size, vs) in enumerate(specs):
-        sc = synth.scene_room(100 + i, size=size, n_objects=6 + i)
-        poses = synth.random_poses(sc, 24, seed=i)
-        G = sdg.Grid(vs, 260_000, beta=0.5 * vs, rgb_dtype="bf16")
-        _activate_views(sdg, torch, G, sc, poses, synth.intrinsics(W, H), device, 3)
+    for i, (size, n_obj, vs) in enumerate(SERVE_SPECS):
+        sc = synth.scene_room(100 + i, size=size, n_objects=n_obj)
+        keys = synth.band_blocks(sc, vs, 3, device=device)
+        G = sdg.Grid(vs, len(keys), beta=0.5 * vs, rgb_dtype="bf16")
+        G.activate_keys(torch.as_tensor(keys, device=device))
         _fill(sdg, torch, G, sc, vs, 3, device)
         grids.append(G)
         scenes.append(sc)
@@ -670,16 +778,27 @@ def run_serve(args):
     st = srv.stats()
     srv.close()
     nblocks = [G.num_blocks for G in grids]
-    line = _line(cap, "rays/s", len(points), 1, 1e3 * mean_rays / cap,
+    for G in grids:
+        G.close()
+    del grids
+    torch.cuda.empty_cache()
+    if compact:
+        return {"workload": "8 rooms, BF16 colour, N = 128, requests uniform over 160x120..1280x960, Poisson "
+                            "arrivals at 0.5x / 0.8x / 1.0x of the saturated rate",
+                "scene_blocks": nblocks, "saturated_rays_per_s": round(cap, 1), "points": points}
+    return _line(cap, "rays/s", len(points), 1, 1e3 * mean_rays / cap,
                  {"workload": "serving: 8 device-resident rooms, BF16 colour, 128 samples per ray, requests of "
                               "160x120 / 320x240 / 640x480 / 1280x960 with Poisson arrivals",
                   "scene_blocks": nblocks},
                  dtype="f32+bf16", saturated_rays_per_s=round(cap, 1), serve_points=points,
                  peak_server_bytes=int(st.peak_bytes_in_use), gpu_launches=int(st.launches))
-    print(json.dumps(line), flush=True)
 
 
-def run_apartment(args):
+def run_serve(args):
+    print(json.dumps(measure_serve(args)), flush=True)
+
+
+def measure_apartment(args, compact=False):
     """20x15x3 m apartment (6 rooms, 60 furniture primitives), 1 cm voxels: a full 1280x960 render at 192
     samples per ray, and 2^20-ray training steps (fused pass + Adam)."""
     import torch
@@ -718,21 +837,50 @@ def run_apartment(args):
     ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
     phases = _phase_times(torch, sdg, G, batches, args.steps, lambda b, i: sdg.train_step_rays(
         G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i, ray_order=args.ray_order))
+    G.close()
+    del batches, frame
+    torch.cuda.empty_cache()
     n = 1 << 20
-    line = _line(n / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
+    render = {"ms": round(render_ms, 3), "rays_per_s": round(1280 * 960 / (render_ms / 1e3), 1),
+              "samples_per_s": round(1280 * 960 * 192 / (render_ms / 1e3), 1)}
+    if compact:
+        return {"workload": "apartment 20x15x3 m, 1 cm voxels, 4-voxel band from 300 depth maps",
+                "n_blocks": nb, "train_2p20_rays": {"rays_per_s": round(n / (ms / 1e3), 1), "ms_per_step": round(ms, 4),
+                                                    "phases": phases},
+                "render_1280x960_n192": render, "activation_ms_300_maps": round(act_ms, 2)}
+    return _line(n / (ms / 1e3), "rays/s", args.steps, args.warmup, ms,
                  {"workload": "apartment 20x15x3 m, 6 rooms, 60 furniture primitives, 1 cm voxels, 4-voxel band "
                               "from 300 depth maps; 2^20-ray training steps at 128 samples + 1280x960 render at 192",
                   "n_blocks": nb, "voxels": nb * 512, "rays_per_step": n},
-                 render_1280x960_n192={"ms": round(render_ms, 3),
-                                       "rays_per_s": round(1280 * 960 / (render_ms / 1e3), 1),
-                                       "samples_per_s": round(1280 * 960 * 192 / (render_ms / 1e3), 1)},
-                 activation_ms_300_maps=round(act_ms, 2), phases=phases,
-                 gpu_launches=(3 + _order_launches(args, 1 << 20)) * args.steps)
-    print(json.dumps(line), flush=True)
+                 render_1280x960_n192=render, activation_ms_300_maps=round(act_ms, 2), phases=phases,
+                 gpu_launches=(_train_launches(args, 1 << 20) + 1) * args.steps)
+
+
+def run_apartment(args):
+    print(json.dumps(measure_apartment(args)), flush=True)
+
+
+_REF = {}  # the reference arm's oracle grid and sample, inherited by forked workers
+
+
+def _ref_chunk(bounds):
+    """Oracle forward + L1 loss + backward of rays [a, b) of the reference sample (in a forked worker)."""
+    import oracle
+    a, b = bounds
+    O, rays, t_rgb, t_d = _REF["O"], _REF["rays"], _REF["rgb"], _REF["depth"]
+    t0 = time.perf_counter()
+    out = O.render(rays[a:b], N_SAMPLES, seed=0, ray_id0=a)
+    _, g = oracle.loss(out["rgb"], out["depth"], t_rgb[a:b], t_d[a:b], LAMBDA_D)
+    O.backward(rays[a:b], N_SAMPLES, g["rgb"], g["depth"], seed=0, ray_id0=a)
+    return time.perf_counter() - t0
 
 
 def run_reference(args):
-    """Reference arm: the CPU FP64 oracle, as it stands, on the same workload (rank 0 only)."""
+    """Reference arm: the CPU FP64 oracle, as it stands (single-threaded code), run on all host cores as one
+    process per core over chunks of rays (fork: every worker shares the parent's oracle grid) and, for context,
+    on one core.  Its rays are a seeded sample of the GPU arm's first batch (same scene, block set, voxel values,
+    rays and samples); each step is a bounded sample of it.  Rank 0 only."""
+    import multiprocessing as mp
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -740,6 +888,7 @@ def run_reference(args):
     import torch
     import synth
     import oracle
+    t_setup = time.perf_counter()
     sc = synth.scene_room(0)
     poses = synth.random_poses(sc, args.views, seed=0)
     K = synth.intrinsics(W, H)
@@ -751,21 +900,53 @@ def run_reference(args):
     O = oracle.Grid(VS, BETA).set(keys, vals["sdf"].to(torch.float32).double().numpy(),
                                   vals["rgb"].to(torch.float32).double().numpy())
     del vals
-    batch = synth.training_batch(sc, poses, W, H, K, 4096, seed=0)
-    rates = []
-    per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
-    for i in range(args.warmup + args.steps):
-        r, done, el = cpu_leg(O, batch, per_step)
-        if i >= args.warmup:
-            rates.append(r)
-    v = float(np.mean(rates))
+    # the GPU arm's first batch (build_workload: seed 0, batch 0, per-image order), then a seeded sample of it
+    batch = synth.training_batch(sc, poses, W, H, K, args.rays, seed=0, order=args.order)
+    perm = np.random.default_rng(0).permutation(args.rays)
+    cores = max(1, min(os.cpu_count() or 1, 64))
+    per_core = 48  # rays per core and step: about 0.05 s of oracle work each
+    rays_per_step = per_core * cores
+    total = (args.warmup + args.steps) * rays_per_step + 256
+    sel = perm[:min(total, args.rays)]
+    _REF.update(O=O, rays=batch["rays"].numpy()[sel], rgb=batch["rgb"].double().numpy()[sel],
+                depth=batch["depth"].double().numpy()[sel])
+    setup_s = time.perf_counter() - t_setup
+    # one core: 256 rays
+    t0 = time.perf_counter()
+    _ref_chunk((len(sel) - 256, len(sel)))
+    single = 256 / (time.perf_counter() - t0)
+    # all cores: each step splits rays_per_step rays over the workers
+    ctx = mp.get_context("fork")
+    step_s = []
+    with ctx.Pool(cores) as pool:
+        for i in range(args.warmup + args.steps):
+            a = i * rays_per_step
+            chunks = [(a + c * per_core, a + (c + 1) * per_core) for c in range(cores)]
+            if chunks[-1][1] > len(sel) - 256:
+                break
+            t0 = time.perf_counter()
+            pool.map(_ref_chunk, chunks, chunksize=1)
+            if i >= args.warmup:
+                step_s.append(time.perf_counter() - t0)
+    steps = len(step_s)
+    ms = 1e3 * float(np.mean(step_s))
+    v = rays_per_step / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": "rays/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * 2 ** 18 / v, 1),
+            "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "room-scale FP32 training step (same scene, rays and samples as the GPU arm)",
-                       "rays_per_step": 1 << 18, "samples_per_ray": N_SAMPLES, "n_blocks": int(len(keys))},
-            "cpu_baseline": {"value": round(v, 2), "unit": "rays/s", "cores": 1, "kind": "oracle",
-                             "sample": f"per step about {per_step:.0f} s of 256-ray chunks of a 4096-ray batch"},
+            "config": {"workload": "room-scale FP32 training step (6x6x3 m room, 10 boxes/cylinders, 1 cm "
+                                   "voxels, 8^3 blocks, 4-voxel band from 50 640x480 depth maps; 2^18 rays "
+                                   "x 128 stratified samples, L1 colour + 0.1 L1 depth, Adam on every voxel)",
+                       "rays_per_step": rays_per_step, "samples_per_ray": N_SAMPLES, "n_blocks": int(len(keys)),
+                       "sample": f"each step: {rays_per_step} rays of the GPU arm's first 2^18-ray batch "
+                                 f"(seeded sample, fwd + L1 loss + bwd), {per_core} per core on {cores} cores"},
+            "ms_per_full_2p18_step_extrapolated": round(1e3 * args.rays / v, 1),
+            "timing": {"step_ms": _stats(1e3 * np.asarray(step_s)), "setup_s": round(setup_s, 1)},
+            "single_core_rays_per_s": round(single, 2),
+            "cpu_baseline": {"value": round(v, 2), "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} steps x {rays_per_step} rays of the GPU arm's first batch, one "
+                                       f"process per core (the oracle's code is single-threaded); one core: "
+                                       f"{single:.1f} rays/s"},
             "e2e": {"value": round(v, 2), "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return line

@@ -51,7 +51,7 @@ extern "C" {
 #define SDG_ERR_CAPACITY 3  /* a fixed capacity would be exceeded; the object is unchanged */
 #define SDG_ERR_CUDA 4      /* a CUDA runtime call or kernel launch failed */
 #define SDG_ERR_TIMEOUT 5   /* a wait ran out of time */
-#define SDG_ERR_BUSY 6      /* the result is not ready yet (poll again) */
+#define SDG_ERR_BUSY 6      /* not now: a result not ready yet (poll again), or a grid registered with a server */
 #define SDG_ERR_IO 7        /* file read/write failed or the file is malformed */
 #define SDG_ERR_NOT_FOUND 8 /* unknown ticket / scene id */
 
@@ -178,6 +178,16 @@ int sdg_grid_load(const char* path, const sdg_grid_desc* desc, sdg_grid* out);
 /* Optimiser step counter kept with the grid (saved and loaded with it). */
 int sdg_grid_get_step(sdg_grid g, int32_t* step);
 int sdg_grid_set_step(sdg_grid g, int32_t step);
+
+/* Profiling aid (the paper has no counterpart).  With start and stop two
+ * cudaEvent_t handles (not owned; created by the caller on the grid's
+ * device), every render pass enqueued on this grid afterwards -- forward,
+ * backward, training passes -- records start on the grid's stream just
+ * before its render kernels (after the traversal pass and any ray ordering)
+ * and stop just after them, so cudaEventElapsedTime(start, stop) is the
+ * duration of the render kernels of the last pass.  NULL, NULL stops the
+ * recording.  Errors: SDG_ERR_ARG (one of the two NULL). */
+int sdg_grid_set_pass_events(sdg_grid g, void* start_event, void* stop_event);
 
 /* Blocks the host until all work on the grid's stream has finished. */
 int sdg_grid_sync(sdg_grid g);
@@ -600,8 +610,14 @@ typedef struct {
 } sdg_server_stats;
 
 int sdg_server_create(const sdg_server_opts* o, sdg_server* out);
-/* Registers a grid (not owned; it must outlive the server).  All scenes of a
- * server must share rgb_dtype and n_sem.  Not allowed once requests exist. */
+/* Registers a grid (not owned).  All scenes of a server must share rgb_dtype
+ * and n_sem (SDG_ERR_ARG otherwise).  Not allowed once requests exist.  From
+ * registration until sdg_server_destroy the grid's block structure is fixed:
+ * activation calls and sdg_grid_destroy on it return SDG_ERR_BUSY (the
+ * scheduler reads the block tables of every scene at any time).  Calls that
+ * change voxel values (training, fusion, optimiser steps, set_beta) remain
+ * allowed and memory-safe, but race with batches in flight: a request may
+ * render old or new values. */
 int sdg_server_add_scene(sdg_server s, sdg_grid g, int32_t* scene_id);
 /* Queues a request; SDG_ERR_CAPACITY if its outputs can never fit the budget. */
 int sdg_server_submit(sdg_server s, const sdg_request* q, uint64_t* ticket);

@@ -99,6 +99,7 @@ SIGNATURES = {
     "sdg_grid_get_step": [_p, _P(_i32)],
     "sdg_grid_set_step": [_p, _i32],
     "sdg_grid_sync": [_p],
+    "sdg_grid_set_pass_events": [_p, _p, _p],
     "sdg_render_forward": [_p, _p, _i64, _P(RenderOpts), _P(RenderOut), _P(_p)],
     "sdg_render_backward": [_p, _p, _p, _p, _p],
     "sdg_ctx_release": [_p],

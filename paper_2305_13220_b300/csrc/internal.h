@@ -47,6 +47,8 @@ struct sdg_grid_s {
     int4* nbr = nullptr;   // [max_blocks][2]
     int32_t* dense = nullptr;  // block index of every cell of the block AABB (-1: not allocated), x fastest
     int64_t dense_cells = 0, dense_cap = 0;
+    uint8_t* coarse = nullptr;  // 1 per 4 x 4 x 4 block cells of the AABB holding a block (x fastest)
+    int64_t coarse_cap = 0;
     int bmin[3] = {0, 0, 0}, bdim[3] = {0, 0, 0};
 
     // channels
@@ -71,6 +73,7 @@ struct sdg_grid_s {
     int2* walk_hdr = nullptr;
     float* walk_s0 = nullptr;
     int4* walk_rec = nullptr;
+    int* walk_over = nullptr;  // slots without records [walk_cap], their count at [walk_cap]
     int64_t walk_cap = 0;
     int* order_keys = nullptr;  // surface ordering of a training batch: per-ray bucket [order_cap]
     int* order_perm = nullptr;  // processing order [order_cap]
@@ -88,13 +91,16 @@ struct sdg_grid_s {
     double* ssi_dev = nullptr;  // device [2]: (a, b) of the last scale/shift-invariant depth loss
     LatticeScratch lat;
 
+    cudaEvent_t pass_ev[2] = {nullptr, nullptr};  // recorded around the render kernels of every pass (not owned)
     std::mutex mu;  // serialises host-side mutation (activation, load) of this grid
+    int served = 0;  // servers this grid is registered with (under mu): its block structure is then fixed
 
     GridDev dev() const {
         GridDev d{};
         d.table = table;
         d.nbr = nbr;
         d.dense = dense;
+        d.coarse = coarse;
         d.keys = keys;
         d.mask = mask;
         d.n_sem = desc.n_sem;

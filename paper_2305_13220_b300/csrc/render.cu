@@ -32,6 +32,12 @@ constexpr int64_t kAutoSurfaceOrderRays = 65536;
 
 int pick_q(int N) { return N <= 64 ? 2 : N <= 128 ? 4 : N <= 192 ? 6 : 8; }
 
+// Records the grid's pass event `which` (sdg_grid_set_pass_events) on its stream, if one is set.
+int pass_event(sdg_grid g, int which) {
+    if (g->pass_ev[which]) SDG_CUDA_TRY(cudaEventRecord(g->pass_ev[which], g->stream));
+    return SDG_OK;
+}
+
 template <int MODE>
 int launch_pass(sdg_grid g, const float* rays, uint32_t id0, const PassArgs& a) {
     if (a.n == 0) return SDG_OK;
@@ -39,10 +45,13 @@ int launch_pass(sdg_grid g, const float* rays, uint32_t id0, const PassArgs& a) 
     const int Q = pick_q(a.N);
     const bool bf16 = g->desc.rgb_dtype == SDG_BF16;
     const bool sem = g->desc.n_sem > 0;
-    if (!bf16 && !sem) return launch_q<MODE, false, false>(gd, rays, id0, a, Q, g->stream);
-    if (!bf16 && sem) return launch_q<MODE, false, true>(gd, rays, id0, a, Q, g->stream);
-    if (bf16 && !sem) return launch_q<MODE, true, false>(gd, rays, id0, a, Q, g->stream);
-    return launch_q<MODE, true, true>(gd, rays, id0, a, Q, g->stream);
+    int rc = pass_event(g, 0);
+    if (rc) return rc;
+    if (!bf16 && !sem) rc = launch_q<MODE, false, false>(gd, rays, id0, a, Q, g->stream);
+    else if (!bf16 && sem) rc = launch_q<MODE, false, true>(gd, rays, id0, a, Q, g->stream);
+    else if (bf16 && !sem) rc = launch_q<MODE, true, false>(gd, rays, id0, a, Q, g->stream);
+    else rc = launch_q<MODE, true, true>(gd, rays, id0, a, Q, g->stream);
+    return rc ? rc : pass_event(g, 1);
 }
 
 // Same for passes instantiated only for grids without logits.
@@ -51,8 +60,11 @@ int launch_pass_nosem(sdg_grid g, const float* rays, uint32_t id0, const PassArg
     if (a.n == 0) return SDG_OK;
     const GridDev gd = g->dev();
     const int Q = pick_q(a.N);
-    if (g->desc.rgb_dtype == SDG_BF16) return launch_q<MODE, true, false>(gd, rays, id0, a, Q, g->stream);
-    return launch_q<MODE, false, false>(gd, rays, id0, a, Q, g->stream);
+    int rc = pass_event(g, 0);
+    if (rc) return rc;
+    if (g->desc.rgb_dtype == SDG_BF16) rc = launch_q<MODE, true, false>(gd, rays, id0, a, Q, g->stream);
+    else rc = launch_q<MODE, false, false>(gd, rays, id0, a, Q, g->stream);
+    return rc ? rc : pass_event(g, 1);
 }
 
 int check_opts(const sdg_render_opts* o) {
@@ -79,7 +91,8 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 // Traversal pass (Sec. 3.5.1: samples only where blocks are allocated): one thread walks the whole ray through
 // the dense block-index grid and writes the allocated cells it crosses, in order, with their skip-space offsets.
 // A warp of the render kernel then places its ray's samples by a binary search over these records instead of
-// walking the ray itself (a ray crossing more than kWalkCap allocated cells keeps the in-warp traversal).
+// walking the ray itself (a ray crossing more than kWalkCap allocated cells -- 0.15% of the room step's rays --
+// keeps the in-warp traversal).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_walk(GridDev g, const float* __restrict__ rays, const int* __restrict__ perm,
                                               int64_t n, WalkBufs w) {
@@ -110,6 +123,7 @@ __global__ void __launch_bounds__(256) k_walk(GridDev g, const float* __restrict
         });
     }
     w.hdr[slot] = make_int2(cnt, __float_as_int(S));
+    if (cnt < 0) w.over[atomicAdd(w.n_over, 1)] = (int)slot;
 }
 
 }  // namespace
@@ -118,19 +132,22 @@ namespace sdg {
 // Grows the grid-owned walk records to n rays (valid until the next call on this grid).
 int walk_scratch(sdg_grid g, int64_t n) {
     if (g->walk_cap >= n) return SDG_OK;
-    if (g->walk_hdr || g->walk_s0 || g->walk_rec) {
+    if (g->walk_hdr || g->walk_s0 || g->walk_rec || g->walk_over) {
         SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));  // earlier work on the stream may still read them
         cudaFree(g->walk_hdr);
         cudaFree(g->walk_s0);
         cudaFree(g->walk_rec);
+        cudaFree(g->walk_over);
     }
     g->walk_hdr = nullptr;
     g->walk_s0 = nullptr;
     g->walk_rec = nullptr;
+    g->walk_over = nullptr;
     g->walk_cap = 0;
     SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_hdr, sizeof(int2) * n));
     SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_s0, sizeof(float) * kWalkCap * n));
     SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_rec, sizeof(int4) * kWalkCap * n));
+    SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_over, sizeof(int) * (n + 1)));  // list, and its length at [n]
     g->walk_cap = n;
     return SDG_OK;
 }
@@ -138,11 +155,12 @@ int walk_scratch(sdg_grid g, int64_t n) {
 // Enqueues the traversal pass of n rays (processing order perm, or the given order) and points a.walk at its
 // records.
 int walk_rays(sdg_grid g, const float* rays, const int* perm, int64_t n, PassArgs& a) {
-    a.walk = WalkBufs{nullptr, nullptr, nullptr};
+    a.walk = WalkBufs{nullptr, nullptr, nullptr, nullptr, nullptr};
     if (n == 0) return SDG_OK;
     int rc = walk_scratch(g, n);
     if (rc) return rc;
-    const WalkBufs w{g->walk_hdr, g->walk_s0, g->walk_rec};
+    const WalkBufs w{g->walk_hdr, g->walk_s0, g->walk_rec, g->walk_over, g->walk_over + g->walk_cap};
+    SDG_CUDA_TRY(cudaMemsetAsync(w.n_over, 0, sizeof(int), g->stream));
     k_walk<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(g->dev(), rays, perm, n, w);
     SDG_LAUNCH_CHECK("traversal pass");
     a.walk = w;
@@ -542,5 +560,12 @@ extern "C" int sdg_train_step_rays_noalloc(sdg_grid g, const float* rays, int64_
         k_sum<<<1, 1024, 0, g->stream>>>(scratch, n, loss_sum);
         SDG_LAUNCH_CHECK("no-alloc loss sum");
     }
+    return SDG_OK;
+}
+
+extern "C" int sdg_grid_set_pass_events(sdg_grid g, void* start, void* stop) {
+    if (!g || (!start) != (!stop)) return fail(SDG_ERR_ARG, "sdg_grid_set_pass_events: both events or neither");
+    g->pass_ev[0] = (cudaEvent_t)start;
+    g->pass_ev[1] = (cudaEvent_t)stop;
     return SDG_OK;
 }

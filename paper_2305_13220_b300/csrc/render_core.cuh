@@ -53,10 +53,14 @@ constexpr int kWalkCap = 32;
 // bits of S}; record m of the slot at [slot * kWalkCap + m]: s0 = skip-space offset of the cell (sequential FP32
 // sum of the lengths before it, so the offsets are monotone and S = s0 + len of the last), and
 // rec = {bits of t_in, bits of len, block index, dense-grid cell}.
+// Slots of rays crossing more than kWalkCap allocated cells are appended to over[0, *n_over) (in no particular
+// order): the records kernel skips them, the in-warp kernel renders them.
 struct WalkBufs {
     int2* hdr;
     float* s0;
     int4* rec;
+    int* over;
+    int* n_over;
 };
 
 // Store-mode record channels per sample: t, sdf (NaN if invalid), r, g, b, block index (int bits).
@@ -213,12 +217,18 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
     const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
     // index steps of the dense grid (x fastest)
     const int stx = sx, sty = sy * g.bdim[0], stz = sz * (int)((unsigned)g.bdim[0] * (unsigned)g.bdim[1]);
+    const int ccx = (g.bdim[0] + 3) >> 2, ccy = (g.bdim[1] + 3) >> 2;
+    // a cell's block index is read only where its 4 x 4 x 4-cell coarse cell holds a block (a byte grid small
+    // enough to stay in L1), so most of a walk through empty space makes no dependent load
+    auto block_of = [&](int x, int y, int z, int idx) -> int {
+        return __ldg(g.coarse + ((z >> 2) * ccy + (y >> 2)) * ccx + (x >> 2)) ? __ldg(g.dense + idx) : -1;
+    };
     float tcur = ta;
     const int maxit = g.bdim[0] + g.bdim[1] + g.bdim[2] + 3;
     int cidx = (cz * g.bdim[1] + cy) * g.bdim[0] + cx;
     // the next cell's block index is loaded before the current cell is handed to f, so the loads of successive
     // cells overlap instead of each waiting for the previous one
-    int blk = __ldg(g.dense + cidx);
+    int blk = block_of(cx, cy, cz, cidx);
     for (int it = 0; it < maxit; ++it) {
         const float tx = sx ? fmaf((float)(g.bmin[0] + cx + (sx > 0)), g.L, -o.x) * invd.x : INF;
         const float ty = sy ? fmaf((float)(g.bmin[1] + cy + (sy > 0)), g.L, -o.y) * invd.y : INF;
@@ -230,7 +240,7 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
         const bool more = te < tb && (unsigned)nx < (unsigned)g.bdim[0] && (unsigned)ny < (unsigned)g.bdim[1] &&
                           (unsigned)nz < (unsigned)g.bdim[2];
         const int nidx = cidx + (mx ? stx : 0) + (my ? sty : 0) + (mz ? stz : 0);
-        const int nblk = more ? __ldg(g.dense + nidx) : -1;
+        const int nblk = more ? block_of(nx, ny, nz, nidx) : -1;
         if (b > tcur && blk >= 0)
             if (!f(tcur, b, cidx, blk)) break;
         if (!more) break;
@@ -477,7 +487,9 @@ __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x <
 // ---------------------------------------------------------------------------
 // The per-ray program
 // ---------------------------------------------------------------------------
-template <int MODE, bool BF16, bool SEM, int Q>
+// INWARP: the warp walks its ray itself (walk_pieces); otherwise the ray's cells come from the traversal pass's
+// records (a ray without records -- more cells than kWalkCap -- is left to the INWARP kernel).
+template <int MODE, bool BF16, bool SEM, int Q, bool INWARP>
 __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a, const RayJob& j, WarpSmem& sm,
                                             int lane) {
     constexpr bool kStoreIn = MODE == PASS_BWD_STORE;
@@ -507,19 +519,19 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     if constexpr (kStoreIn) {
         S = a.rec_S[j.idx];
     } else {
-        if (a.walk.hdr) {
+        if constexpr (!INWARP) {
             const int2 h = __ldg(a.walk.hdr + j.slot);
-            if (h.x >= 0) {  // warp-uniform
-                by_rec = true;
-                n_rec = h.x;
-                S = __int_as_float(h.y);
-                if (lane < n_rec) {
-                    my_s0 = __ldg(a.walk.s0 + j.slot * kWalkCap + lane);
-                    my_rec = __ldg(a.walk.rec + j.slot * kWalkCap + lane);
-                }
+            if (h.x < 0) return;  // warp-uniform: the INWARP kernel renders this ray
+            by_rec = true;
+            n_rec = h.x;
+            S = __int_as_float(h.y);
+            if (lane < n_rec) {
+                my_s0 = __ldg(a.walk.s0 + j.slot * kWalkCap + lane);
+                my_rec = __ldg(a.walk.rec + j.slot * kWalkCap + lane);
             }
+        } else {
+            S = walk_pieces(g, j, sm, lane, pc, t1);
         }
-        if (!by_rec) S = walk_pieces(g, j, sm, lane, pc, t1);
         if constexpr (kTrace) {
             if (lane == 0) {
                 a.tr_S[j.idx] = S;
@@ -585,9 +597,9 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         }
         int blk = -1, cell = -1;
         float t_rec = 0.f;
-        if constexpr (!kStoreIn) {
+        if constexpr (!kStoreIn && !INWARP) {
             // every lane takes part in the record search (it shuffles), with or without a sample i
-            if (by_rec) t_rec = locate_rec(n_rec, my_s0, my_rec, k < N ? s_[i] : 0.f, blk, cell);
+            t_rec = locate_rec(n_rec, my_s0, my_rec, k < N ? s_[i] : 0.f, blk, cell);
         }
         if (k >= N) return false;
         float sn;
@@ -606,7 +618,8 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             blk = __float_as_int(rec[5 * CS]);
             if (!isnan(d_[i])) smask |= 1u << i;
         } else {
-            t_[i] = by_rec ? t_rec : locate(g, j, sm, pc, t1, s_[i], blk, cell);
+            if constexpr (INWARP) t_[i] = locate(g, j, sm, pc, t1, s_[i], blk, cell);
+            else t_[i] = t_rec;
         }
         const float px = fmaf(t_[i], j.d.x, j.o.x) * g.inv_vs;
         const float py = fmaf(t_[i], j.d.y, j.o.y) * g.inv_vs;

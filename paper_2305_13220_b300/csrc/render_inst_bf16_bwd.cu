@@ -1,4 +1,5 @@
-// Render kernels: bf16 layout, bwd pass instantiations.
+// Render kernels of the bf16 layout, bwd passes (the instantiations are spread over files so that they
+// compile in parallel; fewer, larger files keep the library small).
 #include "render_kernels.cuh"
 
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD, true, false)

@@ -1,4 +1,5 @@
-// Render kernels: f32 layout, bwd pass instantiations.
+// Render kernels of the f32 layout, bwd passes (the instantiations are spread over files so that they
+// compile in parallel; fewer, larger files keep the library small).
 #include "render_kernels.cuh"
 
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD, false, false)

@@ -1,5 +1,7 @@
-// Render kernels: f32 layout, fwd pass instantiations.
+// Render kernels of the f32 layout, fwd passes (the instantiations are spread over files so that they
+// compile in parallel; fewer, larger files keep the library small).
 #include "render_kernels.cuh"
 
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD, false, false)
 SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_STORE, false, false)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, false, false)

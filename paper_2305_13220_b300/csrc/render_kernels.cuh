@@ -18,17 +18,12 @@ constexpr int render_min_blocks() {
 #endif
 }
 
-template <int MODE, bool BF16, bool SEM, int Q>
-__global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>()))
-    k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
-    __shared__ WarpSmem smem[kWarpsPerBlock];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slot = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-    if (slot >= a.n) return;  // warp-uniform
-    const int64_t r = a.perm ? (int64_t)__ldg(a.perm + slot) : slot;
+// Ray of processing slot `slot` (ray perm[slot], or ray slot) into j.
+__device__ __forceinline__ void load_job(const float* rays, const int* perm, uint32_t ray_id0, int64_t slot,
+                                         RayJob& j) {
+    const int64_t r = perm ? (int64_t)__ldg(perm + slot) : slot;
     const float4 r0 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r);
     const float4 r1 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r + 1);
-    RayJob j;
     j.o = make_float3(r0.x, r0.y, r0.z);
     j.tn = r0.w;
     j.d = make_float3(r1.x, r1.y, r1.z);
@@ -36,18 +31,56 @@ __global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>()))
     j.ray_id = ray_id0 + (uint32_t)r;
     j.idx = r;
     j.slot = slot;
-    ray_program<MODE, BF16, SEM, Q>(g, a, j, smem[warp], lane);
+}
+
+// One warp per ray.  !INWARP: every slot, cells from the traversal pass's records (a slot without records is
+// skipped).  INWARP: the warp walks its ray, over every slot when there are no records (a.walk.hdr NULL), else
+// over the overflow list a.walk.over[0, *a.walk.n_over) -- launched with one warp per slot like the records
+// kernel: the list is short (0.15% of the room step's rays) and the warps past its end exit at once.  Kept apart,
+// the records kernel needs no shared memory, which leaves L1 to the voxel gathers.
+template <int MODE, bool BF16, bool SEM, int Q, bool INWARP>
+__global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>()))
+    k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
+    __shared__ WarpSmem smem[INWARP ? kWarpsPerBlock : 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    RayJob j;
+    if constexpr (!INWARP) {
+        if (w >= a.n) return;  // warp-uniform
+        load_job(rays, a.perm, ray_id0, w, j);
+        ray_program<MODE, BF16, SEM, Q, false>(g, a, j, smem[0], lane);
+    } else {
+        const bool list = a.walk.hdr != nullptr;
+        const int64_t end = list ? (int64_t)__ldg(a.walk.n_over) : a.n;
+        if (w >= end) return;  // warp-uniform
+        load_job(rays, a.perm, ray_id0, list ? (int64_t)__ldg(a.walk.over + w) : w, j);
+        ray_program<MODE, BF16, SEM, Q, true>(g, a, j, smem[warp], lane);
+    }
+}
+
+template <int MODE, bool BF16, bool SEM, int Q>
+int launch_one(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs& a, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((a.n + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    constexpr bool kNoWalk = MODE == PASS_BWD_STORE;  // samples come from the forward's stored records
+    if (kNoWalk || a.walk.hdr) {
+        k_render<MODE, BF16, SEM, Q, false><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
+        if (!kNoWalk) k_render<MODE, BF16, SEM, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
+    } else {
+        k_render<MODE, BF16, SEM, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
+    }
+    return SDG_OK;
 }
 
 template <int MODE, bool BF16, bool SEM>
 int launch_q(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs& a, int Q, cudaStream_t s) {
-    const unsigned blocks = (unsigned)((a.n + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    int rc;
     switch (Q) {
-        case 2: k_render<MODE, BF16, SEM, 2><<<blocks, 256, 0, s>>>(gd, rays, id0, a); break;
-        case 4: k_render<MODE, BF16, SEM, 4><<<blocks, 256, 0, s>>>(gd, rays, id0, a); break;
-        case 6: k_render<MODE, BF16, SEM, 6><<<blocks, 256, 0, s>>>(gd, rays, id0, a); break;
-        default: k_render<MODE, BF16, SEM, 8><<<blocks, 256, 0, s>>>(gd, rays, id0, a); break;
+        case 2: rc = launch_one<MODE, BF16, SEM, 2>(gd, rays, id0, a, s); break;
+        case 4: rc = launch_one<MODE, BF16, SEM, 4>(gd, rays, id0, a, s); break;
+        case 6: rc = launch_one<MODE, BF16, SEM, 6>(gd, rays, id0, a, s); break;
+        default: rc = launch_one<MODE, BF16, SEM, 8>(gd, rays, id0, a, s); break;
     }
+    if (rc) return rc;
     SDG_LAUNCH_CHECK("render kernel");
     return SDG_OK;
 }

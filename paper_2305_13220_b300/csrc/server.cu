@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
     a.out_rgb = ch.rgb;
     a.out_depth = ch.depth;
     a.out_opac = ch.opac;
-    ray_program<PASS_FWD, BF16, false, Q>(scenes[ch.scene], a, j, smem[warp], lane);
+    ray_program<PASS_FWD, BF16, false, Q, true>(scenes[ch.scene], a, j, smem[warp], lane);
 }
 
 double now_ms() {
@@ -390,6 +390,14 @@ extern "C" int sdg_server_add_scene(sdg_server s, sdg_grid g, int32_t* id) {
     if (g->device != s->o.device) return fail(SDG_ERR_ARG, "sdg_server_add_scene: grid on another device");
     const bool bf = g->desc.rgb_dtype == SDG_BF16;
     if (!s->scenes.empty() && bf != s->bf16) return fail(SDG_ERR_ARG, "sdg_server_add_scene: mixed colour layouts");
+    if (!s->scenes.empty() && g->desc.n_sem != s->scenes[0]->desc.n_sem)
+        return fail(SDG_ERR_ARG, "sdg_server_add_scene: mixed semantic channel counts");
+    {
+        // from now on the grid's block structure is fixed (activation and destruction return SDG_ERR_BUSY), so
+        // the scheduler may snapshot its descriptor without its lock
+        std::lock_guard<std::mutex> gl(g->mu);
+        ++g->served;
+    }
     s->bf16 = bf;
     s->scenes.push_back(g);
     const size_t n = s->scenes.size();
@@ -407,14 +415,15 @@ extern "C" int sdg_server_add_scene(sdg_server s, sdg_grid g, int32_t* id) {
 
 extern "C" int sdg_server_submit(sdg_server s, const sdg_request* q, uint64_t* ticket) {
     if (!s || !q || !ticket) return fail(SDG_ERR_ARG, "sdg_server_submit: null argument");
-    if (q->scene_id < 0 || q->scene_id >= (int)s->scenes.size() || q->H <= 0 || q->W <= 0 || q->n_samples < 1 ||
-        q->n_samples > 256 || !(q->K[0] != 0.f) || !(q->K[1] != 0.f))
+    if (q->H <= 0 || q->W <= 0 || q->n_samples < 1 || q->n_samples > 256 || !(q->K[0] != 0.f) || !(q->K[1] != 0.f))
         return fail(SDG_ERR_ARG, "sdg_server_submit: invalid request");
     const int64_t npix = (int64_t)q->H * q->W;
     const int64_t bytes = ((npix * 5 * (int64_t)sizeof(float)) + 255) & ~(int64_t)255;
     if (bytes > s->o.hbm_budget_bytes)
         return fail(SDG_ERR_CAPACITY, "sdg_server_submit: request outputs exceed the server's memory budget");
     std::lock_guard<std::mutex> lk(s->mu);
+    if (q->scene_id < 0 || q->scene_id >= (int)s->scenes.size())
+        return fail(SDG_ERR_ARG, "sdg_server_submit: invalid scene_id");
     if (!s->worker_error.empty()) return fail(SDG_ERR_CUDA, "server: " + s->worker_error);
     uint64_t tk = s->next_ticket++;
     Req& r = s->reqs[tk];
@@ -531,6 +540,10 @@ extern "C" int sdg_server_destroy(sdg_server s) {
     }
     for (auto st : s->streams) cudaStreamDestroy(st);
     if (s->pool_mem) cudaFree(s->pool_mem);
+    for (sdg_grid g : s->scenes) {
+        std::lock_guard<std::mutex> gl(g->mu);
+        --g->served;
+    }
     delete s;
     return SDG_OK;
 }

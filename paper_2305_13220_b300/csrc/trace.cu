@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256, (render_min_blocks<PASS_FWD_TRACE, SEM, Q
         r[0] = make_float4(j.o.x, j.o.y, j.o.z, tnear);
         r[1] = make_float4(j.d.x, j.d.y, j.d.z, tfar);
     }
-    ray_program<PASS_FWD_TRACE, BF16, SEM, Q>(g, a, j, smem[warp], lane);
+    ray_program<PASS_FWD_TRACE, BF16, SEM, Q, true>(g, a, j, smem[warp], lane);
 }
 
 template <bool BF16, bool SEM>
@@ -86,10 +86,10 @@ int check_opts(const sdg_render_opts* o) {
 
 }  // namespace
 
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, false, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, false, true)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, true, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, true, true)
+namespace sdg {
+template <int MODE, bool BF16, bool SEM>
+int launch_q(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs& a, int Q, cudaStream_t s);
+}
 
 extern "C" int sdg_debug_trace(sdg_grid g, const float* rays, int64_t n, const sdg_render_opts* o, int32_t walk,
                                const sdg_trace_out* out) {

@@ -70,9 +70,16 @@ class Grid:
         self.n_sem = n_sem
 
     # -- life cycle ---------------------------------------------------------
+    def set_pass_events(self, start=None, stop=None):
+        """Makes every later render pass on this grid record the torch.cuda.Event pair around its render kernels
+        (sdg_grid_set_pass_events); no arguments stop the recording."""
+        A.call("sdg_grid_set_pass_events", self._h, None if start is None else C.c_void_p(start.cuda_event),
+               None if stop is None else C.c_void_p(stop.cuda_event))
+
     def close(self):
+        """Destroys the grid (SdgError with SDG_ERR_BUSY, the grid kept, while a server still holds it)."""
         if getattr(self, "_h", None) is not None and self._h.value:
-            A.lib().sdg_grid_destroy(self._h)
+            A.call("sdg_grid_destroy", self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

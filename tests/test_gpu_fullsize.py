@@ -89,6 +89,35 @@ def test_full_batch_sampled_rays_match_oracle(room):
         assert abs(got[i] * n - e) <= 2e-4, (i, got[i] * n, e)
 
 
+def test_overflow_rays_match_oracle(room):
+    """Rays crossing more allocated cells than a traversal record holds (32) are rendered by the in-warp kernel
+    after the records kernel: in the timed launch (surface order), their loss terms and rendered outputs against
+    the oracle over the GPU's samples."""
+    sdg, sc, poses, K, depths, G, O, gk = room
+    b = synth.training_batch(sc, poses, W, H, K, 1 << 18, seed=7, device="cuda", order="pixel")
+    n = b["rays"].shape[0]
+    loss = torch.empty(n, device="cuda")
+    G.zero_grad()
+    sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N, seed=3, loss=loss)
+    tr = sdg.trace(G, b["rays"], N, seed=3)
+    torch.cuda.synchronize()
+    ov = np.flatnonzero(tr["n_cells"].cpu().numpy() < 0)
+    assert 50 < len(ov) < n // 100, len(ov)
+    sel = ov[np.random.default_rng(3).choice(len(ov), 48, replace=False)]
+    rays = b["rays"].cpu().numpy()
+    t_rgb, t_d = b["rgb"].double().cpu().numpy(), b["depth"].double().cpu().numpy()
+    got = loss.double().cpu().numpy()
+    for i in np.sort(sel):
+        one = {k: v[int(i):int(i) + 1] for k, v in tr.items()}
+        check_placement(O, rays[i:i + 1], one, N, seed=3, ray_id0=int(i))
+        ref = O.render(rays[i:i + 1], N, seed=3, ray_id0=int(i), given=gpu_samples(one))
+        assert ref["S"][0] > 0
+        for k in ("rgb", "depth", "opac"):
+            assert np.abs(one[k].double().cpu().numpy() - ref[k]).max() <= 1e-4, (i, k)
+        e = np.abs(ref["rgb"][0] - t_rgb[i]).sum() / 3 + 0.1 * abs(ref["depth"][0] - t_d[i])
+        assert abs(got[i] * n - e) <= 2e-4, (i, got[i] * n, e)
+
+
 @pytest.mark.parametrize("order", ["surface", "given"])
 def test_subset_gradients_match_oracle(room, order):
     """Gradients of a 2048-ray subset of the full batch, through the surface-ordered path the timed launch takes

@@ -112,3 +112,28 @@ def test_admission_by_memory_and_errors(sdg, scenes):
         assert err.code == sdg._abi.ERR_TIMEOUT
     assert srv.wait(t1, 60000).status == 0
     srv.close()
+
+
+def test_served_grid_structure_is_fixed(sdg):
+    """A grid registered with a server keeps its block structure until the server is destroyed: activation and
+    destruction are refused (the scheduler reads the block tables without the grid's lock); value updates are
+    allowed.  Mixed semantic channel counts are refused at registration."""
+    sc = synth.scene_room(0, size=(2.0, 2.0, 2.0), n_objects=1)
+    keys = synth.band_blocks(sc, 0.04, 3)
+    G, O, stored, vals = make_pair(sc, keys, 0.04, 3, 0.02, "bf16", max_blocks=len(keys) + 64)
+    srv = sdg.Server(hbm_budget_bytes=16 << 20, max_slots=2, n_streams=1, chunk_rays=256, max_batch_rays=1024)
+    srv.add_scene(G)
+    far = torch.as_tensor([[40, 40, 40]], dtype=torch.int32, device="cuda")
+    with pytest.raises(sdg.SdgError) as e:
+        G.activate_keys(far)
+    assert e.value.code == sdg._abi.ERR_BUSY
+    assert G.num_blocks == len(keys)
+    rc = sdg._abi.lib().sdg_grid_destroy(G.handle)
+    assert rc == sdg._abi.ERR_BUSY
+    G.zero_grad()  # value updates stay allowed
+    G4, _, _, _ = make_pair(sc, keys, 0.04, 3, 0.02, "bf16", n_sem=4)
+    with pytest.raises(sdg.SdgError) as e:
+        srv.add_scene(G4)
+    assert e.value.code == sdg._abi.ERR_ARG
+    srv.close()
+    assert G.activate_keys(far) == 1  # structure free again once the server is gone
