@@ -720,8 +720,8 @@ def run_precision(args):
 
 # Serving scenes: rooms of the room-scale kind (boxes and cylinders on the floor), sized and voxelised so that
 # their block counts span about 10k to 200k (blocks of the analytic band, 3 voxels).
-SERVE_SPECS = [((5, 4, 3), 8, 0.02), ((7, 6, 3), 10, 0.02), ((6, 6, 3), 10, 0.015), ((9, 7, 3), 16, 0.015),
-               ((6, 6, 3), 12, 0.01), ((8, 8, 3), 20, 0.01), ((11, 9, 3), 30, 0.01), ((14, 12, 3), 44, 0.01)]
+SERVE_SPECS = [((6, 5, 3), 10, 0.02), ((8, 6, 3), 12, 0.02), ((6, 6, 3), 10, 0.015), ((9, 7, 3), 16, 0.015),
+               ((6, 6, 3), 12, 0.01), ((8, 8, 3), 20, 0.01), ((12, 9, 3), 30, 0.01), ((17, 14, 3), 60, 0.01)]
 
 
 def measure_serve(args, compact=False):

@@ -134,7 +134,6 @@ struct GridDev {
     const ulonglong2* table;  // hash slots
     const int4* nbr;          // [N][2] int4: block index of +{0,x,y,xy,z,xz,yz,xyz} neighbours, -1 if absent
     const int32_t* dense;     // block index of every cell of the block AABB (-1: not allocated), x fastest
-    const uint8_t* coarse;    // 1 per 4 x 4 x 4 cells of the AABB holding any block, dims (bdim + 3) / 4
     const int4* keys;         // [N] {x, y, z, 0}
     uint32_t mask;
     int32_t n_sem;

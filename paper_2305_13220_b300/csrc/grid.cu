@@ -338,7 +338,7 @@ void free_grid_buffers(sdg_grid g) {
     void* ptrs[] = {g->table, g->tmp_table, g->keys, g->nbr, g->dense, g->geo, g->ggeo, g->m_geo, g->v_geo,
                     g->sdf, g->gsdf, g->m_sdf, g->v_sdf, g->rgbh, g->grgb, g->m_rgb, g->v_rgb, g->sem, g->gsem,
                     g->m_sem, g->v_sem, g->weight, g->sort_buf, g->counters, g->minmax, g->loss_buf,
-                    g->walk_hdr, g->walk_s0, g->walk_rec, g->walk_over, g->coarse,
+                    g->walk_hdr, g->walk_s0, g->walk_rec, g->walk_over,
                     g->order_keys, g->order_perm, g->order_hist, g->fuse_cams, g->beta_grad, g->beta_part,
                     g->ssi_dev, g->lat.fp, g->lat.idx, g->lat.skey, g->lat.keys, g->lat.vidx, g->lat.vbary,
                     g->lat.val0, g->lat.val1, g->lat.nb, g->lat.counters, g->lat.fq, g->lat.sr, g->lat.srank,
@@ -368,34 +368,14 @@ int sort_keys(sdg_grid g, int64_t n) {
 }
 
 // Makes the dense block-index grid hold at least `cells` cells (the old contents are not kept).
-// Coarse occupancy cells of a block AABB of dims d: 4 x 4 x 4 block cells each.
-int64_t coarse_cells(const int64_t d[3]) { return ((d[0] + 3) >> 2) * ((d[1] + 3) >> 2) * ((d[2] + 3) >> 2); }
-
-int reserve_dense(sdg_grid g, int64_t cells, int64_t ccells) {
-    if (cells > g->dense_cap) {
-        int32_t* nd = nullptr;
-        SDG_CUDA_TRY(device_malloc((void**)&nd, cells * sizeof(int32_t)));
-        if (g->dense) cudaFree(g->dense);
-        g->dense = nd;
-        g->dense_cap = cells;
-    }
-    if (ccells > g->coarse_cap) {
-        uint8_t* nc = nullptr;
-        SDG_CUDA_TRY(device_malloc((void**)&nc, ccells));
-        if (g->coarse) cudaFree(g->coarse);
-        g->coarse = nc;
-        g->coarse_cap = ccells;
-    }
+int reserve_dense(sdg_grid g, int64_t cells) {
+    if (cells <= g->dense_cap) return SDG_OK;
+    int32_t* nd = nullptr;
+    SDG_CUDA_TRY(device_malloc((void**)&nd, cells * sizeof(int32_t)));
+    if (g->dense) cudaFree(g->dense);
+    g->dense = nd;
+    g->dense_cap = cells;
     return SDG_OK;
-}
-
-// coarse[cell of block i] = 1 for every block: the 4 x 4 x 4-block cells holding at least one block.
-__global__ void k_coarse(const int4* __restrict__ keys, int64_t n, int bx, int by, int bz, int cx, int cy,
-                         uint8_t* coarse) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int4 k = keys[i];
-        coarse[((int64_t)((k.z - bz) >> 2) * cy + ((k.y - by) >> 2)) * cx + ((k.x - bx) >> 2)] = 1;
-    }
 }
 
 // Recomputes the AABB (from all keys), the dense block-index grid and the neighbour table.
@@ -414,23 +394,18 @@ int rebuild_derived(sdg_grid g) {
     SDG_LAUNCH_CHECK("minmax");
     SDG_CUDA_TRY(cudaMemcpyAsync(g->h_minmax, g->minmax, sizeof(init), cudaMemcpyDeviceToHost, g->stream));
     SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    int64_t cells = 1, dims[3];
+    int64_t cells = 1;
     for (int a = 0; a < 3; ++a) {
         g->bmin[a] = g->h_minmax[a];
         g->bdim[a] = g->h_minmax[3 + a] - g->h_minmax[a] + 1;
         cells *= g->bdim[a];
-        dims[a] = g->bdim[a];
     }
-    const int64_t ccells = coarse_cells(dims);
-    int rc = reserve_dense(g, cells, ccells);
+    int rc = reserve_dense(g, cells);
     if (rc) return rc;
     g->dense_cells = cells;
     SDG_CUDA_TRY(cudaMemsetAsync(g->dense, 0xFF, cells * sizeof(int32_t), g->stream));
-    SDG_CUDA_TRY(cudaMemsetAsync(g->coarse, 0, ccells, g->stream));
     k_dense<<<grid_blocks(N), kThreads, 0, g->stream>>>(g->keys, N, g->bmin[0], g->bmin[1], g->bmin[2], g->bdim[0],
                                                         g->bdim[1], g->dense);
-    k_coarse<<<grid_blocks(N), kThreads, 0, g->stream>>>(g->keys, N, g->bmin[0], g->bmin[1], g->bmin[2],
-                                                         (g->bdim[0] + 3) >> 2, (g->bdim[1] + 3) >> 2, g->coarse);
     k_neighbours<<<grid_blocks(N), kThreads, 0, g->stream>>>(g->keys, N, g->table, g->mask, g->nbr);
     SDG_LAUNCH_CHECK("block index/neighbours");
     return SDG_OK;
@@ -482,15 +457,12 @@ int finish_activation(sdg_grid g, int64_t* n_new) {
     k_minmax<<<grid_blocks(cnt), kThreads, 0, g->stream>>>(g->sort_buf, (int64_t)cnt, g->minmax);
     SDG_CUDA_TRY(cudaMemcpyAsync(g->h_minmax, g->minmax, sizeof(init), cudaMemcpyDeviceToHost, g->stream));
     SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
-    int64_t cells = 1, dims[3];
-    for (int a = 0; a < 3; ++a) {
-        dims[a] = (int64_t)g->h_minmax[3 + a] - g->h_minmax[a] + 1;
-        cells *= dims[a];
-    }
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) cells *= (int64_t)g->h_minmax[3 + a] - g->h_minmax[a] + 1;
     if (cells > kMaxDenseCells)
         return fail(SDG_ERR_CAPACITY, "activation: block bounding box exceeds 2^31 blocks; grid unchanged");
     // every allocation happens before the first insertion, so a failure leaves the grid unchanged
-    rc = reserve_dense(g, cells, coarse_cells(dims));
+    rc = reserve_dense(g, cells);
     if (rc) return rc;
     k_insert<<<grid_blocks(cnt), kThreads, 0, g->stream>>>(g->sort_buf, (int64_t)cnt, g->n_blocks, g->table, g->mask,
                                                             g->keys, g->counters);

@@ -47,8 +47,6 @@ struct sdg_grid_s {
     int4* nbr = nullptr;   // [max_blocks][2]
     int32_t* dense = nullptr;  // block index of every cell of the block AABB (-1: not allocated), x fastest
     int64_t dense_cells = 0, dense_cap = 0;
-    uint8_t* coarse = nullptr;  // 1 per 4 x 4 x 4 block cells of the AABB holding a block (x fastest)
-    int64_t coarse_cap = 0;
     int bmin[3] = {0, 0, 0}, bdim[3] = {0, 0, 0};
 
     // channels
@@ -100,7 +98,6 @@ struct sdg_grid_s {
         d.table = table;
         d.nbr = nbr;
         d.dense = dense;
-        d.coarse = coarse;
         d.keys = keys;
         d.mask = mask;
         d.n_sem = desc.n_sem;

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) k_walk(GridDev g, const float* __restrict
         const float3 invd = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
         float* s0 = w.s0 + slot * kWalkCap;
         int4* rec = w.rec + slot * kWalkCap;
-        walk_cells(g, o, d, invd, t0, t1, [&](float x0, float x1, int cell, int blk) {
+        walk_cells_pipelined<8>(g, o, d, invd, t0, t1, [&](float x0, float x1, int cell, int blk) {
             if (cnt == kWalkCap) {
                 cnt = -1;  // more cells than records: the render warp walks this ray itself
                 return false;

@@ -217,18 +217,12 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
     const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
     // index steps of the dense grid (x fastest)
     const int stx = sx, sty = sy * g.bdim[0], stz = sz * (int)((unsigned)g.bdim[0] * (unsigned)g.bdim[1]);
-    const int ccx = (g.bdim[0] + 3) >> 2, ccy = (g.bdim[1] + 3) >> 2;
-    // a cell's block index is read only where its 4 x 4 x 4-cell coarse cell holds a block (a byte grid small
-    // enough to stay in L1), so most of a walk through empty space makes no dependent load
-    auto block_of = [&](int x, int y, int z, int idx) -> int {
-        return __ldg(g.coarse + ((z >> 2) * ccy + (y >> 2)) * ccx + (x >> 2)) ? __ldg(g.dense + idx) : -1;
-    };
     float tcur = ta;
     const int maxit = g.bdim[0] + g.bdim[1] + g.bdim[2] + 3;
     int cidx = (cz * g.bdim[1] + cy) * g.bdim[0] + cx;
     // the next cell's block index is loaded before the current cell is handed to f, so the loads of successive
     // cells overlap instead of each waiting for the previous one
-    int blk = block_of(cx, cy, cz, cidx);
+    int blk = __ldg(g.dense + cidx);
     for (int it = 0; it < maxit; ++it) {
         const float tx = sx ? fmaf((float)(g.bmin[0] + cx + (sx > 0)), g.L, -o.x) * invd.x : INF;
         const float ty = sy ? fmaf((float)(g.bmin[1] + cy + (sy > 0)), g.L, -o.y) * invd.y : INF;
@@ -240,7 +234,7 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
         const bool more = te < tb && (unsigned)nx < (unsigned)g.bdim[0] && (unsigned)ny < (unsigned)g.bdim[1] &&
                           (unsigned)nz < (unsigned)g.bdim[2];
         const int nidx = cidx + (mx ? stx : 0) + (my ? sty : 0) + (mz ? stz : 0);
-        const int nblk = more ? block_of(nx, ny, nz, nidx) : -1;
+        const int nblk = more ? __ldg(g.dense + nidx) : -1;
         if (b > tcur && blk >= 0)
             if (!f(tcur, b, cidx, blk)) break;
         if (!more) break;
@@ -250,6 +244,72 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
         cidx = nidx;
         blk = nblk;
         tcur = fmaxf(te, ta);
+    }
+}
+
+// The same walk for a thread that walks a whole ray alone (the traversal pass): D cells' block-index loads are
+// kept in flight, so the walk advances about one cell per D load latencies instead of one per latency.  The
+// cells, their stretches and the order in which f sees them are exactly those of walk_cells.
+template <int D, class F>
+__device__ __forceinline__ void walk_cells_pipelined(const GridDev& g, const float3& o, const float3& d,
+                                                     const float3& invd, float ta, float tb, F&& f) {
+    if (!(tb > ta)) return;
+    const float INF = __int_as_float(0x7f800000);
+    int cx = (int)floorf(fmaf(ta, d.x, o.x) * g.inv_L) - g.bmin[0];
+    int cy = (int)floorf(fmaf(ta, d.y, o.y) * g.inv_L) - g.bmin[1];
+    int cz = (int)floorf(fmaf(ta, d.z, o.z) * g.inv_L) - g.bmin[2];
+    cx = min(max(cx, 0), g.bdim[0] - 1);
+    cy = min(max(cy, 0), g.bdim[1] - 1);
+    cz = min(max(cz, 0), g.bdim[2] - 1);
+    const int sx = d.x > 0.f ? 1 : (d.x < 0.f ? -1 : 0);
+    const int sy = d.y > 0.f ? 1 : (d.y < 0.f ? -1 : 0);
+    const int sz = d.z > 0.f ? 1 : (d.z < 0.f ? -1 : 0);
+    const int stx = sx, sty = sy * g.bdim[0], stz = sz * (int)((unsigned)g.bdim[0] * (unsigned)g.bdim[1]);
+    float tcur = ta;
+    int cidx = (cz * g.bdim[1] + cy) * g.bdim[0] + cx;
+    int left = g.bdim[0] + g.bdim[1] + g.bdim[2] + 3;  // bounds the walk, as walk_cells' iteration limit
+    bool alive = true;
+    // ring of D cells between their load and their use: stretch [a, b), dense-grid cell (-1: empty slot), block
+    float ra[D], rb[D];
+    int rc[D], rblk[D];
+    auto produce = [&](int k) {
+        ra[k] = 0.f;
+        rb[k] = 0.f;
+        rc[k] = -1;
+        rblk[k] = -1;
+        if (!alive) return;
+        const float tx = sx ? fmaf((float)(g.bmin[0] + cx + (sx > 0)), g.L, -o.x) * invd.x : INF;
+        const float ty = sy ? fmaf((float)(g.bmin[1] + cy + (sy > 0)), g.L, -o.y) * invd.y : INF;
+        const float tz = sz ? fmaf((float)(g.bmin[2] + cz + (sz > 0)), g.L, -o.z) * invd.z : INF;
+        const float te = fminf(tx, fminf(ty, tz));
+        ra[k] = tcur;
+        rb[k] = fminf(te, tb);
+        rc[k] = cidx;
+        rblk[k] = __ldg(g.dense + cidx);  // used D cells later
+        const bool mx = tx == te, my = ty == te, mz = tz == te;
+        const int nx = cx + (mx ? sx : 0), ny = cy + (my ? sy : 0), nz = cz + (mz ? sz : 0);
+        alive = te < tb && (unsigned)nx < (unsigned)g.bdim[0] && (unsigned)ny < (unsigned)g.bdim[1] &&
+                (unsigned)nz < (unsigned)g.bdim[2] && --left > 0;
+        if (alive) {
+            cidx += (mx ? stx : 0) + (my ? sty : 0) + (mz ? stz : 0);
+            cx = nx;
+            cy = ny;
+            cz = nz;
+            tcur = fmaxf(te, ta);
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < D; ++k) produce(k);
+    bool pending = true;
+    while (pending) {
+        pending = false;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (rc[k] >= 0 && rb[k] > ra[k] && rblk[k] >= 0)
+                if (!f(ra[k], rb[k], rc[k], rblk[k])) return;
+            produce(k);
+            pending |= rc[k] >= 0;
+        }
     }
 }
 
