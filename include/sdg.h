@@ -189,6 +189,22 @@ int sdg_grid_set_step(sdg_grid g, int32_t step);
  * recording.  Errors: SDG_ERR_ARG (one of the two NULL). */
 int sdg_grid_set_pass_events(sdg_grid g, void* start_event, void* stop_event);
 
+/* Bounds-checked build (the paper has no counterpart; a debugging aid).  A
+ * library compiled with -DSDG_CHECKED checks in its render, traversal and
+ * query kernels every block index, trilinear-corner voxel address,
+ * dense-grid cell and ray row they derive before using it; the first index
+ * out of range is recorded in a status word per device (code << 48 | the
+ * index's low 48 bits; codes SDG_CHECK_*) -- never a trap -- and the access is
+ * skipped (the stencil counts as invalid, the cell as unallocated, the ray as
+ * ray 0).  This call synchronises the device, reads that word into *status
+ * (0: no violation) and clears it if `clear`; *checked tells whether the
+ * loaded library is the checked build (in the normal build *status is 0). */
+#define SDG_CHECK_BLOCK 1
+#define SDG_CHECK_VOXEL 2
+#define SDG_CHECK_DENSE 3
+#define SDG_CHECK_RAY 4
+int sdg_checked_status(int32_t device, int32_t clear, uint64_t* status, int32_t* checked);
+
 /* Blocks the host until all work on the grid's stream has finished. */
 int sdg_grid_sync(sdg_grid g);
 

@@ -5,7 +5,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsdg.so")
+# SDG_LIBRARY selects another build of the library in this directory (libsdg_checked.so: the bounds-checked build)
+LIB_PATH = os.path.join(HERE, os.environ.get("SDG_LIBRARY", "libsdg.so"))
 
 OK, ERR_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_IO, ERR_NOT_FOUND = range(9)
 F32, BF16 = 0, 1
@@ -100,6 +101,7 @@ SIGNATURES = {
     "sdg_grid_set_step": [_p, _i32],
     "sdg_grid_sync": [_p],
     "sdg_grid_set_pass_events": [_p, _p, _p],
+    "sdg_checked_status": [_i32, _i32, _P(C.c_uint64), _P(_i32)],
     "sdg_render_forward": [_p, _p, _i64, _P(RenderOpts), _P(RenderOut), _P(_p)],
     "sdg_render_backward": [_p, _p, _p, _p, _p],
     "sdg_ctx_release": [_p],
@@ -169,3 +171,10 @@ def check(code: int, where: str):
 def call(name: str, *args) -> int:
     """Calls an ABI function and raises SdgError on a non-OK status."""
     return check(getattr(lib(), name)(*args), name)
+
+
+def checked_status(device: int = 0, clear: bool = False):
+    """(status word, whether the loaded library is the bounds-checked build); see sdg_checked_status."""
+    st, ck = C.c_uint64(), C.c_int32()
+    call("sdg_checked_status", device, 1 if clear else 0, C.byref(st), C.byref(ck))
+    return st.value, bool(ck.value)

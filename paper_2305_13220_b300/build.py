@@ -61,6 +61,23 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int = 0, out: 
     return lib
 
 
+CHECKED_LIB = os.path.join(HERE, "libsdg_checked.so")
+
+
+def build_checked(force: bool = False) -> str:
+    """The bounds-checked build (-DSDG_CHECKED) as libsdg_checked.so, selected at run time with
+    SDG_LIBRARY=libsdg_checked.so.  Rebuilt when a source is newer than it."""
+    if not force and os.path.exists(CHECKED_LIB):
+        t = os.path.getmtime(CHECKED_LIB)
+        deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
+            glob.glob(os.path.join(INCLUDE, "*.h"))
+        if not any(os.path.getmtime(p) > t for p in deps):
+            return CHECKED_LIB
+    return build(force=True, out=CHECKED_LIB, extra_flags=["-DSDG_CHECKED"])
+
+
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose_ptxas="--verbose-ptxas" in sys.argv)
     print(LIB)
+    if "--checked" in sys.argv:
+        print(build_checked(force="--force" in sys.argv))

@@ -153,7 +153,31 @@ struct GridDev {
     // semantics (either layout)
     const __nv_bfloat16* sem;  // [N*512][n_sem]
     float* gsem;               // [N*512][n_sem]
+    // bounds-checked build only: cells of the dense block-index grid, and the device status word that records the
+    // first index found out of range
+    int64_t dense_cells;
+    unsigned long long* status;
 };
+
+// ---------------------------------------------------------------------------
+// Bounds-checked build (compile with -DSDG_CHECKED).  Every block index, voxel address, dense-grid cell and ray
+// index a kernel derives is checked before it is used; the first one out of range is recorded in a device
+// status word -- code << 48 | the index's low 48 bits -- with no trap, and the access it guards is skipped (the
+// stencil counts as invalid, the cell as unallocated, the ray as absent).  In the normal build every check is the
+// constant true and compiles to nothing.
+// ---------------------------------------------------------------------------
+// (codes SDG_CHECK_BLOCK, _VOXEL, _DENSE, _RAY: include/sdg.h)
+#ifdef SDG_CHECKED
+__device__ __forceinline__ bool sdg_in_range(unsigned long long* status, long long i, long long n, unsigned code) {
+    if (i >= 0 && i < n) return true;
+    if (status) atomicCAS(status, 0ull, ((unsigned long long)code << 48) | ((unsigned long long)i & 0xFFFFFFFFFFFFull));
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool sdg_in_range(unsigned long long*, long long, long long, unsigned) {
+    return true;
+}
+#endif
 
 // Status word bits written by kernels (never a trap).
 #define SDG_STATUS_TABLE_FULL 1u

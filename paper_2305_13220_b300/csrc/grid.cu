@@ -923,3 +923,65 @@ extern "C" int sdg_grid_load(const char* path, const sdg_grid_desc* over, sdg_gr
     *out = g;
     return SDG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Bounds-checked build: one status word per device
+// ---------------------------------------------------------------------------
+#ifdef SDG_CHECKED
+namespace {
+std::mutex g_checked_mu;
+unsigned long long* g_checked_word[64] = {};
+}  // namespace
+#endif
+
+namespace sdg {
+unsigned long long* checked_status_word(int device) {
+#ifdef SDG_CHECKED
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_checked_mu);
+    if (!g_checked_word[device]) {
+        unsigned long long* p = nullptr;
+        if (cudaMalloc((void**)&p, sizeof(unsigned long long)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaFree(p);
+            return nullptr;
+        }
+        g_checked_word[device] = p;
+    }
+    return g_checked_word[device];
+#else
+    (void)device;
+    return nullptr;
+#endif
+}
+}  // namespace sdg
+
+extern "C" int sdg_checked_status(int32_t device, int32_t clear, uint64_t* status, int32_t* checked) {
+    if (!status || !checked) return fail(SDG_ERR_ARG, "sdg_checked_status: null argument");
+    *status = 0;
+#ifdef SDG_CHECKED
+    *checked = 1;
+    int prev = 0;
+    SDG_CUDA_TRY(cudaGetDevice(&prev));
+    SDG_CUDA_TRY(cudaSetDevice(device));
+    unsigned long long* w = sdg::checked_status_word(device);
+    int rc = SDG_OK;
+    if (!w) {
+        rc = fail(SDG_ERR_OOM, "sdg_checked_status: no status word");
+    } else {
+        unsigned long long v = 0;
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && clear) e = cudaMemset(w, 0, sizeof(v));
+        if (e != cudaSuccess) rc = cuda_fail(e, "sdg_checked_status");
+        *status = v;
+    }
+    cudaSetDevice(prev);
+    return rc;
+#else
+    (void)device;
+    (void)clear;
+    *checked = 0;
+    return SDG_OK;
+#endif
+}

@@ -30,6 +30,12 @@ struct LatticeScratch {
             cap_fp2 = 0;
 };
 
+namespace sdg {
+// Device status word of the bounds-checked build (SDG_CHECKED) on `device`, allocated on first use; NULL in the
+// normal build.
+unsigned long long* checked_status_word(int device);
+}  // namespace sdg
+
 struct sdg_grid_s {
     sdg_grid_desc desc;
     cudaStream_t stream = nullptr;
@@ -120,6 +126,8 @@ struct sdg_grid_s {
         d.grgb = grgb;
         d.sem = sem;
         d.gsem = gsem;
+        d.dense_cells = dense_cells;
+        d.status = sdg::checked_status_word(device);
         return d;
     }
 };

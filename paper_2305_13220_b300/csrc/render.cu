@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256) k_walk(GridDev g, const float* __restrict
                                               int64_t n, WalkBufs w) {
     const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= n) return;
-    const int64_t r = perm ? (int64_t)__ldg(perm + slot) : slot;
+    int64_t r = perm ? (int64_t)__ldg(perm + slot) : slot;
+    if (!sdg_in_range(g.status, r, n, SDG_CHECK_RAY)) r = 0;  // checked build: a bad order row reads ray 0
     const float4 r0 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r);
     const float4 r1 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r + 1);
     const float3 o = make_float3(r0.x, r0.y, r0.z), d = make_float3(r1.x, r1.y, r1.z);

@@ -5,16 +5,22 @@
 //
 // Work decomposition (one warp = one ray), chosen so that control flow stays
 // uniform across the warp:
-//  * traversal: the ray's clipped range [t0, t1] is cut into 32 equal pieces;
-//    lane j walks the block cells of piece j once (a block-level
-//    Amanatides-Woo walk reading the dense block-index grid) and records each
-//    allocated cell it crosses -- t range, block index, block key -- in
-//    shared memory (up to kSegs per piece; a piece with more is re-walked
-//    exactly when one of its samples is placed).  A sequential shuffle prefix
-//    of the pieces' allocated lengths gives the skip-space offsets P_j.
-//  * sampling: lane l owns samples l*Q .. l*Q+Q-1.  It draws s_k itself,
-//    finds its piece by binary search over P and its cell in that piece's
-//    list, so every lane runs the same instructions.
+//  * traversal: a pass of its own (k_walk, one thread per ray) walks the ray
+//    through the dense block-index grid (block-level Amanatides-Woo) and
+//    writes the allocated cells it crosses -- t range, block index, grid cell
+//    -- with their exact sequential skip-space offsets; lane m of the render
+//    warp loads record m.  A ray crossing more than kWalkCap allocated cells,
+//    and every ray of the passes that run without the traversal pass (the
+//    serving loop, the allocation-free pass), is walked in-warp instead: the
+//    clipped range is cut into 32 equal pieces, lane j walks piece j and
+//    records its cells in shared memory (up to kSegs; a piece with more is
+//    re-walked when one of its samples is placed), and a sequential shuffle
+//    prefix of the pieces' allocated lengths gives the offsets P_j.
+//  * sampling: lane l owns samples l*Q .. l*Q+Q-1.  It draws s_k itself and
+//    finds its cell in the ray's walk records (lane m holds record m) by a
+//    binary search over their skip-space offsets for its first sample and a
+//    forward scan for the others (or, walking in-warp, by a binary search over
+//    P and the piece's list), so every lane runs the same instructions.
 //  * fetch: a lane first places all its samples, then evaluates them in
 //    order; a sample in a new cell loads its 8 corner voxels (one 16-byte
 //    load each in the FP32 layout), a sample in the cell of the lane's
@@ -194,7 +200,7 @@ __device__ __forceinline__ int dense_cell(const GridDev& g, int bx, int by, int 
 // Index of the block at block coordinates (bx, by, bz), -1 if it is not allocated (or outside the AABB).
 __device__ __forceinline__ int block_at(const GridDev& g, int bx, int by, int bz) {
     const int c = dense_cell(g, bx, by, bz);
-    return c < 0 ? -1 : __ldg(g.dense + c);
+    return c < 0 || !sdg_in_range(g.status, c, g.dense_cells, SDG_CHECK_DENSE) ? -1 : __ldg(g.dense + c);
 }
 
 // Calls f(a, b, cell, blk) for every allocated block cell the ray crosses inside [ta, tb), in order of
@@ -222,7 +228,7 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
     int cidx = (cz * g.bdim[1] + cy) * g.bdim[0] + cx;
     // the next cell's block index is loaded before the current cell is handed to f, so the loads of successive
     // cells overlap instead of each waiting for the previous one
-    int blk = __ldg(g.dense + cidx);
+    int blk = sdg_in_range(g.status, cidx, g.dense_cells, SDG_CHECK_DENSE) ? __ldg(g.dense + cidx) : -1;
     for (int it = 0; it < maxit; ++it) {
         const float tx = sx ? fmaf((float)(g.bmin[0] + cx + (sx > 0)), g.L, -o.x) * invd.x : INF;
         const float ty = sy ? fmaf((float)(g.bmin[1] + cy + (sy > 0)), g.L, -o.y) * invd.y : INF;
@@ -234,7 +240,8 @@ __device__ __forceinline__ void walk_cells(const GridDev& g, const float3& o, co
         const bool more = te < tb && (unsigned)nx < (unsigned)g.bdim[0] && (unsigned)ny < (unsigned)g.bdim[1] &&
                           (unsigned)nz < (unsigned)g.bdim[2];
         const int nidx = cidx + (mx ? stx : 0) + (my ? sty : 0) + (mz ? stz : 0);
-        const int nblk = more ? __ldg(g.dense + nidx) : -1;
+        const int nblk =
+            more && sdg_in_range(g.status, nidx, g.dense_cells, SDG_CHECK_DENSE) ? __ldg(g.dense + nidx) : -1;
         if (b > tcur && blk >= 0)
             if (!f(tcur, b, cidx, blk)) break;
         if (!more) break;
@@ -285,7 +292,8 @@ __device__ __forceinline__ void walk_cells_pipelined(const GridDev& g, const flo
         ra[k] = tcur;
         rb[k] = fminf(te, tb);
         rc[k] = cidx;
-        rblk[k] = __ldg(g.dense + cidx);  // used D cells later
+        rblk[k] = sdg_in_range(g.status, cidx, g.dense_cells, SDG_CHECK_DENSE) ? __ldg(g.dense + cidx)
+                                                                                 : -1;  // used D cells later
         const bool mx = tx == te, my = ty == te, mz = tz == te;
         const int nx = cx + (mx ? sx : 0), ny = cy + (my ? sy : 0), nz = cz + (mz ? sz : 0);
         alive = te < tb && (unsigned)nx < (unsigned)g.bdim[0] && (unsigned)ny < (unsigned)g.bdim[1] &&
@@ -408,24 +416,6 @@ __device__ __forceinline__ float locate(const GridDev& g, const RayJob& j, const
 // ---------------------------------------------------------------------------
 // Traversal as its own pass: one thread walks a whole ray
 // ---------------------------------------------------------------------------
-// Record m of the lane-distributed walk records (lane m holds record m): the largest m with s0[m] <= s, found by
-// a binary search over the lanes' offsets.  Every lane of the warp must call it (it shuffles).
-__device__ __forceinline__ float locate_rec(int n_rec, float my_s0, const int4& my_rec, float s, int& blk,
-                                            int& cell) {
-    int m = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const float v = __shfl_sync(kFull, my_s0, m + step);
-        if (m + step < n_rec && v <= s) m += step;
-    }
-    const float s0 = __shfl_sync(kFull, my_s0, m);
-    const float tin = __int_as_float(__shfl_sync(kFull, my_rec.x, m));
-    const float len = __int_as_float(__shfl_sync(kFull, my_rec.y, m));
-    blk = __shfl_sync(kFull, my_rec.z, m);
-    cell = __shfl_sync(kFull, my_rec.w, m);
-    return tin + fminf(s - s0, len);
-}
-
 // ---------------------------------------------------------------------------
 // Voxel stencil of a cell (Eq. 17): the 8 grid points around x
 // ---------------------------------------------------------------------------
@@ -436,6 +426,7 @@ __device__ __forceinline__ float locate_rec(int n_rec, float my_s0, const int4& 
 __device__ __forceinline__ bool corner_addresses(const GridDev& g, int blk, int lcell, int addr[8]) {
     const int lx = lcell & 7, ly = (lcell >> 3) & 7, lz = lcell >> 6;
     const bool ox = lx == 7, oy = ly == 7, oz = lz == 7;
+    if (!sdg_in_range(g.status, blk, g.n_blocks, SDG_CHECK_BLOCK)) return false;
     const int4 n0 = __ldg(g.nbr + 2 * blk), n1 = __ldg(g.nbr + 2 * blk + 1);
     const int b1 = ox ? n0.y : blk;
     const int b2 = oy ? n0.z : blk;
@@ -456,7 +447,13 @@ __device__ __forceinline__ bool corner_addresses(const GridDev& g, int blk, int 
     addr[5] = b5 * 512 + q10 + z1;
     addr[6] = b6 * 512 + q01 + z1;
     addr[7] = b7 * 512 + q11 + z1;
-    return (b1 | b2 | b3 | b4 | b5 | b6 | b7) >= 0;
+    const bool all = (b1 | b2 | b3 | b4 | b5 | b6 | b7) >= 0;
+#ifdef SDG_CHECKED
+    if (all)  // every address the fetch and the scatter will use
+        for (int e = 0; e < 8; ++e)
+            if (!sdg_in_range(g.status, addr[e], g.n_blocks * 512, SDG_CHECK_VOXEL)) return false;
+#endif
+    return all;
 }
 
 template <bool BF16>
@@ -636,6 +633,8 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     };
 
     unsigned smask = 0;  // stored mode: samples whose record is valid
+    int rm = 0, r_blk = -1, r_cell = -1;  // the lane's current walk record and its fields
+    float r_s0 = 0.f, r_tin = 0.f, r_len = 0.f;
     // place sample i: its s, t, cell and block; false if the lane has no sample i
     auto place = [&](int i) -> bool {
         const int k = lane * Q + i;
@@ -658,8 +657,39 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         int blk = -1, cell = -1;
         float t_rec = 0.f;
         if constexpr (!kStoreIn && !INWARP) {
-            // every lane takes part in the record search (it shuffles), with or without a sample i
-            t_rec = locate_rec(n_rec, my_s0, my_rec, k < N ? s_[i] : 0.f, blk, cell);
+            // every lane takes part in the record search (it shuffles), with or without a sample i: a binary
+            // search for the lane's first sample, then (its samples are consecutive) a forward scan one record at
+            // a time, the record's fields fetched again only when some lane moved
+            const float sq = k < N ? s_[i] : 0.f;
+            bool moved = i == 0;
+            if (i == 0) {
+                rm = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const float v = __shfl_sync(kFull, my_s0, rm + step);
+                    if (rm + step < n_rec && v <= sq) rm += step;
+                }
+            } else {
+                for (int it = 0; it < kWalkCap; ++it) {
+                    const float v = __shfl_sync(kFull, my_s0, rm + 1 < kWalkCap ? rm + 1 : kWalkCap - 1);
+                    const bool adv = rm + 1 < n_rec && v <= sq;
+                    if (!__any_sync(kFull, adv)) break;
+                    if (adv) {
+                        ++rm;
+                        moved = true;
+                    }
+                }
+            }
+            if (__any_sync(kFull, moved)) {
+                r_s0 = __shfl_sync(kFull, my_s0, rm);
+                r_tin = __int_as_float(__shfl_sync(kFull, my_rec.x, rm));
+                r_len = __int_as_float(__shfl_sync(kFull, my_rec.y, rm));
+                r_blk = __shfl_sync(kFull, my_rec.z, rm);
+                r_cell = __shfl_sync(kFull, my_rec.w, rm);
+            }
+            blk = r_blk;
+            cell = r_cell;
+            t_rec = r_tin + fminf(sq - r_s0, r_len);
         }
         if (k >= N) return false;
         float sn;
@@ -690,7 +720,9 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         if constexpr (!kStoreIn) {
             // the sample's own block: the traversal cell's, unless rounding put it across a block face
             const int own = dense_cell(g, cx >> 3, cy >> 3, cz >> 3);
-            if (own != cell) blk = own < 0 ? -1 : __ldg(g.dense + own);
+            if (own != cell)
+                blk = own < 0 || !sdg_in_range(g.status, own, g.dense_cells, SDG_CHECK_DENSE) ? -1
+                                                                                          : __ldg(g.dense + own);
         }
         blk_[i] = blk;
         if constexpr (kTrace) {

@@ -19,9 +19,10 @@ constexpr int render_min_blocks() {
 }
 
 // Ray of processing slot `slot` (ray perm[slot], or ray slot) into j.
-__device__ __forceinline__ void load_job(const float* rays, const int* perm, uint32_t ray_id0, int64_t slot,
-                                         RayJob& j) {
-    const int64_t r = perm ? (int64_t)__ldg(perm + slot) : slot;
+__device__ __forceinline__ void load_job(const GridDev& g, const float* rays, const int* perm, uint32_t ray_id0,
+                                         int64_t slot, int64_t n, RayJob& j) {
+    int64_t r = perm ? (int64_t)__ldg(perm + slot) : slot;
+    if (!sdg_in_range(g.status, r, n, SDG_CHECK_RAY)) r = 0;  // checked build: a bad order row reads ray 0
     const float4 r0 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r);
     const float4 r1 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r + 1);
     j.o = make_float3(r0.x, r0.y, r0.z);
@@ -47,13 +48,13 @@ __global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>()))
     RayJob j;
     if constexpr (!INWARP) {
         if (w >= a.n) return;  // warp-uniform
-        load_job(rays, a.perm, ray_id0, w, j);
+        load_job(g, rays, a.perm, ray_id0, w, a.n, j);
         ray_program<MODE, BF16, SEM, Q, false>(g, a, j, smem[0], lane);
     } else {
         const bool list = a.walk.hdr != nullptr;
         const int64_t end = list ? (int64_t)__ldg(a.walk.n_over) : a.n;
         if (w >= end) return;  // warp-uniform
-        load_job(rays, a.perm, ray_id0, list ? (int64_t)__ldg(a.walk.over + w) : w, j);
+        load_job(g, rays, a.perm, ray_id0, list ? (int64_t)__ldg(a.walk.over + w) : w, a.n, j);
         ray_program<MODE, BF16, SEM, Q, true>(g, a, j, smem[warp], lane);
     }
 }

@@ -25,3 +25,17 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _bounds_checked_build(request):
+    """Under SDG_EXPECT_CHECKED=1 (the bounds-checked run of the GPU suite, tests/test_gpu_checked.py) every GPU
+    test must run on libsdg_checked.so and leave its out-of-range status word at 0."""
+    yield
+    if os.environ.get("SDG_EXPECT_CHECKED") != "1" or "gpu" not in request.keywords:
+        return
+    import paper_2305_13220_b300 as sdg
+    status, checked = sdg._abi.checked_status(0, clear=True)
+    assert checked, "SDG_EXPECT_CHECKED=1 but the loaded library is not the bounds-checked build"
+    assert status == 0, f"bounds-checked build recorded an index out of range: code {status >> 48}, " \
+                        f"index {status & 0xFFFFFFFFFFFF}"

@@ -61,8 +61,8 @@ def test_beta_gradient_matches_oracle_and_voxel_gradients_are_unchanged(sdg):
     got = G.beta_grad()
     assert got == pytest.approx(want["beta"], rel=1e-3)
     with_beta = grad_arrays(G, G.num_blocks)
-    assert_grad_close(with_beta["sdf"], plain["sdf"], rel=1e-5, floor=1e-6, what="sdf (beta variant)")
-    assert_grad_close(with_beta["rgb"], plain["rgb"], rel=1e-5, floor=1e-6, what="rgb (beta variant)")
+    assert_grad_close(with_beta["sdf"], plain["sdf"], rel=1e-5, floor=1e-5, what="sdf (beta variant)")
+    assert_grad_close(with_beta["rgb"], plain["rgb"], rel=1e-5, floor=1e-5, what="rgb (beta variant)")
     # a second pass accumulates
     sdg.train_step_rays(G, rays.cuda(), _dev(t_rgb), _dev(t_depth), n_samples=64, stratified=False,
                         learn_beta=True)

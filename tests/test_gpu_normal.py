@@ -57,7 +57,7 @@ def test_normal_loss_matches_oracle(sdg, rgb_dtype):
     G.zero_grad()
     sdg.train_step_rays(G, rays.cuda(), _dev(t_rgb), _dev(t_depth), n_samples=64, stratified=False)
     plain = grad_arrays(G, G.num_blocks)
-    assert_grad_close(zero["sdf"], plain["sdf"], rel=1e-5, floor=1e-6, what="sdf (lambda_n = 0)")
+    assert_grad_close(zero["sdf"], plain["sdf"], rel=1e-5, floor=1e-5, what="sdf (lambda_n = 0)")
 
 
 def test_normal_pass_rejects_what_it_does_not_support(sdg):
