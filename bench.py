@@ -40,6 +40,9 @@ def parse():
     p.add_argument("--rays", type=int, default=1 << 18)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--parallel", default="replicas", choices=["replicas", "dp"],
+                   help="N > 1: independent replicas (each rank its own batch), or one batch sharded by rays over "
+                        "the ranks with an all-reduce of the gradients before the replicated optimiser step")
     p.add_argument("--no-extra", action="store_true",
                    help="room line without the precision / serving / apartment sub-measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
@@ -331,14 +334,21 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_2305_13220_b300 as sdg
     device = f"cuda:{local}"
-    wl = build_workload(sdg, torch, device, args.views, args.rays, seed=rank, max_blocks=args.max_blocks,
-                        order=args.order)
+    dp_mode = args.parallel == "dp" and world > 1
+    # data parallel: every rank holds the same grid and batch and renders its shard of it
+    wl = build_workload(sdg, torch, device, args.views, args.rays, seed=0 if dp_mode else rank,
+                        max_blocks=args.max_blocks, order=args.order)
     G = wl["grid"]
     n = args.rays
     stream = torch.cuda.current_stream()
     loss_sum = torch.zeros(1, device=device)
 
     def step(b):
+        if dp_mode:
+            from paper_2305_13220_b300 import dp
+            dp.data_parallel_step(G, b["rays"], b["rgb"], b["depth"], rank, world, n_samples=N_SAMPLES,
+                                  seed=stepno[0], lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
+            return
         sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
                             lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
         G.adam_step(lr=1e-3)
@@ -369,9 +379,16 @@ def run_ours(args):
         stepno[0] = 1000 + i
         G.set_pass_events(kev[i][0], kev[i][1])
         evs[i][0].record(stream)
-        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
-                            lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
-        evs[i][1].record(stream)
+        if dp_mode:  # this rank's shard, then the gradient all-reduce with the optimiser step
+            from paper_2305_13220_b300 import dp
+            dp.shard_train(G, b["rays"], b["rgb"], b["depth"], rank, world, n_samples=N_SAMPLES, seed=stepno[0],
+                           lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
+            evs[i][1].record(stream)
+            dp.all_reduce_grads(G)
+        else:
+            sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
+                                lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
+            evs[i][1].record(stream)
         G.adam_step(lr=1e-3)
         evs[i][2].record(stream)
     end.record(stream)
@@ -385,7 +402,8 @@ def run_ours(args):
     step_t = [e[0].elapsed_time(e[2]) for e in evs]
     train_ms, kern_ms, adam_ms = (float(np.median(x)) for x in (train_t, kern_t, adam_t))
     ms_step = total_ms / K
-    value = aggregate_rays_per_s(world, n, ms_step)
+    # replicas: every rank a whole batch; data parallel: one batch over all ranks
+    value = (n / (ms_step / 1e3)) if dp_mode else aggregate_rays_per_s(world, n, ms_step)
 
     # unfused forward and backward of the same batches (timed apart; not part of the headline step)
     fb = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
@@ -443,6 +461,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = reduce_max(e0.elapsed_time(e1) / K, device)
+    e2e_value = (n / (e2e_ms / 1e3)) if dp_mode else aggregate_rays_per_s(world, n, e2e_ms)
 
     res = None
     if rank == 0:
@@ -451,7 +470,8 @@ def run_ours(args):
         adam_bytes = params * 32
         line = {"metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "strong" if dp_mode else "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
                 "config": {"workload": "room-scale FP32 training step (6x6x3 m room, 10 boxes/cylinders, 1 cm "
                                        "voxels, 8^3 blocks, 4-voxel band from 50 640x480 depth maps; 2^18 rays "
                                        "x 128 stratified samples, L1 colour + 0.1 L1 depth, Adam on every voxel)",
@@ -459,7 +479,8 @@ def run_ours(args):
                            "ray_order": args.ray_order + (" (surface order, sorted on the GPU inside the step)"
                                                           if _order_launches(args, n) else ""),
                            "voxels": nb * 512, "params": params,
-                           "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "parallelism": (f"dp{world} (ray shards, gradient all-reduce)" if dp_mode else
+                                           f"replicas{world}" if world > 1 else "single"),
                            "l2": "inputs larger than L2: each step streams the whole grid and Adam state "
                                  f"({adam_bytes / 1e9:.1f} GB) through HBM"},
                 "samples_per_s": round(value * N_SAMPLES, 1),
@@ -472,7 +493,7 @@ def run_ours(args):
                                    "the traversal, the render kernels and the loss sum; the render kernels are "
                                    "timed by events the library records around them (sdg_grid_set_pass_events)"},
                 "clocks": clk, "gpu_launches": (_train_launches(args, n) + 1) * K,
-                "e2e": {"value": round(aggregate_rays_per_s(world, n, e2e_ms), 1), "unit": "rays/s",
+                "e2e": {"value": round(e2e_value, 1), "unit": "rays/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}}
         peak, peak_src = _peak()
         adam_gbs = adam_bytes / (adam_ms / 1e3) / 1e9

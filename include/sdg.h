@@ -322,6 +322,9 @@ typedef struct {
     float lambda_sem;   /* 0.1 */
     int32_t ray_order;  /* SDG_ORDER_*; used by sdg_train_step_rays only */
     int32_t learn_beta; /* sdg_train_step_rays: also accumulate dL/dbeta (see below) */
+    int64_t norm_rays;  /* the n of the means "over rays" in the training passes; 0 = the call's own ray count.
+                           A data-parallel step that splits a batch of M rays over ranks passes M, so that the
+                           ranks' gradients sum to the whole batch's */
 } sdg_loss_opts;
 
 /* Learnable Laplace scale (beta of Sec. 3.5.1 as a parameter, as VolSDF

@@ -40,7 +40,7 @@ class RenderOut(C.Structure):
 
 class LossOpts(C.Structure):
     _fields_ = [("lambda_depth", C.c_float), ("lambda_sem", C.c_float), ("ray_order", C.c_int32),
-                ("learn_beta", C.c_int32)]
+                ("learn_beta", C.c_int32), ("norm_rays", C.c_int64)]
 
 
 class AdamOpts(C.Structure):

@@ -394,7 +394,7 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
     a.t_sem = g->desc.n_sem ? tsem : nullptr;
     a.lam_d = lo->lambda_depth;
     a.lam_s = lo->lambda_sem;
-    a.inv_n = 1.0f / (float)n;
+    a.inv_n = 1.0f / (float)(lo->norm_rays > 0 ? lo->norm_rays : n);
     a.loss = per_ray;
     if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
         if ((rc = order_rays_by_surface(g, rays, tdepth, n, &a.perm))) return rc;
@@ -456,7 +456,7 @@ extern "C" int sdg_train_step_rays_normal(sdg_grid g, const float* rays, int64_t
     a.t_normal = tnormal;
     a.lam_d = lo->lambda_depth;
     a.lam_n = lambda_normal;
-    a.inv_n = 1.0f / (float)n;
+    a.inv_n = 1.0f / (float)(lo->norm_rays > 0 ? lo->norm_rays : n);
     a.loss = per_ray;
     if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
         if ((rc = order_rays_by_surface(g, rays, tdepth, n, &a.perm))) return rc;
@@ -553,7 +553,7 @@ extern "C" int sdg_train_step_rays_noalloc(sdg_grid g, const float* rays, int64_
     a.t_sem = g->desc.n_sem ? tsem : nullptr;
     a.lam_d = lo->lambda_depth;
     a.lam_s = lo->lambda_sem;
-    a.inv_n = 1.0f / (float)n;
+    a.inv_n = 1.0f / (float)(lo->norm_rays > 0 ? lo->norm_rays : n);
     a.loss = loss_sum ? scratch : nullptr;  // every ray writes its entry before the sum reads it
     rc = launch_pass<PASS_TRAIN>(g, rays, o->ray_id0, a);
     if (rc) return rc;
