@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--parallel", default="replicas", choices=["replicas", "dp"],
                    help="N > 1: independent replicas (each rank its own batch), or one batch sharded by rays over "
                         "the ranks with an all-reduce of the gradients before the replicated optimiser step")
+    p.add_argument("--no-prepare", action="store_true",
+                   help="room step without the preparation pipeline (each batch ordered and walked inside its own "
+                        "step instead of beside the previous step's optimiser)")
     p.add_argument("--no-extra", action="store_true",
                    help="room line without the precision / serving / apartment sub-measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
@@ -53,6 +56,8 @@ def parse():
                    help="room: the headline training step; the others are the precision, serving and apartment "
                         "workloads (one JSON line each)")
     p.add_argument("--requests", type=int, default=2000, help="serve: requests per arrival rate")
+    p.add_argument("--serve-scenes", default="0,1,2,3,4,5,6,7",
+                   help="serve: which of the eight serving rooms to register (comma-separated indices)")
     p.add_argument("--order", default="pixel", choices=["pixel", "drawn"],
                    help="ray order inside a batch: grouped by view and pixel (a per-image loader) or as drawn")
     p.add_argument("--ray-order", default="auto", choices=["auto", "given", "surface"],
@@ -343,20 +348,41 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     loss_sum = torch.zeros(1, device=device)
 
-    def step(b):
+    # Preparation pipeline: batch i + 1's ordering and traversal are enqueued (on the grid's auxiliary stream)
+    # after batch i's training pass and before its optimiser step, so they run beside the HBM-bound optimiser.
+    # prep[0] is the slot batch i was prepared in (None: not prepared).
+    pipelined = not args.no_prepare and not dp_mode
+    prep = [None]
+
+    def train(b, seed, ev=None):
+        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=seed,
+                            lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order, prepared=prep[0])
+        if ev is not None:
+            ev.record(stream)
+
+    def prepare_next(b_next):
+        if pipelined and b_next is not None:
+            slot = 0 if prep[0] is None else 1 - prep[0]
+            sdg.train_prepare(G, b_next["rays"], b_next["depth"], slot, ray_order=args.ray_order)
+            prep[0] = slot
+        else:
+            prep[0] = None
+
+    def step(b, b_next=None):
         if dp_mode:
             from paper_2305_13220_b300 import dp
             dp.data_parallel_step(G, b["rays"], b["rgb"], b["depth"], rank, world, n_samples=N_SAMPLES,
                                   seed=stepno[0], lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
             return
-        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
-                            lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
+        train(b, stepno[0])
+        prepare_next(b_next)
         G.adam_step(lr=1e-3)
 
+    nb_ = len(wl["batches"])
     stepno = [0]
     for i in range(args.warmup):
         stepno[0] = i
-        step(wl["batches"][i % len(wl["batches"])])
+        step(wl["batches"][i % nb_], wl["batches"][(i + 1) % nb_])
     torch.cuda.synchronize()
     # phase timing, all with CUDA events on the grid's stream: the training pass (ordering, traversal, render
     # kernels, loss sum), the render kernels alone (recorded by the library around them), the optimiser
@@ -375,7 +401,7 @@ def run_ours(args):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for i in range(K):
-        b = wl["batches"][i % len(wl["batches"])]
+        b = wl["batches"][(args.warmup + i) % nb_]
         stepno[0] = 1000 + i
         G.set_pass_events(kev[i][0], kev[i][1])
         evs[i][0].record(stream)
@@ -386,9 +412,8 @@ def run_ours(args):
             evs[i][1].record(stream)
             dp.all_reduce_grads(G)
         else:
-            sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=stepno[0],
-                                lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
-            evs[i][1].record(stream)
+            train(b, stepno[0], evs[i][1])
+            prepare_next(wl["batches"][(args.warmup + i + 1) % nb_])
         G.adam_step(lr=1e-3)
         evs[i][2].record(stream)
     end.record(stream)
@@ -404,6 +429,21 @@ def run_ours(args):
     ms_step = total_ms / K
     # replicas: every rank a whole batch; data parallel: one batch over all ranks
     value = (n / (ms_step / 1e3)) if dp_mode else aggregate_rays_per_s(world, n, ms_step)
+
+    # the same steps without the preparation pipeline, for comparison (not the headline)
+    unprepared_ms = None
+    if pipelined:
+        prep[0] = None
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        for i in range(K):
+            b = wl["batches"][i % nb_]
+            sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=2000 + i,
+                                lambda_depth=LAMBDA_D, loss_sum=loss_sum, ray_order=args.ray_order)
+            G.adam_step(lr=1e-3)
+        u1.record(stream)
+        torch.cuda.synchronize()
+        unprepared_ms = u0.elapsed_time(u1) / K
 
     # unfused forward and backward of the same batches (timed apart; not part of the headline step)
     fb = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
@@ -444,12 +484,22 @@ def run_ours(args):
         for s_ in range(2):
             consumed[s_].record(stream)
         upload(0, 0)
+        prep[0] = None
+        stream.wait_event(uploaded[0])
+        prepare_next(dev_in[0])
         for i in range(count):
             slot = i % 2
             if i + 1 < count:
                 upload(i + 1, 1 - slot)
             stream.wait_event(uploaded[slot])
-            step(dev_in[slot])
+            stepno[0] = 4000 + i
+            train(dev_in[slot], stepno[0])
+            if i + 1 < count:
+                stream.wait_event(uploaded[1 - slot])  # the next batch's inputs, for its preparation
+                prepare_next(dev_in[1 - slot])
+            else:
+                prep[0] = None
+            G.adam_step(lr=1e-3)
             consumed[slot].record(stream)
             host_loss.copy_(loss_sum, non_blocking=True)
 
@@ -487,11 +537,17 @@ def run_ours(args):
                 "phases": {"train_kernel_ms": round(train_ms, 4), "render_kernels_ms": round(kern_ms, 4),
                            "adam_ms": round(adam_ms, 4), "activation_ms_50_maps": round(wl["act_ms"], 3)},
                 "timing": {"step_ms": _stats(step_t), "train_pass_ms": _stats(train_t),
+                           "pipeline": ("each batch's ordering and traversal prepared on the grid's auxiliary "
+                                        "stream beside the previous step's optimiser (sdg_train_prepare); the "
+                                        "same steps unprepared: " + (f"{unprepared_ms:.4f} ms per step"
+                                                                    if unprepared_ms else "not run"))
+                           if pipelined else "none",
                            "render_kernels_ms": _stats(kern_t), "adam_ms": _stats(adam_t),
                            "unfused_forward_ms": _stats(fwd_t), "unfused_loss_backward_ms": _stats(bwd_t),
-                           "note": "CUDA events on the grid's stream; the train pass holds the surface ordering, "
-                                   "the traversal, the render kernels and the loss sum; the render kernels are "
-                                   "timed by events the library records around them (sdg_grid_set_pass_events)"},
+                           "note": "CUDA events on the grid's stream; the train pass holds the render kernels "
+                                   "and the loss sum (and, without the preparation pipeline, the surface ordering "
+                                   "and the traversal); the render kernels are timed by events the library "
+                                   "records around them (sdg_grid_set_pass_events)"},
                 "clocks": clk, "gpu_launches": (_train_launches(args, n) + 1) * K,
                 "e2e": {"value": round(e2e_value, 1), "unit": "rays/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}}
@@ -517,9 +573,8 @@ def run_ours(args):
                                 "launch_ms_median": round(kern_ms, 4),
                                 "note": "the fused training pass's render kernels (records kernel + in-warp "
                                         "kernel for rays beyond the record capacity), algorithmic bytes from the "
-                                        "oracle's count over their median duration; the whole training phase "
-                                        f"(ordering, traversal, loss sum included) gives "
-                                        f"{bpr * n / (train_ms / 1e3) / 1e9:.1f} GB/s"}
+                                        "oracle's count over their median duration; over the training pass as "
+                                        f"timed (train_pass_ms) {bpr * n / (train_ms / 1e3) / 1e9:.1f} GB/s"}
             line["roofline_other"] = {"kernel": "k_opt_f32", "achieved": round(adam_gbs, 1),
                                       "frac": round(adam_gbs / peak, 4), "unit": "GB/s",
                                       "algorithmic_bytes_per_launch": adam_bytes}
@@ -753,7 +808,8 @@ def measure_serve(args, compact=False):
     import synth
     device = "cuda:0"
     grids, scenes = [], []
-    for i, (size, n_obj, vs) in enumerate(SERVE_SPECS):
+    for i in [int(x) for x in args.serve_scenes.split(",")]:
+        size, n_obj, vs = SERVE_SPECS[i]
         sc = synth.scene_room(100 + i, size=size, n_objects=n_obj)
         keys = synth.band_blocks(sc, vs, 3, device=device)
         G = sdg.Grid(vs, len(keys), beta=0.5 * vs, rgb_dtype="bf16")
@@ -768,7 +824,7 @@ def measure_serve(args, compact=False):
     poses = [synth.random_poses(sc, 8, seed=50) for sc in scenes]
 
     def req(i):
-        s = int(rng.integers(0, 8))
+        s = int(rng.integers(0, len(ids)))
         w, h = res[int(rng.integers(0, 4))]
         return ids[s], h, w, synth.intrinsics(w, h), poses[s][i % 8]
 
@@ -804,12 +860,12 @@ def measure_serve(args, compact=False):
     del grids
     torch.cuda.empty_cache()
     if compact:
-        return {"workload": "8 rooms, BF16 colour, N = 128, requests uniform over 160x120..1280x960, Poisson "
-                            "arrivals at 0.5x / 0.8x / 1.0x of the saturated rate",
+        return {"workload": f"{len(ids)} rooms, BF16 colour, N = 128, requests uniform over 160x120..1280x960, "
+                            "Poisson arrivals at 0.5x / 0.8x / 1.0x of the saturated rate",
                 "scene_blocks": nblocks, "saturated_rays_per_s": round(cap, 1), "points": points}
     return _line(cap, "rays/s", len(points), 1, 1e3 * mean_rays / cap,
-                 {"workload": "serving: 8 device-resident rooms, BF16 colour, 128 samples per ray, requests of "
-                              "160x120 / 320x240 / 640x480 / 1280x960 with Poisson arrivals",
+                 {"workload": f"serving: {len(ids)} device-resident rooms, BF16 colour, 128 samples per ray, "
+                              "requests of 160x120 / 320x240 / 640x480 / 1280x960 with Poisson arrivals",
                   "scene_blocks": nblocks},
                  dtype="f32+bf16", saturated_rays_per_s=round(cap, 1), serve_points=points,
                  peak_server_bytes=int(st.peak_bytes_in_use), gpu_launches=int(st.launches))
@@ -924,8 +980,8 @@ def run_reference(args):
     # the GPU arm's first batch (build_workload: seed 0, batch 0, per-image order), then a seeded sample of it
     batch = synth.training_batch(sc, poses, W, H, K, args.rays, seed=0, order=args.order)
     perm = np.random.default_rng(0).permutation(args.rays)
-    cores = max(1, min(os.cpu_count() or 1, 64))
-    per_core = 48  # rays per core and step: about 0.05 s of oracle work each
+    cores = max(1, min(len(os.sched_getaffinity(0)), 64))
+    per_core = 128  # rays per core and step: about 0.15 s of oracle work each
     rays_per_step = per_core * cores
     total = (args.warmup + args.steps) * rays_per_step + 256
     sel = perm[:min(total, args.rays)]

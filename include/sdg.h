@@ -325,7 +325,20 @@ typedef struct {
     int64_t norm_rays;  /* the n of the means "over rays" in the training passes; 0 = the call's own ray count.
                            A data-parallel step that splits a batch of M rays over ranks passes M, so that the
                            ranks' gradients sum to the whole batch's */
+    int32_t prepared;   /* sdg_train_step_rays: 0, or 1 + the slot sdg_train_prepare prepared these rays in */
+    int32_t reserved;   /* must be 0 */
 } sdg_loss_opts;
+
+/* Prepares a training batch ahead (the paper has no counterpart; a scheduling aid): enqueues the ray
+ * ordering (lo->ray_order, as sdg_train_step_rays would apply it) and the traversal pass of these n rays on the
+ * grid's auxiliary stream, into preparation slot `slot` (0 or 1), after everything already enqueued on the
+ * grid's stream.  The next sdg_train_step_rays of the same rays_dev and n with lo->prepared = slot + 1 uses them
+ * and waits for them on the grid's stream.  Issued after one step's training pass and before its optimiser step,
+ * the next batch's traversal (issue-bound) runs beside the optimiser (HBM-bound).  The rays and t_depth must not
+ * change before that call; preparing a slot again replaces its batch.  Per-ray results are those of an
+ * unprepared call.  Errors: SDG_ERR_ARG (bad slot or size, null argument), SDG_ERR_OOM, SDG_ERR_CUDA. */
+int sdg_train_prepare(sdg_grid g, const float* rays_dev, int64_t n, const float* t_depth_dev,
+                      const sdg_loss_opts* lo, int32_t slot);
 
 /* Learnable Laplace scale (beta of Sec. 3.5.1 as a parameter, as VolSDF
  * learns it).  With lo->learn_beta set, sdg_train_step_rays also accumulates

@@ -10,9 +10,9 @@ _abi.lib()  # fail loudly at import when the CUDA library is missing
 
 from .grid import Grid, render_opts  # noqa: E402
 from .render import (DifferentiableRenderer, RenderContext, backward, loss_depth_ssi, loss_l1,  # noqa: E402
-                     render, trace, trace_view, train_step_rays, train_step_rays_normal)
+                     render, trace, trace_view, train_prepare, train_step_rays, train_step_rays_normal)
 from .serve import Server  # noqa: E402
 
-__all__ = ["Grid", "render_opts", "render", "trace", "trace_view", "backward", "loss_l1", "loss_depth_ssi", "train_step_rays",
+__all__ = ["Grid", "render_opts", "render", "trace", "trace_view", "train_prepare", "backward", "loss_l1", "loss_depth_ssi", "train_step_rays",
            "train_step_rays_normal",
            "DifferentiableRenderer", "RenderContext", "SdgError", "Server"]

@@ -40,7 +40,8 @@ class RenderOut(C.Structure):
 
 class LossOpts(C.Structure):
     _fields_ = [("lambda_depth", C.c_float), ("lambda_sem", C.c_float), ("ray_order", C.c_int32),
-                ("learn_beta", C.c_int32), ("norm_rays", C.c_int64)]
+                ("learn_beta", C.c_int32), ("norm_rays", C.c_int64), ("prepared", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class AdamOpts(C.Structure):
@@ -119,6 +120,7 @@ SIGNATURES = {
     "sdg_fuse_frames": [_p, _i64, C.c_int32, C.c_int32, _p, _p, _p, _p, _p, C.c_float],
     "sdg_fuse_finalize": [_p],
     "sdg_train_step_rays": [_p, _p, _i64, _p, _p, _p, _P(RenderOpts), _P(LossOpts), _p, _p],
+    "sdg_train_prepare": [_p, _p, _i64, _p, _P(LossOpts), _i32],
     "sdg_adam_step": [_p, _P(AdamOpts)],
     "sdg_server_create": [_P(ServerOpts), _P(_p)],
     "sdg_server_add_scene": [_p, _p, _P(_i32)],

@@ -338,13 +338,19 @@ void free_grid_buffers(sdg_grid g) {
     void* ptrs[] = {g->table, g->tmp_table, g->keys, g->nbr, g->dense, g->geo, g->ggeo, g->m_geo, g->v_geo,
                     g->sdf, g->gsdf, g->m_sdf, g->v_sdf, g->rgbh, g->grgb, g->m_rgb, g->v_rgb, g->sem, g->gsem,
                     g->m_sem, g->v_sem, g->weight, g->sort_buf, g->counters, g->minmax, g->loss_buf,
-                    g->walk_hdr, g->walk_s0, g->walk_rec, g->walk_over,
-                    g->order_keys, g->order_perm, g->order_hist, g->fuse_cams, g->beta_grad, g->beta_part,
+                    g->fuse_cams, g->beta_grad, g->beta_part,
                     g->ssi_dev, g->lat.fp, g->lat.idx, g->lat.skey, g->lat.keys, g->lat.vidx, g->lat.vbary,
                     g->lat.val0, g->lat.val1, g->lat.nb, g->lat.counters, g->lat.fq, g->lat.sr, g->lat.srank,
                     g->lat.vslot, g->lat.fp2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    free_batch(g->batch);
+    for (PreparedBatch& pb : g->prep) {
+        free_batch(pb.b);
+        if (pb.fence) cudaEventDestroy(pb.fence);
+        if (pb.ready) cudaEventDestroy(pb.ready);
+    }
+    if (g->aux) cudaStreamDestroy(g->aux);
     if (g->h_counters) cudaFreeHost(g->h_counters);
     if (g->h_minmax) cudaFreeHost(g->h_minmax);
 }
@@ -583,6 +589,7 @@ extern "C" int sdg_grid_destroy(sdg_grid g) {
     }
     cudaSetDevice(g->device);
     cudaStreamSynchronize(g->stream);
+    if (g->aux) cudaStreamSynchronize(g->aux);
     free_grid_buffers(g);
     delete g;
     return SDG_OK;

@@ -30,6 +30,31 @@ struct LatticeScratch {
             cap_fp2 = 0;
 };
 
+// Per-batch scratch of a pass: the surface ordering of its rays and the records of its traversal pass.
+struct BatchBufs {
+    int* order_keys = nullptr;  // per-ray bucket [order_cap]
+    int* order_perm = nullptr;  // processing order [order_cap]
+    int* order_hist = nullptr;  // bucket counts, then offsets [kOrderBuckets]
+    int64_t order_cap = 0;
+    // traversal records for up to walk_cap rays: header, skip-space offsets, cell records
+    int2* walk_hdr = nullptr;
+    float* walk_s0 = nullptr;
+    int4* walk_rec = nullptr;
+    int* walk_over = nullptr;  // slots without records [walk_cap], their count at [walk_cap]
+    int64_t walk_cap = 0;
+};
+
+// A training batch whose ordering and traversal ran ahead on the auxiliary stream.
+struct PreparedBatch {
+    BatchBufs b;
+    cudaEvent_t fence = nullptr;  // recorded on the grid's stream when the preparation is enqueued
+    cudaEvent_t ready = nullptr;  // recorded on the auxiliary stream when the preparation is done
+    const float* rays = nullptr;
+    int64_t n = 0;
+    const int* perm = nullptr;  // NULL: given order
+    bool valid = false;
+};
+
 namespace sdg {
 // Device status word of the bounds-checked build (SDG_CHECKED) on `device`, allocated on first use; NULL in the
 // normal build.
@@ -73,16 +98,9 @@ struct sdg_grid_s {
     int* h_minmax = nullptr;                   // pinned host [6]
     float* loss_buf = nullptr;                 // per-ray loss scratch of the fused training pass
     int64_t loss_cap = 0;
-    // records of the traversal pass (k_walk) for up to walk_cap rays: header, skip-space offsets, cell records
-    int2* walk_hdr = nullptr;
-    float* walk_s0 = nullptr;
-    int4* walk_rec = nullptr;
-    int* walk_over = nullptr;  // slots without records [walk_cap], their count at [walk_cap]
-    int64_t walk_cap = 0;
-    int* order_keys = nullptr;  // surface ordering of a training batch: per-ray bucket [order_cap]
-    int* order_perm = nullptr;  // processing order [order_cap]
-    int* order_hist = nullptr;  // bucket counts, then offsets [kOrderBuckets]
-    int64_t order_cap = 0;
+    BatchBufs batch;     // ordering and traversal scratch of the passes enqueued on `stream`
+    PreparedBatch prep[2];  // training batches prepared ahead on `aux` (sdg_train_prepare)
+    cudaStream_t aux = nullptr;  // auxiliary stream of the preparations, created on first use
     void* fuse_cams = nullptr;  // per-frame cameras of a fusion call [fuse_cam_cap]
     int64_t fuse_cam_cap = 0;
     // learnable Laplace scale: dL/dbeta accumulates on the device until the next optimiser step
@@ -142,6 +160,13 @@ int loss_scratch(sdg_grid g, int64_t n, float** out);
 // Enqueues the traversal pass (k_walk) of n rays, processed in order perm (NULL: as given), into the grid-owned
 // walk records and points a.walk at them (render.cu).
 int walk_rays(sdg_grid g, const float* rays, const int* perm, int64_t n, PassArgs& a);
+// The same into the batch scratch b on stream s (every buffer growth first drains the grid's streams).
+int walk_rays_into(sdg_grid g, BatchBufs& b, cudaStream_t s, const float* rays, const int* perm, int64_t n,
+                   PassArgs& a);
+// Frees a batch scratch (the caller has drained the streams that use it).
+void free_batch(BatchBufs& b);
+// Blocks until the grid's stream and its auxiliary stream are idle.
+int drain_streams(sdg_grid g);
 
 // Buckets of the surface ordering of a training batch (order.cu).
 constexpr int kOrderBuckets = 1 << 15;
@@ -150,4 +175,7 @@ constexpr int kOrderBuckets = 1 << 15;
 // grid-owned processing order (valid until the next call on this grid).  Sets *perm to NULL, with nothing
 // enqueued, when the grid holds no block.
 int order_rays_by_surface(sdg_grid g, const float* rays, const float* tdepth, int64_t n, const int** perm);
+// The same into the batch scratch b on stream s.
+int order_rays_into(sdg_grid g, BatchBufs& b, cudaStream_t s, const float* rays, const float* tdepth, int64_t n,
+                    const int** perm);
 }  // namespace sdg

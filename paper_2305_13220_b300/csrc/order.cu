@@ -141,21 +141,25 @@ int bit_length(uint32_t v) { return v ? 32 - __builtin_clz(v) : 0; }
 
 }  // namespace
 
-int order_rays_by_surface(sdg_grid g, const float* rays, const float* tdepth, int64_t n, const int** perm) {
+int order_rays_into(sdg_grid g, BatchBufs& b, cudaStream_t st, const float* rays, const float* tdepth, int64_t n,
+                    const int** perm) {
     *perm = nullptr;
     if (g->n_blocks == 0 || n == 0) return SDG_OK;
     if (n > ((int64_t)1 << 31) - 1) return fail(SDG_ERR_ARG, "surface ordering: at most 2^31 - 1 rays");
-    if (g->order_cap < n) {
-        if (g->order_keys || g->order_perm) SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
-        if (g->order_keys) cudaFree(g->order_keys);
-        if (g->order_perm) cudaFree(g->order_perm);
-        g->order_keys = g->order_perm = nullptr;
-        g->order_cap = 0;
-        SDG_CUDA_TRY(cudaMalloc((void**)&g->order_keys, sizeof(int) * n));
-        SDG_CUDA_TRY(cudaMalloc((void**)&g->order_perm, sizeof(int) * n));
-        g->order_cap = n;
+    if (b.order_cap < n) {
+        if (b.order_keys || b.order_perm) {
+            int rc = drain_streams(g);  // earlier work may still read them
+            if (rc) return rc;
+        }
+        if (b.order_keys) cudaFree(b.order_keys);
+        if (b.order_perm) cudaFree(b.order_perm);
+        b.order_keys = b.order_perm = nullptr;
+        b.order_cap = 0;
+        SDG_CUDA_TRY(cudaMalloc((void**)&b.order_keys, sizeof(int) * n));
+        SDG_CUDA_TRY(cudaMalloc((void**)&b.order_perm, sizeof(int) * n));
+        b.order_cap = n;
     }
-    if (!g->order_hist) SDG_CUDA_TRY(cudaMalloc((void**)&g->order_hist, sizeof(int) * kOrderBuckets));
+    if (!b.order_hist) SDG_CUDA_TRY(cudaMalloc((void**)&b.order_hist, sizeof(int) * kOrderBuckets));
 
     OrderParams p{};
     p.inv_L = 1.0f / (8.0f * g->desc.voxel_size);
@@ -177,17 +181,21 @@ int order_rays_by_surface(sdg_grid g, const float* rays, const float* tdepth, in
     p.last = used < kOrderBuckets ? used : kOrderBuckets - 1;
 
     const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
-    SDG_CUDA_TRY(cudaMemsetAsync(g->order_hist, 0, sizeof(int) * kOrderBuckets, g->stream));
-    k_surface_keys<<<blocks, kThreads, 0, g->stream>>>(rays, tdepth, n, p, g->order_keys, g->order_hist);
+    SDG_CUDA_TRY(cudaMemsetAsync(b.order_hist, 0, sizeof(int) * kOrderBuckets, st));
+    k_surface_keys<<<blocks, kThreads, 0, st>>>(rays, tdepth, n, p, b.order_keys, b.order_hist);
     SDG_LAUNCH_CHECK("surface keys");
     SDG_CUDA_TRY(cudaFuncSetAttribute(k_scan_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(int) * kOrderBuckets)));  // per device, so set on every call
-    k_scan_buckets<<<1, 1024, sizeof(int) * kOrderBuckets, g->stream>>>(g->order_hist);
+    k_scan_buckets<<<1, 1024, sizeof(int) * kOrderBuckets, st>>>(b.order_hist);
     SDG_LAUNCH_CHECK("bucket scan");
-    k_scatter_rays<<<blocks, kThreads, 0, g->stream>>>(g->order_keys, n, g->order_hist, g->order_perm);
+    k_scatter_rays<<<blocks, kThreads, 0, st>>>(b.order_keys, n, b.order_hist, b.order_perm);
     SDG_LAUNCH_CHECK("ray scatter");
-    *perm = g->order_perm;
+    *perm = b.order_perm;
     return SDG_OK;
+}
+
+int order_rays_by_surface(sdg_grid g, const float* rays, const float* tdepth, int64_t n, const int** perm) {
+    return order_rays_into(g, g->batch, g->stream, rays, tdepth, n, perm);
 }
 
 }  // namespace sdg

@@ -130,42 +130,67 @@ __global__ void __launch_bounds__(256) k_walk(GridDev g, const float* __restrict
 }  // namespace
 
 namespace sdg {
-// Grows the grid-owned walk records to n rays (valid until the next call on this grid).
-int walk_scratch(sdg_grid g, int64_t n) {
-    if (g->walk_cap >= n) return SDG_OK;
-    if (g->walk_hdr || g->walk_s0 || g->walk_rec || g->walk_over) {
-        SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));  // earlier work on the stream may still read them
-        cudaFree(g->walk_hdr);
-        cudaFree(g->walk_s0);
-        cudaFree(g->walk_rec);
-        cudaFree(g->walk_over);
-    }
-    g->walk_hdr = nullptr;
-    g->walk_s0 = nullptr;
-    g->walk_rec = nullptr;
-    g->walk_over = nullptr;
-    g->walk_cap = 0;
-    SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_hdr, sizeof(int2) * n));
-    SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_s0, sizeof(float) * kWalkCap * n));
-    SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_rec, sizeof(int4) * kWalkCap * n));
-    SDG_CUDA_TRY(cudaMalloc((void**)&g->walk_over, sizeof(int) * (n + 1)));  // list, and its length at [n]
-    g->walk_cap = n;
+// Blocks until the grid's stream and its auxiliary stream are idle.
+int drain_streams(sdg_grid g) {
+    SDG_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (g->aux) SDG_CUDA_TRY(cudaStreamSynchronize(g->aux));
     return SDG_OK;
 }
 
-// Enqueues the traversal pass of n rays (processing order perm, or the given order) and points a.walk at its
-// records.
-int walk_rays(sdg_grid g, const float* rays, const int* perm, int64_t n, PassArgs& a) {
+void free_batch(BatchBufs& b) {
+    void* ptrs[] = {b.order_keys, b.order_perm, b.order_hist, b.walk_hdr, b.walk_s0, b.walk_rec, b.walk_over};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    b = BatchBufs{};
+}
+
+// Grows the walk records of b to n rays (valid until the next pass that uses b).
+int walk_scratch(sdg_grid g, BatchBufs& b, int64_t n) {
+    if (b.walk_cap >= n) return SDG_OK;
+    if (b.walk_hdr || b.walk_s0 || b.walk_rec || b.walk_over) {
+        int rc = drain_streams(g);  // earlier work may still read them
+        if (rc) return rc;
+        cudaFree(b.walk_hdr);
+        cudaFree(b.walk_s0);
+        cudaFree(b.walk_rec);
+        cudaFree(b.walk_over);
+    }
+    b.walk_hdr = nullptr;
+    b.walk_s0 = nullptr;
+    b.walk_rec = nullptr;
+    b.walk_over = nullptr;
+    b.walk_cap = 0;
+    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_hdr, sizeof(int2) * n));
+    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_s0, sizeof(float) * kWalkCap * n));
+    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_rec, sizeof(int4) * kWalkCap * n));
+    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_over, sizeof(int) * (n + 1)));  // list, and its length at [n]
+    b.walk_cap = n;
+    return SDG_OK;
+}
+
+// The records of b as the render kernels read them.
+WalkBufs walk_bufs(const BatchBufs& b) {
+    return WalkBufs{b.walk_hdr, b.walk_s0, b.walk_rec, b.walk_over, b.walk_over + b.walk_cap};
+}
+
+int walk_rays_into(sdg_grid g, BatchBufs& b, cudaStream_t st, const float* rays, const int* perm, int64_t n,
+                   PassArgs& a) {
     a.walk = WalkBufs{nullptr, nullptr, nullptr, nullptr, nullptr};
     if (n == 0) return SDG_OK;
-    int rc = walk_scratch(g, n);
+    int rc = walk_scratch(g, b, n);
     if (rc) return rc;
-    const WalkBufs w{g->walk_hdr, g->walk_s0, g->walk_rec, g->walk_over, g->walk_over + g->walk_cap};
-    SDG_CUDA_TRY(cudaMemsetAsync(w.n_over, 0, sizeof(int), g->stream));
-    k_walk<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(g->dev(), rays, perm, n, w);
+    const WalkBufs w = walk_bufs(b);
+    SDG_CUDA_TRY(cudaMemsetAsync(w.n_over, 0, sizeof(int), st));
+    k_walk<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->dev(), rays, perm, n, w);
     SDG_LAUNCH_CHECK("traversal pass");
     a.walk = w;
     return SDG_OK;
+}
+
+// Enqueues the traversal pass of n rays (processing order perm, or the given order) on the grid's stream into its
+// batch scratch and points a.walk at the records.
+int walk_rays(sdg_grid g, const float* rays, const int* perm, int64_t n, PassArgs& a) {
+    return walk_rays_into(g, g->batch, g->stream, rays, perm, n, a);
 }
 }  // namespace sdg
 
@@ -379,6 +404,8 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
     if (n > (int64_t)1 << 31) return fail(SDG_ERR_ARG, "sdg_train_step_rays: at most 2^31 rays per call");
     if (lo->ray_order != SDG_ORDER_AUTO && lo->ray_order != SDG_ORDER_GIVEN && lo->ray_order != SDG_ORDER_SURFACE)
         return fail(SDG_ERR_ARG, "sdg_train_step_rays: unknown ray_order");
+    if (lo->prepared < 0 || lo->prepared > 2 || lo->reserved != 0)
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays: prepared must be 0, 1 or 2 and reserved 0");
     if ((rc = use_device(g))) return rc;
     if (n == 0) {
         if (loss_sum) SDG_CUDA_TRY(cudaMemsetAsync(loss_sum, 0, sizeof(float), g->stream));
@@ -396,10 +423,20 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
     a.lam_s = lo->lambda_sem;
     a.inv_n = 1.0f / (float)(lo->norm_rays > 0 ? lo->norm_rays : n);
     a.loss = per_ray;
-    if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
-        if ((rc = order_rays_by_surface(g, rays, tdepth, n, &a.perm))) return rc;
+    if (lo->prepared) {
+        PreparedBatch& P = g->prep[lo->prepared - 1];
+        if (!P.valid || P.rays != rays || P.n != n)
+            return fail(SDG_ERR_ARG, "sdg_train_step_rays: the prepared slot does not hold these rays");
+        SDG_CUDA_TRY(cudaStreamWaitEvent(g->stream, P.ready, 0));
+        a.perm = P.perm;
+        a.walk = walk_bufs(P.b);
+        P.valid = false;
+    } else {
+        if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
+            if ((rc = order_rays_by_surface(g, rays, tdepth, n, &a.perm))) return rc;
+        }
+        if ((rc = walk_rays(g, rays, a.perm, n, a))) return rc;
     }
-    if ((rc = walk_rays(g, rays, a.perm, n, a))) return rc;
     if (lo->learn_beta) {
         if (g->beta_part_cap < n) {
             if (g->beta_part) {
@@ -441,6 +478,7 @@ extern "C" int sdg_train_step_rays_normal(sdg_grid g, const float* rays, int64_t
     if (n > (int64_t)1 << 31) return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: at most 2^31 rays per call");
     if (g->desc.n_sem) return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: grids with logits are not supported");
     if (lo->learn_beta) return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: learn_beta is not supported");
+    if (lo->prepared) return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: prepared batches are not supported");
     if (lo->ray_order != SDG_ORDER_AUTO && lo->ray_order != SDG_ORDER_GIVEN && lo->ray_order != SDG_ORDER_SURFACE)
         return fail(SDG_ERR_ARG, "sdg_train_step_rays_normal: unknown ray_order");
     if ((rc = use_device(g))) return rc;
@@ -533,6 +571,8 @@ extern "C" int sdg_train_step_rays_noalloc(sdg_grid g, const float* rays, int64_
         return fail(SDG_ERR_ARG, "sdg_train_step_rays_noalloc: null argument");
     if (lo->learn_beta)  // dL/dbeta needs a per-ray partial buffer this entry point does not have
         return fail(SDG_ERR_ARG, "sdg_train_step_rays_noalloc: learn_beta is not supported");
+    if (lo->prepared)  // a prepared batch lives in grid-owned scratch
+        return fail(SDG_ERR_ARG, "sdg_train_step_rays_noalloc: prepared batches are not supported");
     if (n > kNoAllocMaxRays)
         return fail(SDG_ERR_CAPACITY, "sdg_train_step_rays_noalloc: n = " + std::to_string(n) +
                                           " rays exceeds the fixed scratch capacity of 1048576 rays");
@@ -568,5 +608,37 @@ extern "C" int sdg_grid_set_pass_events(sdg_grid g, void* start, void* stop) {
     if (!g || (!start) != (!stop)) return fail(SDG_ERR_ARG, "sdg_grid_set_pass_events: both events or neither");
     g->pass_ev[0] = (cudaEvent_t)start;
     g->pass_ev[1] = (cudaEvent_t)stop;
+    return SDG_OK;
+}
+
+extern "C" int sdg_train_prepare(sdg_grid g, const float* rays, int64_t n, const float* tdepth,
+                                 const sdg_loss_opts* lo, int32_t slot) {
+    if (!g || !lo || n <= 0 || !rays || !tdepth || slot < 0 || slot > 1)
+        return fail(SDG_ERR_ARG, "sdg_train_prepare: null argument, n <= 0 or slot not 0 or 1");
+    if (!aligned16(rays)) return fail(SDG_ERR_ARG, "sdg_train_prepare: rays must be 16-byte aligned");
+    if (n > (int64_t)1 << 31) return fail(SDG_ERR_ARG, "sdg_train_prepare: at most 2^31 rays per call");
+    if (lo->ray_order != SDG_ORDER_AUTO && lo->ray_order != SDG_ORDER_GIVEN && lo->ray_order != SDG_ORDER_SURFACE)
+        return fail(SDG_ERR_ARG, "sdg_train_prepare: unknown ray_order");
+    int rc = use_device(g);
+    if (rc) return rc;
+    if (!g->aux) SDG_CUDA_TRY(cudaStreamCreateWithFlags(&g->aux, cudaStreamNonBlocking));
+    PreparedBatch& P = g->prep[slot];
+    if (!P.fence) SDG_CUDA_TRY(cudaEventCreateWithFlags(&P.fence, cudaEventDisableTiming));
+    if (!P.ready) SDG_CUDA_TRY(cudaEventCreateWithFlags(&P.ready, cudaEventDisableTiming));
+    P.valid = false;
+    // after everything already on the grid's stream: the inputs, and the last pass that read this slot
+    SDG_CUDA_TRY(cudaEventRecord(P.fence, g->stream));
+    SDG_CUDA_TRY(cudaStreamWaitEvent(g->aux, P.fence, 0));
+    const int* perm = nullptr;
+    if (lo->ray_order == SDG_ORDER_SURFACE || (lo->ray_order == SDG_ORDER_AUTO && n >= kAutoSurfaceOrderRays)) {
+        if ((rc = order_rays_into(g, P.b, g->aux, rays, tdepth, n, &perm))) return rc;
+    }
+    PassArgs a{};
+    if ((rc = walk_rays_into(g, P.b, g->aux, rays, perm, n, a))) return rc;
+    SDG_CUDA_TRY(cudaEventRecord(P.ready, g->aux));
+    P.rays = rays;
+    P.n = n;
+    P.perm = perm;
+    P.valid = true;
     return SDG_OK;
 }

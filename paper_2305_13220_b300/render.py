@@ -145,22 +145,35 @@ def train_step_rays(grid: Grid, rays: torch.Tensor, t_rgb: torch.Tensor, t_depth
                     t_sem: Optional[torch.Tensor] = None, n_samples: int = 128, seed: int = 0, ray_id0: int = 0,
                     stratified: bool = True, bg=(0.0, 0.0, 0.0), lambda_depth: float = 0.1, lambda_sem: float = 0.1,
                     loss: Optional[torch.Tensor] = None, loss_sum: Optional[torch.Tensor] = None,
-                    ray_order: str = "auto", learn_beta: bool = False, norm_rays: int = 0):
+                    ray_order: str = "auto", learn_beta: bool = False, norm_rays: int = 0,
+                    prepared: Optional[int] = None):
     """Fused forward + L1 losses + backward; gradients accumulate into the grid.
 
     ray_order: "auto" (surface order for batches of 65536 rays or more), "given" or "surface" (rays grouped by
     the coarse cell of their target surface point; per-ray results are unchanged).  learn_beta: also accumulate
     dL/dbeta for the next optimiser step, which then updates the grid's Laplace scale.  norm_rays: the n of the
-    means over rays (0: these rays' count; a data-parallel shard passes the whole batch's)."""
+    means over rays (0: these rays' count; a data-parallel shard passes the whole batch's).  prepared: the slot
+    train_prepare prepared these rays in (their ordering and traversal then ran ahead)."""
     o = render_opts(n_samples, seed, ray_id0, stratified, "recompute", bg)
     orders = {"auto": A.ORDER_AUTO, "given": A.ORDER_GIVEN, "surface": A.ORDER_SURFACE}
     if ray_order not in orders:
         raise ValueError(f"ray_order must be one of {sorted(orders)}")
     lo = A.LossOpts(lambda_depth=lambda_depth, lambda_sem=lambda_sem, ray_order=orders[ray_order],
-                    learn_beta=1 if learn_beta else 0, norm_rays=int(norm_rays))
+                    learn_beta=1 if learn_beta else 0, norm_rays=int(norm_rays),
+                    prepared=0 if prepared is None else int(prepared) + 1)
     A.call("sdg_train_step_rays", grid.handle, _ptr(rays, torch.float32, "rays"), rays.shape[0],
            _ptr(t_rgb, torch.float32, "t_rgb"), _ptr(t_depth, torch.float32, "t_depth"), _ptr(t_sem), C.byref(o),
            C.byref(lo), _ptr(loss), _ptr(loss_sum))
+
+
+def train_prepare(grid: Grid, rays: torch.Tensor, t_depth: torch.Tensor, slot: int, ray_order: str = "auto"):
+    """Enqueues the ordering and traversal of a training batch on the grid's auxiliary stream into `slot` (0, 1):
+    called after one step's train_step_rays and before its optimiser step, the next batch's traversal runs beside
+    the optimiser; pass prepared=slot to the train_step_rays of these rays."""
+    orders = {"auto": A.ORDER_AUTO, "given": A.ORDER_GIVEN, "surface": A.ORDER_SURFACE}
+    lo = A.LossOpts(ray_order=orders[ray_order])
+    A.call("sdg_train_prepare", grid.handle, _ptr(rays, torch.float32, "rays"), rays.shape[0],
+           _ptr(t_depth, torch.float32, "t_depth"), C.byref(lo), int(slot))
 
 
 class _RenderFn(torch.autograd.Function):
