@@ -617,7 +617,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     const float s_after = __shfl_down_sync(kFull, s_[0], 1);  // first sample of the next lane
 
     float t_[Q] = {}, dl_[Q], d_[Q], cr_[Q], cg_[Q], cb_[Q], tau_[Q], dsig_[Q];
-    int blk_[Q], lc_[Q];
+    int ba_[Q];  // base voxel of the sample's cell: block * 512 + local cell index (-1: no block)
     float bq_[kBeta ? Q : 1];
     float gnx_[kNrm ? Q : 1], gny_[kNrm ? Q : 1], gnz_[kNrm ? Q : 1];  // grad f at the samples (Eq. 17)
     unsigned vmask = 0;
@@ -641,7 +641,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         t_[i] = 0.f; dl_[i] = 0.f; d_[i] = 0.f; cr_[i] = cg_[i] = cb_[i] = 0.f; tau_[i] = 0.f; dsig_[i] = 0.f;
         if constexpr (kBeta) bq_[i] = 0.f;
         if constexpr (kNrm) gnx_[i] = gny_[i] = gnz_[i] = 0.f;
-        blk_[i] = -1; lc_[i] = 0;
+        ba_[i] = -1;
         if (!any) {  // warp-uniform
             if constexpr (kTrace) {
                 if (k < N) {
@@ -716,7 +716,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         const float pz = fmaf(t_[i], j.d.z, j.o.z) * g.inv_vs;
         const float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
         const int cx = (int)flx, cy = (int)fly, cz = (int)flz;
-        lc_[i] = (cx & 7) | ((cy & 7) << 3) | ((cz & 7) << 6);
+        const int lc = (cx & 7) | ((cy & 7) << 3) | ((cz & 7) << 6);
         if constexpr (!kStoreIn) {
             // the sample's own block: the traversal cell's, unless rounding put it across a block face
             const int own = dense_cell(g, cx >> 3, cy >> 3, cz >> 3);
@@ -724,7 +724,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 blk = own < 0 || !sdg_in_range(g.status, own, g.dense_cells, SDG_CHECK_DENSE) ? -1
                                                                                           : __ldg(g.dense + own);
         }
-        blk_[i] = blk;
+        ba_[i] = blk >= 0 ? blk * 512 + lc : -1;
         if constexpr (kTrace) {
             const int64_t q = j.idx * N + k;
             a.tr_t[q] = t_[i];
@@ -744,12 +744,12 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         } else {
             // a sample in the previous sample's cell reuses its corner values
             const bool same =
-                reuse && i > 0 && ((vmask >> (i - 1)) & 1u) && blk_[i] == blk_[i - 1] && lc_[i] == lc_[i - 1];
+                reuse && i > 0 && ((vmask >> (i - 1)) & 1u) && ba_[i] == ba_[i - 1];
             if (same) {
                 valid = true;
             } else {
                 int addr[8];
-                valid = blk_[i] >= 0 && corner_addresses(g, blk_[i], lc_[i], addr);
+                valid = ba_[i] >= 0 && corner_addresses(g, ba_[i] >> 9, ba_[i] & 511, addr);
                 if (valid) load_corners<BF16>(g, addr, cs, crr, cgg, cbb);
             }
             if (valid) {
@@ -788,7 +788,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             rec[2 * CS] = cr_[i];
             rec[3 * CS] = cg_[i];
             rec[4 * CS] = cb_[i];
-            rec[5 * CS] = __int_as_float(blk_[i]);
+            rec[5 * CS] = __int_as_float(ba_[i] >= 0 ? ba_[i] >> 9 : -1);
         }
     };
     // The fused training and the forward modes place all samples first and then reuse a cell's corners for the
@@ -832,7 +832,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     }
 
     // runs: consecutive valid samples of a lane in the same cell share their 8 corners
-    auto same_cell = [&](int i0, int i1) { return blk_[i0] == blk_[i1] && lc_[i0] == lc_[i1]; };
+    auto same_cell = [&](int i0, int i1) { return ba_[i0] == ba_[i1]; };
     auto run_start = [&](int i) {
         return ((vmask >> i) & 1u) && (i == 0 || !((vmask >> (i - 1)) & 1u) || !same_cell(i - 1, i));
     };
@@ -856,7 +856,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 if (run_start(i)) {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) W[e] = 0.f;
-                    corner_addresses(g, blk_[i], lc_[i], addr);
+                    corner_addresses(g, ba_[i] >> 9, ba_[i] & 511, addr);
                 }
                 if (v) {
                     float r[8];
@@ -1008,7 +1008,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if (run_start(i)) {
-                    corner_addresses(g, blk_[i], lc_[i], addr);
+                    corner_addresses(g, ba_[i] >> 9, ba_[i] & 511, addr);
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         dot[e] = 0.f;
@@ -1068,7 +1068,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             if (run_start(i)) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) aS[e] = aW[e] = 0.f;
-                corner_addresses(g, blk_[i], lc_[i], addr);
+                corner_addresses(g, ba_[i] >> 9, ba_[i] & 511, addr);
             }
             if (v) {
                 float r[8];
