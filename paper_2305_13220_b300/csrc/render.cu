@@ -20,11 +20,6 @@ struct sdg_ctx_s {
     float* rec_S;
 };
 
-namespace sdg {
-template <int MODE, bool BF16, bool SEM>
-int launch_q(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs& a, int Q, cudaStream_t s);
-}
-
 namespace {
 
 // Smallest batch that SDG_ORDER_AUTO puts in surface order.
@@ -43,14 +38,9 @@ int launch_pass(sdg_grid g, const float* rays, uint32_t id0, const PassArgs& a) 
     if (a.n == 0) return SDG_OK;
     const GridDev gd = g->dev();
     const int Q = pick_q(a.N);
-    const bool bf16 = g->desc.rgb_dtype == SDG_BF16;
-    const bool sem = g->desc.n_sem > 0;
     int rc = pass_event(g, 0);
     if (rc) return rc;
-    if (!bf16 && !sem) rc = launch_q<MODE, false, false>(gd, rays, id0, a, Q, g->stream);
-    else if (!bf16 && sem) rc = launch_q<MODE, false, true>(gd, rays, id0, a, Q, g->stream);
-    else if (bf16 && !sem) rc = launch_q<MODE, true, false>(gd, rays, id0, a, Q, g->stream);
-    else rc = launch_q<MODE, true, true>(gd, rays, id0, a, Q, g->stream);
+    rc = launch_layout<MODE>(g->desc.rgb_dtype == SDG_BF16, g->desc.n_sem, gd, rays, id0, a, Q, g->stream);
     return rc ? rc : pass_event(g, 1);
 }
 
@@ -62,8 +52,8 @@ int launch_pass_nosem(sdg_grid g, const float* rays, uint32_t id0, const PassArg
     const int Q = pick_q(a.N);
     int rc = pass_event(g, 0);
     if (rc) return rc;
-    if (g->desc.rgb_dtype == SDG_BF16) rc = launch_q<MODE, true, false>(gd, rays, id0, a, Q, g->stream);
-    else rc = launch_q<MODE, false, false>(gd, rays, id0, a, Q, g->stream);
+    if (g->desc.rgb_dtype == SDG_BF16) rc = launch_q<MODE, true, 0>(gd, rays, id0, a, Q, g->stream);
+    else rc = launch_q<MODE, false, 0>(gd, rays, id0, a, Q, g->stream);
     return rc ? rc : pass_event(g, 1);
 }
 

@@ -2,8 +2,8 @@
 // compile in parallel; fewer, larger files keep the library small).
 #include "render_kernels.cuh"
 
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD, true, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD_STORE, true, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN, true, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_BETA, true, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_NRM, true, false)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD, true, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD_STORE, true, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN, true, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_BETA, true, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_NRM, true, 0)

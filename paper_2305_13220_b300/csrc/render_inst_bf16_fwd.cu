@@ -2,6 +2,6 @@
 // compile in parallel; fewer, larger files keep the library small).
 #include "render_kernels.cuh"
 
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD, true, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_STORE, true, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, true, false)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD, true, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_STORE, true, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, true, 0)

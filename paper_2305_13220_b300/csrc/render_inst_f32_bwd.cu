@@ -2,8 +2,8 @@
 // compile in parallel; fewer, larger files keep the library small).
 #include "render_kernels.cuh"
 
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD, false, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD_STORE, false, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN, false, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_BETA, false, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_NRM, false, false)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD, false, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_BWD_STORE, false, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN, false, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_BETA, false, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_NRM, false, 0)

@@ -2,6 +2,6 @@
 // compile in parallel; fewer, larger files keep the library small).
 #include "render_kernels.cuh"
 
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD, false, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_STORE, false, false)
-SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, false, false)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD, false, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_STORE, false, 0)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, false, 0)

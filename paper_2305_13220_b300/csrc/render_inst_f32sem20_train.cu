@@ -1,0 +1,7 @@
+// Render kernels of the f32sem layout with up to 20 semantic channels, train passes (the
+// instantiations are spread over files so that they compile in parallel; fewer, larger files keep the library
+// small).
+#include "render_kernels.cuh"
+
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN, false, sdg::kSemCapSmall)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_TRAIN_BETA, false, sdg::kSemCapSmall)

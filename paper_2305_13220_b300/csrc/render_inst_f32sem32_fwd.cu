@@ -1,0 +1,8 @@
+// Render kernels of the f32sem layout with 24-32 semantic channels, fwd passes (the
+// instantiations are spread over files so that they compile in parallel; fewer, larger files keep the library
+// small).
+#include "render_kernels.cuh"
+
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD, false, 32)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_STORE, false, 32)
+SDG_INSTANTIATE_LAUNCH(sdg::PASS_FWD_TRACE, false, 32)

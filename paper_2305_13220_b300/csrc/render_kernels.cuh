@@ -8,13 +8,13 @@ namespace sdg {
 
 // Resident 256-thread blocks per SM requested from the register allocator: three (80 registers) where the
 // program fits with no or a few bytes of spill (measured on the room training step: 1.69 -> 1.49 ms), fewer
-// for the larger per-lane sample counts and the semantic variants, which need more registers.
-template <int MODE, bool SEM, int Q>
+// for the larger per-lane sample counts and the semantic variants (NSC > 0), which need more registers.
+template <int MODE, int NSC, int Q>
 constexpr int render_min_blocks() {
 #ifdef SDG_RENDER_MIN_BLOCKS
     return SDG_RENDER_MIN_BLOCKS;
 #else
-    return SEM ? (Q >= 6 ? 1 : 2) : (MODE == PASS_TRAIN_NRM || Q >= 6 ? 2 : 3);
+    return NSC > 0 ? (Q >= 6 ? 1 : 2) : (MODE == PASS_TRAIN_NRM || Q >= 6 ? 2 : 3);
 #endif
 }
 
@@ -39,8 +39,8 @@ __device__ __forceinline__ void load_job(const GridDev& g, const float* rays, co
 // over the overflow list a.walk.over[0, *a.walk.n_over) -- launched with one warp per slot like the records
 // kernel: the list is short (0.15% of the room step's rays) and the warps past its end exit at once.  Kept apart,
 // the records kernel needs no shared memory, which leaves L1 to the voxel gathers.
-template <int MODE, bool BF16, bool SEM, int Q, bool INWARP>
-__global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>()))
+template <int MODE, bool BF16, int NSC, int Q, bool INWARP>
+__global__ void __launch_bounds__(256, (render_min_blocks<MODE, NSC, Q>()))
     k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
     __shared__ WarpSmem smem[INWARP ? kWarpsPerBlock : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -49,37 +49,37 @@ __global__ void __launch_bounds__(256, (render_min_blocks<MODE, SEM, Q>()))
     if constexpr (!INWARP) {
         if (w >= a.n) return;  // warp-uniform
         load_job(g, rays, a.perm, ray_id0, w, a.n, j);
-        ray_program<MODE, BF16, SEM, Q, false>(g, a, j, smem[0], lane);
+        ray_program<MODE, BF16, NSC, Q, false>(g, a, j, smem[0], lane);
     } else {
         const bool list = a.walk.hdr != nullptr;
         const int64_t end = list ? (int64_t)__ldg(a.walk.n_over) : a.n;
         if (w >= end) return;  // warp-uniform
         load_job(g, rays, a.perm, ray_id0, list ? (int64_t)__ldg(a.walk.over + w) : w, a.n, j);
-        ray_program<MODE, BF16, SEM, Q, true>(g, a, j, smem[warp], lane);
+        ray_program<MODE, BF16, NSC, Q, true>(g, a, j, smem[warp], lane);
     }
 }
 
-template <int MODE, bool BF16, bool SEM, int Q>
+template <int MODE, bool BF16, int NSC, int Q>
 int launch_one(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs& a, cudaStream_t s) {
     const unsigned blocks = (unsigned)((a.n + kWarpsPerBlock - 1) / kWarpsPerBlock);
     constexpr bool kNoWalk = MODE == PASS_BWD_STORE;  // samples come from the forward's stored records
     if (kNoWalk || a.walk.hdr) {
-        k_render<MODE, BF16, SEM, Q, false><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
-        if (!kNoWalk) k_render<MODE, BF16, SEM, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
+        k_render<MODE, BF16, NSC, Q, false><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
+        if (!kNoWalk) k_render<MODE, BF16, NSC, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
     } else {
-        k_render<MODE, BF16, SEM, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
+        k_render<MODE, BF16, NSC, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
     }
     return SDG_OK;
 }
 
-template <int MODE, bool BF16, bool SEM>
+template <int MODE, bool BF16, int NSC>
 int launch_q(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs& a, int Q, cudaStream_t s) {
     int rc;
     switch (Q) {
-        case 2: rc = launch_one<MODE, BF16, SEM, 2>(gd, rays, id0, a, s); break;
-        case 4: rc = launch_one<MODE, BF16, SEM, 4>(gd, rays, id0, a, s); break;
-        case 6: rc = launch_one<MODE, BF16, SEM, 6>(gd, rays, id0, a, s); break;
-        default: rc = launch_one<MODE, BF16, SEM, 8>(gd, rays, id0, a, s); break;
+        case 2: rc = launch_one<MODE, BF16, NSC, 2>(gd, rays, id0, a, s); break;
+        case 4: rc = launch_one<MODE, BF16, NSC, 4>(gd, rays, id0, a, s); break;
+        case 6: rc = launch_one<MODE, BF16, NSC, 6>(gd, rays, id0, a, s); break;
+        default: rc = launch_one<MODE, BF16, NSC, 8>(gd, rays, id0, a, s); break;
     }
     if (rc) return rc;
     SDG_LAUNCH_CHECK("render kernel");
@@ -89,6 +89,9 @@ int launch_q(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs&
 
 }  // namespace sdg
 
-#define SDG_INSTANTIATE_LAUNCH(MODE, BF16, SEM)                                                         \
-    template int sdg::launch_q<MODE, BF16, SEM>(const GridDev&, const float*, uint32_t, const PassArgs&, int, \
+#define SDG_INSTANTIATE_LAUNCH(MODE, BF16, NSC)                                                         \
+    template int sdg::launch_q<MODE, BF16, NSC>(const GridDev&, const float*, uint32_t, const PassArgs&, int, \
                                                 cudaStream_t);
+#define SDG_EXTERN_LAUNCH(MODE, BF16, NSC)                                                                   \
+    extern template int sdg::launch_q<MODE, BF16, NSC>(const GridDev&, const float*, uint32_t, const PassArgs&, \
+                                                       int, cudaStream_t);

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
     a.out_rgb = ch.rgb;
     a.out_depth = ch.depth;
     a.out_opac = ch.opac;
-    ray_program<PASS_FWD, BF16, false, Q, true>(scenes[ch.scene], a, j, smem[warp], lane);
+    ray_program<PASS_FWD, BF16, 0, Q, true>(scenes[ch.scene], a, j, smem[warp], lane);
 }
 
 double now_ms() {

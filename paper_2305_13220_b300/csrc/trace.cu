@@ -4,14 +4,22 @@
 #include "internal.h"
 #include "render_kernels.cuh"
 
+// Instantiated in the render_inst_*_fwd.cu files.
+SDG_EXTERN_LAUNCH(sdg::PASS_FWD_TRACE, false, 0)
+SDG_EXTERN_LAUNCH(sdg::PASS_FWD_TRACE, true, 0)
+SDG_EXTERN_LAUNCH(sdg::PASS_FWD_TRACE, false, sdg::kSemCapSmall)
+SDG_EXTERN_LAUNCH(sdg::PASS_FWD_TRACE, true, sdg::kSemCapSmall)
+SDG_EXTERN_LAUNCH(sdg::PASS_FWD_TRACE, false, 32)
+SDG_EXTERN_LAUNCH(sdg::PASS_FWD_TRACE, true, 32)
+
 using namespace sdg;
 
 namespace {
 
 // One warp per pixel of an H x W pinhole view, rays formed by pinhole_ray as the serving kernel forms them and
 // walked in-warp as it walks them.
-template <bool BF16, bool SEM, int Q>
-__global__ void __launch_bounds__(256, (render_min_blocks<PASS_FWD_TRACE, SEM, Q>()))
+template <bool BF16, int NSC, int Q>
+__global__ void __launch_bounds__(256, (render_min_blocks<PASS_FWD_TRACE, NSC, Q>()))
     k_trace_view(GridDev g, int H, int W, Cam6 cam, float tnear, float tfar, float* rays_out, PassArgs a) {
     __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -30,18 +38,18 @@ __global__ void __launch_bounds__(256, (render_min_blocks<PASS_FWD_TRACE, SEM, Q
         r[0] = make_float4(j.o.x, j.o.y, j.o.z, tnear);
         r[1] = make_float4(j.d.x, j.d.y, j.d.z, tfar);
     }
-    ray_program<PASS_FWD_TRACE, BF16, SEM, Q, true>(g, a, j, smem[warp], lane);
+    ray_program<PASS_FWD_TRACE, BF16, NSC, Q, true>(g, a, j, smem[warp], lane);
 }
 
-template <bool BF16, bool SEM>
+template <bool BF16, int NSC>
 int launch_view(const GridDev& gd, int H, int W, const Cam6& cam, float tn, float tf, float* rays_out,
                 const PassArgs& a, int Q, cudaStream_t s) {
     const unsigned blocks = (unsigned)(((int64_t)H * W + kWarpsPerBlock - 1) / kWarpsPerBlock);
     switch (Q) {
-        case 2: k_trace_view<BF16, SEM, 2><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
-        case 4: k_trace_view<BF16, SEM, 4><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
-        case 6: k_trace_view<BF16, SEM, 6><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
-        default: k_trace_view<BF16, SEM, 8><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
+        case 2: k_trace_view<BF16, NSC, 2><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
+        case 4: k_trace_view<BF16, NSC, 4><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
+        case 6: k_trace_view<BF16, NSC, 6><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
+        default: k_trace_view<BF16, NSC, 8><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
     }
     SDG_LAUNCH_CHECK("trace view kernel");
     return SDG_OK;
@@ -86,11 +94,6 @@ int check_opts(const sdg_render_opts* o) {
 
 }  // namespace
 
-namespace sdg {
-template <int MODE, bool BF16, bool SEM>
-int launch_q(const GridDev& gd, const float* rays, uint32_t id0, const PassArgs& a, int Q, cudaStream_t s);
-}
-
 extern "C" int sdg_debug_trace(sdg_grid g, const float* rays, int64_t n, const sdg_render_opts* o, int32_t walk,
                                const sdg_trace_out* out) {
     if (!g || n < 0 || (n > 0 && !rays)) return fail(SDG_ERR_ARG, "sdg_debug_trace: null argument");
@@ -105,11 +108,8 @@ extern "C" int sdg_debug_trace(sdg_grid g, const float* rays, int64_t n, const s
     if (walk == SDG_WALK_PASS && (rc = walk_rays(g, rays, nullptr, n, a))) return rc;
     const GridDev gd = g->dev();
     const int Q = pick_q(o->n_samples);
-    const bool bf16 = g->desc.rgb_dtype == SDG_BF16, sem = g->desc.n_sem > 0;
-    if (!bf16 && !sem) return launch_q<PASS_FWD_TRACE, false, false>(gd, rays, o->ray_id0, a, Q, g->stream);
-    if (!bf16 && sem) return launch_q<PASS_FWD_TRACE, false, true>(gd, rays, o->ray_id0, a, Q, g->stream);
-    if (bf16 && !sem) return launch_q<PASS_FWD_TRACE, true, false>(gd, rays, o->ray_id0, a, Q, g->stream);
-    return launch_q<PASS_FWD_TRACE, true, true>(gd, rays, o->ray_id0, a, Q, g->stream);
+    return launch_layout<PASS_FWD_TRACE>(g->desc.rgb_dtype == SDG_BF16, g->desc.n_sem, gd, rays, o->ray_id0, a, Q,
+                                         g->stream);
 }
 
 extern "C" int sdg_debug_trace_view(sdg_grid g, int32_t H, int32_t W, const float K[4], const float T[12],
@@ -129,9 +129,14 @@ extern "C" int sdg_debug_trace_view(sdg_grid g, int32_t H, int32_t W, const floa
     for (int i = 0; i < 12; ++i) cam.T[i] = T[i];
     const GridDev gd = g->dev();
     const int Q = pick_q(o->n_samples);
-    const bool bf16 = g->desc.rgb_dtype == SDG_BF16, sem = g->desc.n_sem > 0;
-    if (!bf16 && !sem) return launch_view<false, false>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
-    if (!bf16 && sem) return launch_view<false, true>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
-    if (bf16 && !sem) return launch_view<true, false>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
-    return launch_view<true, true>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
+    const bool bf16 = g->desc.rgb_dtype == SDG_BF16;
+    const int cap = sem_cap(g->desc.n_sem);
+    if (cap == 0)
+        return bf16 ? launch_view<true, 0>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream)
+                    : launch_view<false, 0>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
+    if (cap == kSemCapSmall)
+        return bf16 ? launch_view<true, kSemCapSmall>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream)
+                    : launch_view<false, kSemCapSmall>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
+    return bf16 ? launch_view<true, 32>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream)
+                : launch_view<false, 32>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
 }

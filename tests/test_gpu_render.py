@@ -207,9 +207,14 @@ def test_fused_train_step_matches_oracle(sdg, room):
     assert lv.sum().item() == pytest.approx(L, rel=1e-4)
 
 
-@pytest.mark.parametrize("n_sem", [8, 20])
-def test_bf16_and_semantics_match_oracle(sdg, n_sem):
-    sc, G, O, stored, vals = tiny_room("bf16", n_sem)
+# (layout, logits per voxel): the render program is unrolled for 20 semantic channels (n_sem <= 20) or for 32
+# (n_sem 24-32); both capacities run in both colour layouts
+SEM_CASES = [("bf16", 8), ("bf16", 20), ("f32", 20), ("bf16", 32), ("f32", 24)]
+
+
+@pytest.mark.parametrize("layout,n_sem", SEM_CASES)
+def test_semantics_match_oracle(sdg, layout, n_sem):
+    sc, G, O, stored, vals = tiny_room(layout, n_sem)
     rays = _view(sc, 48, 32, seed=7)
     tr, _ = _all_rays(sdg, G, O, rays, 64, seed=4, ns=n_sem)
     n = len(rays)
@@ -222,6 +227,36 @@ def test_bf16_and_semantics_match_oracle(sdg, n_sem):
     torch.cuda.synchronize()
     got = grad_arrays(G, G.num_blocks)
     want = O.backward(rays.numpy(), 64, *(x.double().numpy() for x in seeds), seed=4, given=gpu_samples(tr))
+    for k in ("sdf", "rgb", "sem"):
+        assert_grad_close(got[k], want[k], what=k)
+
+
+@pytest.mark.parametrize("layout,n_sem", [("bf16", 20), ("f32", 20), ("bf16", 32), ("f32", 24)])
+def test_fused_semantic_train_step_matches_oracle(sdg, layout, n_sem):
+    """Fused forward + L1 colour/depth + squared-L2 logit losses + backward (the precision variant's training pass)
+    over every ray of a view, against the oracle's loss and backward over the GPU's samples."""
+    sc, G, O, _, _ = tiny_room(layout, n_sem)
+    rays = _view(sc, 48, 32, seed=9)
+    tr = sdg.trace(G, rays.cuda(), 64, seed=5)
+    check_placement(O, rays, tr, 64, seed=5)
+    gv = gpu_samples(tr)
+    ref = O.render(rays, 64, seed=5, given=gv)
+    n = rays.shape[0]
+    rng = np.random.default_rng(3)
+    t_rgb = ref["rgb"] + rng.choice([-0.05, 0.05], size=(n, 3))
+    t_depth = ref["depth"] + rng.choice([-0.1, 0.1], size=n)
+    t_sem = ref["sem"] + rng.normal(0.0, 0.5, size=(n, n_sem))
+    L, seeds = oracle.loss(ref["rgb"], ref["depth"], t_rgb, t_depth, 0.1, sem=ref["sem"], t_sem=t_sem, lam_s=0.1)
+    want = O.backward(rays, 64, seeds["rgb"], seeds["depth"], np.zeros(n), seeds["sem"], seed=5, given=gv)
+    G.zero_grad()
+    loss = torch.empty(n, device="cuda")
+    lsum = torch.empty(1, device="cuda")
+    dev = lambda x: torch.as_tensor(x, dtype=torch.float32, device="cuda")  # noqa: E731
+    sdg.train_step_rays(G, rays.cuda(), dev(t_rgb), dev(t_depth), dev(t_sem), n_samples=64, seed=5,
+                        lambda_sem=0.1, loss=loss, loss_sum=lsum)
+    torch.cuda.synchronize()
+    assert lsum.item() == pytest.approx(L, rel=1e-4)
+    got = grad_arrays(G, G.num_blocks)
     for k in ("sdf", "rgb", "sem"):
         assert_grad_close(got[k], want[k], what=k)
 
