@@ -541,6 +541,15 @@ __device__ __forceinline__ float warp_excl_suffix(float v, int lane) {
 
 __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
+// a[i] for a register array and a run-time i (selects, no local memory)
+template <int Q, class T>
+__device__ __forceinline__ T pick(const T (&a)[Q], int i) {
+    T r = a[0];
+#pragma unroll
+    for (int k = 1; k < Q; ++k) r = i == k ? a[k] : r;
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // The per-ray program
 // ---------------------------------------------------------------------------
@@ -626,14 +635,15 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     unsigned vmask = 0;
     // fractional position of sample i in its cell, recomputed from t_[i] wherever it is needed (the same
     // operations give the same bits), so no per-sample fractions stay in registers
-    auto cell_frac = [&](int i, float& fx, float& fy, float& fz) {
-        const float px = fmaf(t_[i], j.d.x, j.o.x) * g.inv_vs;
-        const float py = fmaf(t_[i], j.d.y, j.o.y) * g.inv_vs;
-        const float pz = fmaf(t_[i], j.d.z, j.o.z) * g.inv_vs;
+    auto cell_frac_t = [&](float t, float& fx, float& fy, float& fz) {
+        const float px = fmaf(t, j.d.x, j.o.x) * g.inv_vs;
+        const float py = fmaf(t, j.d.y, j.o.y) * g.inv_vs;
+        const float pz = fmaf(t, j.d.z, j.o.z) * g.inv_vs;
         fx = px - floorf(px);
         fy = py - floorf(py);
         fz = pz - floorf(pz);
     };
+    auto cell_frac = [&](int i, float& fx, float& fy, float& fz) { cell_frac_t(t_[i], fx, fy, fz); };
 
     unsigned smask = 0;  // stored mode: samples whose record is valid
     int rm = 0, r_blk = -1, r_cell = -1;  // the lane's current walk record and its fields
@@ -842,6 +852,16 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     auto run_end = [&](int i) {
         return ((vmask >> i) & 1u) && (i == Q - 1 || !((vmask >> (i + 1)) & 1u) || !same_cell(i, i + 1));
     };
+    // The semantic phases run their sample loop rolled (one copy of the channel loops instead of Q), taking the
+    // lane's sample i out of the per-sample registers with pick() and its run boundaries from these masks.
+    unsigned rs_mask = 0, re_mask = 0;
+    if constexpr (SEM) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            rs_mask |= (run_start(i) ? 1u : 0u) << i;
+            re_mask |= (run_end(i) ? 1u : 0u) << i;
+        }
+    }
 
     // semantic logits: per run, corner weights W_e = sum_i w_i r_e(f_i)
     float sem_acc[SEMCAP > 0 ? SEMCAP : 1];
@@ -853,23 +873,25 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
         if (any) {
             float W[8];
             int addr[8];
-#pragma unroll
+#pragma unroll 1
             for (int i = 0; i < Q; ++i) {
                 const bool v = (vmask >> i) & 1u;
-                if (run_start(i)) {
+                if ((rs_mask >> i) & 1u) {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) W[e] = 0.f;
-                    corner_addresses(g, ba_[i] >> 9, ba_[i] & 511, addr);
+                    const int bai = pick(ba_, i);
+                    corner_addresses(g, bai >> 9, bai & 511, addr);
                 }
                 if (v) {
                     float r[8];
                     float fx, fy, fz;
-                    cell_frac(i, fx, fy, fz);
+                    cell_frac_t(pick(t_, i), fx, fy, fz);
                     trilinear_weights(fx, fy, fz, r);
+                    const float wi = pick(w_, i);
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) W[e] = fmaf(w_[i], r[e], W[e]);
+                    for (int e = 0; e < 8; ++e) W[e] = fmaf(wi, r[e], W[e]);
                 }
-                if (run_end(i)) {
+                if ((re_mask >> i) & 1u) {
 #pragma unroll
                     for (int c4 = 0; c4 < SEMCAP / 4; ++c4) {
                         if (4 * c4 < ns) {
@@ -1008,10 +1030,11 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             // per run: dot_e = g_sem . theta_s(corner e), then v_i += sum_e r_e(f_i) dot_e
             int addr[8];
             float dot[8];
-#pragma unroll
+#pragma unroll 1
             for (int i = 0; i < Q; ++i) {
-                if (run_start(i)) {
-                    corner_addresses(g, ba_[i] >> 9, ba_[i] & 511, addr);
+                if ((rs_mask >> i) & 1u) {
+                    const int bai = pick(ba_, i);
+                    corner_addresses(g, bai >> 9, bai & 511, addr);
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         dot[e] = 0.f;
@@ -1028,12 +1051,14 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 if ((vmask >> i) & 1u) {
                     float r[8];
                     float fx, fy, fz;
-                    cell_frac(i, fx, fy, fz);
+                    cell_frac_t(pick(t_, i), fx, fy, fz);
                     trilinear_weights(fx, fy, fz, r);
                     float acc = 0.f;
 #pragma unroll
                     for (int e = 0; e < 8; ++e) acc = fmaf(r[e], dot[e], acc);
-                    v_[i] += acc;
+#pragma unroll
+                    for (int k = 0; k < Q; ++k)
+                        if (k == i) v_[k] += acc;
                 }
             }
         }
@@ -1065,34 +1090,36 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     {
         int addr[8];
         float aS[8], aW[8];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
+        // sample i of the lane (a compile-time constant in the unrolled loop, where pick() is a[i])
+        auto scatter_sample = [&](int i) {
             const bool v = (vmask >> i) & 1u;
-            if (run_start(i)) {
+            if (SEM ? ((rs_mask >> i) & 1u) != 0 : run_start(i)) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) aS[e] = aW[e] = 0.f;
-                corner_addresses(g, ba_[i] >> 9, ba_[i] & 511, addr);
+                const int bai = pick(ba_, i);
+                corner_addresses(g, bai >> 9, bai & 511, addr);
             }
             if (v) {
                 float r[8];
                 float fx, fy, fz;
-                cell_frac(i, fx, fy, fz);
+                cell_frac_t(pick(t_, i), fx, fy, fz);
                 trilinear_weights(fx, fy, fz, r);
+                const float ddi = pick(dd_, i), wi = pick(w_, i);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    aS[e] = fmaf(r[e], dd_[i], aS[e]);
-                    aW[e] = fmaf(r[e], w_[i], aW[e]);
+                    aS[e] = fmaf(r[e], ddi, aS[e]);
+                    aW[e] = fmaf(r[e], wi, aW[e]);
                 }
                 if constexpr (kNrm) {
                     // the rendered normal's grad f part: w_i g_N . grad_x r_e(x_i) onto each corner's SDF
-                    const float sc = w_[i] * g.inv_vs;
+                    const float sc = wi * g.inv_vs;
                     float q[8];
                     dot_weight_gradients(fx, fy, fz, sc * gNx, sc * gNy, sc * gNz, q);
 #pragma unroll
                     for (int e = 0; e < 8; ++e) aS[e] += q[e];
                 }
             }
-            if (run_end(i)) {
+            if (SEM ? ((re_mask >> i) & 1u) != 0 : run_end(i)) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     if constexpr (!BF16) {
@@ -1111,6 +1138,13 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                     }
                 }
             }
+        };
+        if constexpr (SEM) {
+#pragma unroll 1
+            for (int i = 0; i < Q; ++i) scatter_sample(i);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) scatter_sample(i);
         }
     }
 }
@@ -1119,8 +1153,8 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 // Launch entry of the render kernels (defined in render_kernels.cuh, instantiated in the render_inst_*.cu files)
 // ---------------------------------------------------------------------------
 // Semantic channel capacities the kernels are instantiated for: a grid with at most kSemCapSmall logits per voxel
-// runs the program unrolled for kSemCapSmall channels (less code and no spills: 8.4 -> 6.6 ms per 2^18-ray
-// training pass with 20 logits), one with more (24-32) the program unrolled for 32.
+// runs the program unrolled for kSemCapSmall channels (less code than for 32, and no spills at 128 registers),
+// one with more (24-32) the program unrolled for 32.
 constexpr int kSemCapSmall = 20;
 inline int sem_cap(int n_sem) { return n_sem == 0 ? 0 : n_sem <= kSemCapSmall ? kSemCapSmall : 32; }
 
