@@ -618,16 +618,23 @@ def _timed_steps(torch, step, batches, K, W_):
 
 
 def _phase_times(torch, sdg, G, batches, K, train):
-    """Median CUDA-event times of the training pass and of the optimiser step."""
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    """Median CUDA-event times of the training pass, of its render kernels (events the library records around
+    them) and of the optimiser step."""
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    for e in ev:  # the library records the pass events; they exist once recorded here
+        e[3].record()
+        e[4].record()
     for i in range(K):
+        G.set_pass_events(ev[i][3], ev[i][4])
         ev[i][0].record()
         train(batches[i % len(batches)], 2000 + i)
         ev[i][1].record()
         G.adam_step(lr=1e-3)
         ev[i][2].record()
+    G.set_pass_events()
     torch.cuda.synchronize()
     return {"train_kernel_ms": round(float(np.median([e[0].elapsed_time(e[1]) for e in ev])), 4),
+            "render_kernels_ms": round(float(np.median([e[3].elapsed_time(e[4]) for e in ev])), 4),
             "adam_ms": round(float(np.median([e[1].elapsed_time(e[2]) for e in ev])), 4)}
 
 
@@ -746,6 +753,7 @@ def measure_precision(args, compact=False):
             "sem": vals["sem"].cpu().numpy()}
     del vals
     got = {k: out[k].double().cpu().numpy() for k in ("rgb", "depth", "opac", "sem")}
+    cnt_rays = batches[0]["rays"][np.linspace(0, args.rays - 1, 1024).astype(np.int64)].cpu().numpy()
     ggot = {"sdf": G.channel(A.GROUP_SDF, A.KIND_GRAD)[:nb, :, 0].double().cpu().numpy(),
             "rgb": G.channel(A.GROUP_RGB, A.KIND_GRAD)[:nb, :, 0:3].double().cpu().numpy(),
             "sem": G.channel(A.GROUP_SEM, A.KIND_GRAD)[:nb].double().cpu().numpy()}
@@ -755,6 +763,8 @@ def measure_precision(args, compact=False):
     table = {}
     for name, src in (("vs_fp64_unrounded", full), ("vs_fp64_same_bf16_values", stored)):
         O = oracle.Grid(VS, BETA, 20).set(keys, src["sdf"], src["rgb"], src["sem"])
+        if src is stored:  # distinct voxels and blocks per ray, for the roofline's algorithmic bytes
+            vx, bl = O.count_touched(cnt_rays, N_SAMPLES, seed=0)
         ref = O.render(rays_np, N_SAMPLES, seed=0, given=given)
         row = {k: float(np.abs(got[k] - ref[k]).max()) for k in ("rgb", "depth", "opac", "sem")}
         gref = O.backward(rays_np, N_SAMPLES, sd[0], sd[1], sd[2], sd[3], seed=0, given=given)
@@ -777,16 +787,26 @@ def measure_precision(args, compact=False):
     del batches
     torch.cuda.empty_cache()
     rps = args.rays / (ms / 1e3)
+    # per distinct voxel: 52 B read (SDF 4, colour 8, 20 BF16 logits 40) and 200 B of gradient read-modify-write
+    # (SDF 4, colour 16, logits 80, each read and written); per block 40 B; per ray 32 B, targets 96 B, loss 4 B
+    bpr = float((vx * 252.0 + bl * 40.0 + 32 + 96 + 4).mean())
+    peak, peak_src = _peak()
+    kern_gbs = bpr * args.rays / (phases["render_kernels_ms"] / 1e3) / 1e9
+    roof = {"kernel": "k_render_train (BF16 colour, 20 logits)", "bound": "hbm", "achieved": round(kern_gbs, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(kern_gbs / peak, 4), "traffic": None,
+            "peak_source": peak_src, "algorithmic_bytes_per_launch": round(bpr * args.rays),
+            "bytes_per_ray": round(bpr, 1), "distinct_voxels": round(float(vx.mean()), 1),
+            "distinct_blocks": round(float(bl.mean()), 2), "launch_ms_median": phases["render_kernels_ms"]}
     if compact:
         return {"workload": "room step, BF16 colour + 20 BF16 logits (FP32 SDF, transmittance, accumulation)",
-                "rays_per_s": round(rps, 1), "ms_per_step": round(ms, 4), "phases": phases,
+                "rays_per_s": round(rps, 1), "ms_per_step": round(ms, 4), "phases": phases, "roofline": roof,
                 "errors_on_4096_rays_all_compared": table, "steps": args.steps, "warmup": args.warmup}
     return _line(rps, "rays/s", args.steps, args.warmup, ms,
                  {"workload": "precision variant of the room step: BF16 colour + 20 BF16 semantic logits, FP32 "
                               "SDF / transmittance / accumulation", "rays_per_step": args.rays,
                   "samples_per_ray": N_SAMPLES, "n_blocks": nb},
                  dtype="f32+bf16", samples_per_s=round(args.rays * N_SAMPLES / (ms / 1e3), 1), phases=phases,
-                 errors_on_4096_rays_all_compared=table,
+                 roofline=roof, errors_on_4096_rays_all_compared=table,
                  gpu_launches=(_train_launches(args, args.rays) + 1) * args.steps)
 
 
