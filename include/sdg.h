@@ -280,8 +280,9 @@ int sdg_render_backward(sdg_ctx ctx, const float* g_rgb_dev, const float* g_dept
  *   rgb, depth, opac forward outputs, as sdg_render_forward.
  * Samples of a ray with S = 0 read t = 0, cell = 0, block = -1, valid = 0.
  * walk: SDG_WALK_PASS (the traversal pass used by sdg_render_forward,
- * sdg_render_backward and the training passes) or SDG_WALK_IN_WARP (the
- * in-warp traversal used by the serving loop and the allocation-free pass).
+ * sdg_render_backward, the training passes and the serving loop) or
+ * SDG_WALK_IN_WARP (the in-warp traversal used by the allocation-free pass and
+ * for the rays that cross more than SDG_TRACE_CELLS allocated cells).
  * Asynchronous on the grid's stream.  Errors: SDG_ERR_ARG (null or
  * misaligned buffer, bad walk), SDG_ERR_OOM, SDG_ERR_CUDA. */
 #define SDG_TRACE_CELLS 32
@@ -303,9 +304,10 @@ int sdg_debug_trace(sdg_grid g, const float* rays_dev, int64_t n, const sdg_rend
 /* Same export for the H x W pinhole view that the serving loop renders for a
  * request (K = {fx, fy, cx, cy}, T row-major 3x4 camera-to-world, host
  * arrays; pixel (u, v) is ray v * W + u, its direction normalised): the rays
- * are formed by the serving kernel's own code and walked in-warp as it walks
- * them, so the outputs equal the served request's bit for bit.  rays_out
- * [H*W][8] (device) receives the rays {o, tnear, d, tfar}. */
+ * are formed by the serving kernels' own code (ray id = pixel index; the
+ * options' ray_id0 is not used) and walked by the traversal pass as the
+ * serving loop walks them, so the outputs equal the served request's bit for
+ * bit.  rays_out [H*W][8] (device) receives the rays {o, tnear, d, tfar}. */
 int sdg_debug_trace_view(sdg_grid g, int32_t H, int32_t W, const float K[4], const float T[12], float tnear,
                          float tfar, const sdg_render_opts* opts, float* rays_out_dev, const sdg_trace_out* out);
 
@@ -601,7 +603,11 @@ int sdg_fuse_finalize(sdg_grid g);
  * batches that mix chunks of different requests, resolutions and scenes on
  * several streams, so batches overlap on the device.  A request's result
  * does not depend on what it was batched with: every ray is computed by the
- * same per-ray code, from its own pixel index. */
+ * same per-ray code, from its own pixel index (a traversal pass over the
+ * batch, then the records kernel; rays crossing more than SDG_TRACE_CELLS
+ * allocated cells walked in-warp).  Besides the output pool the server holds
+ * traversal records for max_batch_rays rays per stream: 8 + 20 *
+ * SDG_TRACE_CELLS + 4 bytes a ray (about 170 MB per stream at 2^18 rays). */
 typedef struct {
     int64_t hbm_budget_bytes; /* device memory for in-flight outputs (the server allocates it once) */
     int32_t max_slots;        /* requests in flight at once, >= 1 */

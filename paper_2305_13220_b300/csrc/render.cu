@@ -92,29 +92,7 @@ __global__ void __launch_bounds__(256) k_walk(GridDev g, const float* __restrict
     if (!sdg_in_range(g.status, r, n, SDG_CHECK_RAY)) r = 0;  // checked build: a bad order row reads ray 0
     const float4 r0 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r);
     const float4 r1 = __ldg(reinterpret_cast<const float4*>(rays) + 2 * r + 1);
-    const float3 o = make_float3(r0.x, r0.y, r0.z), d = make_float3(r1.x, r1.y, r1.z);
-    float t0 = r0.w, t1 = r1.w;
-    int cnt = 0;
-    float S = 0.f;
-    if (clip_to_grid(g, o, d, t0, t1)) {
-        const float3 invd = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-        float* s0 = w.s0 + slot * kWalkCap;
-        int4* rec = w.rec + slot * kWalkCap;
-        walk_cells_pipelined<8>(g, o, d, invd, t0, t1, [&](float x0, float x1, int cell, int blk) {
-            if (cnt == kWalkCap) {
-                cnt = -1;  // more cells than records: the render warp walks this ray itself
-                return false;
-            }
-            const float len = x1 - x0;
-            s0[cnt] = S;
-            rec[cnt] = make_int4(__float_as_int(x0), __float_as_int(len), blk, cell);
-            S += len;
-            ++cnt;
-            return true;
-        });
-    }
-    w.hdr[slot] = make_int2(cnt, __float_as_int(S));
-    if (cnt < 0) w.over[atomicAdd(w.n_over, 1)] = (int)slot;
+    walk_ray_records(g, make_float3(r0.x, r0.y, r0.z), make_float3(r1.x, r1.y, r1.z), r0.w, r1.w, w, slot);
 }
 
 }  // namespace

@@ -321,6 +321,34 @@ __device__ __forceinline__ void walk_cells_pipelined(const GridDev& g, const flo
     }
 }
 
+// The traversal pass for one ray: clips (o, d) over [t0, t1] to the grid and walks it, writing the allocated cells
+// it crosses as records of slot `slot` of w with their sequential skip-space offsets, and the slot's header
+// {record count (-1: more than kWalkCap, the slot appended to the overflow list), bits of S}.
+__device__ __forceinline__ void walk_ray_records(const GridDev& g, const float3& o, const float3& d, float t0,
+                                                 float t1, const WalkBufs& w, int64_t slot) {
+    int cnt = 0;
+    float S = 0.f;
+    if (clip_to_grid(g, o, d, t0, t1)) {
+        const float3 invd = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+        float* s0 = w.s0 + slot * kWalkCap;
+        int4* rec = w.rec + slot * kWalkCap;
+        walk_cells_pipelined<8>(g, o, d, invd, t0, t1, [&](float x0, float x1, int cell, int blk) {
+            if (cnt == kWalkCap) {
+                cnt = -1;  // more cells than records: the render warp walks this ray itself
+                return false;
+            }
+            const float len = x1 - x0;
+            s0[cnt] = S;
+            rec[cnt] = make_int4(__float_as_int(x0), __float_as_int(len), blk, cell);
+            S += len;
+            ++cnt;
+            return true;
+        });
+    }
+    w.hdr[slot] = make_int2(cnt, __float_as_int(S));
+    if (cnt < 0) w.over[atomicAdd(w.n_over, 1)] = (int)slot;
+}
+
 struct Pieces {
     float t0, dt, S;
     float3 invd;

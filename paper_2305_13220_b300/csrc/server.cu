@@ -13,9 +13,12 @@
 //     new requests join the following batch as soon as they are admitted,
 //   * completes a request when the events of all batches holding its chunks
 //     have fired.
-// Each ray is generated in the kernel from its request's camera and pixel
-// index and rendered by the same per-ray program as sdg_render_forward, so a
-// request's result does not depend on its batch mates.
+// Each ray is generated in the kernels from its request's camera and pixel
+// index: a traversal pass (one thread per ray) writes the allocated cells it
+// crosses, then the records kernel renders it with the same per-ray program
+// as sdg_render_forward (a ray crossing more than kWalkCap cells is walked
+// in-warp by a third kernel over the overflow list), so a request's result
+// does not depend on its batch mates.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -44,35 +47,61 @@ struct ChunkDesc {
     int32_t strat;
 };
 
-// 3 CTAs per SM at 4 samples per lane (80 registers), 2 above
-template <bool BF16, int Q>
+// The ray of batch slot `slot` (chunk slot / chunk_rays, its pixel slot % chunk_rays); false past the chunk's end.
+__device__ __forceinline__ bool slot_ray(const ChunkDesc* chunks, int chunk_rays, int64_t slot, const ChunkDesc*& ch,
+                                         int64_t& pix, float3& o, float3& d) {
+    const int local = (int)(slot % chunk_rays);
+    ch = chunks + slot / chunk_rays;
+    if (local >= ch->npix) return false;
+    pix = ch->pix0 + local;
+    pinhole_ray(ch->K, ch->T, (int)(pix % ch->W), (int)(pix / ch->W), o, d);
+    return true;
+}
+
+// Traversal pass of a batch: one thread per ray slot.
+__global__ void __launch_bounds__(256) k_serve_walk(const GridDev* __restrict__ scenes,
+                                                     const ChunkDesc* __restrict__ chunks, int chunk_rays,
+                                                     int64_t nslots, WalkBufs w) {
+    const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= nslots) return;
+    const ChunkDesc* ch;
+    int64_t pix;
+    float3 o, d;
+    if (!slot_ray(chunks, chunk_rays, slot, ch, pix, o, d)) return;  // never rendered: no header needed
+    walk_ray_records(scenes[ch->scene], o, d, ch->tnear, ch->tfar, w, slot);
+}
+
+// One warp per ray.  OVER false: every slot of the batch, cells from the traversal pass's records (a slot without
+// records is left to the overflow kernel); OVER true: the slots of the overflow list, walked in-warp (a grid as
+// large as the batch's, the warps past the list's end exiting at once).  3 CTAs per SM at 4 samples per lane
+// (80 registers), 2 above.
+template <bool BF16, int Q, bool OVER>
 __global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
-    k_serve(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks, int chunk_rays) {
-    __shared__ WarpSmem smem[kWarpsPerBlock];
+    k_serve(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks, int chunk_rays, WalkBufs wb) {
+    __shared__ WarpSmem smem[OVER ? kWarpsPerBlock : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-    const int c = (int)(w / chunk_rays);
-    const int local = (int)(w % chunk_rays);
-    const ChunkDesc& ch = chunks[c];
-    if (local >= ch.npix) return;  // warp-uniform
-    const int64_t pix = ch.pix0 + local;
-    const int u = (int)(pix % ch.W), v = (int)(pix / ch.W);
+    int64_t slot = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if constexpr (OVER) {
+        if (slot >= (int64_t)__ldg(wb.n_over)) return;  // warp-uniform
+        slot = __ldg(wb.over + slot);
+    }
+    const ChunkDesc* ch;
     RayJob j;
-    pinhole_ray(ch.K, ch.T, u, v, j.o, j.d);
-    j.tn = ch.tnear;
-    j.tf = ch.tfar;
-    j.ray_id = (uint32_t)pix;
-    j.idx = pix;
-    j.slot = 0;  // no walk records: the warp walks its ray
+    if (!slot_ray(chunks, chunk_rays, slot, ch, j.idx, j.o, j.d)) return;  // warp-uniform
+    j.tn = ch->tnear;
+    j.tf = ch->tfar;
+    j.ray_id = (uint32_t)j.idx;
+    j.slot = slot;
     PassArgs a{};
-    a.N = ch.N;
-    a.seed = ch.seed;
-    a.strat = ch.strat;
+    a.N = ch->N;
+    a.seed = ch->seed;
+    a.strat = ch->strat;
     a.n = 0;
-    a.out_rgb = ch.rgb;
-    a.out_depth = ch.depth;
-    a.out_opac = ch.opac;
-    ray_program<PASS_FWD, BF16, 0, Q, true>(scenes[ch.scene], a, j, smem[warp], lane);
+    a.out_rgb = ch->rgb;
+    a.out_depth = ch->depth;
+    a.out_opac = ch->opac;
+    a.walk = wb;
+    ray_program<PASS_FWD, BF16, 0, Q, OVER>(scenes[ch->scene], a, j, smem[OVER ? warp : 0], lane);
 }
 
 double now_ms() {
@@ -138,6 +167,7 @@ struct Req {
 
 struct Batch {
     cudaStream_t stream;
+    int stream_index = 0;
     cudaEvent_t ev;
     ChunkDesc* h_chunks = nullptr;
     ChunkDesc* d_chunks = nullptr;
@@ -159,6 +189,7 @@ struct sdg_server_s {
     char* pool_mem = nullptr;
     Pool pool;
     std::vector<cudaStream_t> streams;
+    std::vector<WalkBufs> walk;  // traversal records of the batch running on each stream (max_batch_rays slots)
     std::vector<Batch> batches;
     std::deque<Batch*> inflight;  // launch order
     int next_stream = 0;
@@ -289,14 +320,25 @@ struct sdg_server_s {
                 if (reqs[tk].next_pix < reqs[tk].npix) keep.push_back(tk);
             active.swap(keep);
             for (size_t s = 0; s < scenes.size(); ++s) b->h_scenes[s] = scenes[s]->dev();
+            b->stream_index = next_stream;
             b->stream = streams[next_stream];
             next_stream = (next_stream + 1) % (int)streams.size();
             cudaMemcpyAsync(b->d_scenes, b->h_scenes, sizeof(GridDev) * scenes.size(), cudaMemcpyHostToDevice,
                             b->stream);
             cudaMemcpyAsync(b->d_chunks, b->h_chunks, sizeof(ChunkDesc) * nch, cudaMemcpyHostToDevice, b->stream);
-            const unsigned blocks = (unsigned)(((int64_t)nch * o.chunk_rays + kWarpsPerBlock - 1) / kWarpsPerBlock);
+            // batches on one stream run in order, so the stream's records serve each in turn
+            const WalkBufs& wb = walk[b->stream_index];
+            const int64_t nslots = (int64_t)nch * o.chunk_rays;
+            const unsigned blocks = (unsigned)((nslots + kWarpsPerBlock - 1) / kWarpsPerBlock);
             const int Q = pick_q(maxN);
-#define SDG_SERVE(BF, QQ) k_serve<BF, QQ><<<blocks, 256, 0, b->stream>>>(b->d_scenes, b->d_chunks, o.chunk_rays)
+            cudaMemsetAsync(wb.n_over, 0, sizeof(int), b->stream);
+            k_serve_walk<<<(unsigned)((nslots + 255) / 256), 256, 0, b->stream>>>(b->d_scenes, b->d_chunks,
+                                                                                   o.chunk_rays, nslots, wb);
+#define SDG_SERVE(BF, QQ)                                                                                      \
+    do {                                                                                                       \
+        k_serve<BF, QQ, false><<<blocks, 256, 0, b->stream>>>(b->d_scenes, b->d_chunks, o.chunk_rays, wb);      \
+        k_serve<BF, QQ, true><<<blocks, 256, 0, b->stream>>>(b->d_scenes, b->d_chunks, o.chunk_rays, wb);       \
+    } while (0)
             if (bf16) {
                 if (Q == 2) SDG_SERVE(true, 2); else if (Q == 4) SDG_SERVE(true, 4);
                 else if (Q == 6) SDG_SERVE(true, 6); else SDG_SERVE(true, 8);
@@ -335,6 +377,15 @@ struct sdg_server_s {
     }
 };
 
+static void free_walk(sdg_server s) {
+    for (WalkBufs& w : s->walk) {
+        void* ptrs[] = {w.hdr, w.s0, w.rec, w.over};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+    }
+    s->walk.clear();
+}
+
 extern "C" int sdg_server_create(const sdg_server_opts* o, sdg_server* out) {
     if (!o || !out) return fail(SDG_ERR_ARG, "sdg_server_create: null argument");
     *out = nullptr;
@@ -356,6 +407,7 @@ extern "C" int sdg_server_create(const sdg_server_opts* o, sdg_server* out) {
             if (b.d_scenes) cudaFree(b.d_scenes);
         }
         for (auto st : s->streams) cudaStreamDestroy(st);
+        free_walk(s);
         if (s->pool_mem) cudaFree(s->pool_mem);
         delete s;
         return fail(rc, m);
@@ -368,6 +420,18 @@ extern "C" int sdg_server_create(const sdg_server_opts* o, sdg_server* out) {
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "server stream"));
         s->streams.push_back(st);
+        // traversal records for max_batch_rays slots: 8 + kWalkCap * 20 bytes a slot, and the overflow list
+        const int64_t R = o->max_batch_rays;
+        WalkBufs w{};
+        if ((e = cudaMalloc((void**)&w.hdr, sizeof(int2) * R)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&w.s0, sizeof(float) * kWalkCap * R)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&w.rec, sizeof(int4) * kWalkCap * R)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&w.over, sizeof(int) * (R + 1))) != cudaSuccess) {
+            s->walk.push_back(w);
+            return cleanup(cuda_fail(e, "server traversal records"));
+        }
+        w.n_over = w.over + R;
+        s->walk.push_back(w);
     }
     const int max_chunks = o->max_batch_rays / o->chunk_rays;
     s->batches.resize(2 * o->n_streams);
@@ -539,6 +603,7 @@ extern "C" int sdg_server_destroy(sdg_server s) {
         if (b.d_scenes) cudaFree(b.d_scenes);
     }
     for (auto st : s->streams) cudaStreamDestroy(st);
+    free_walk(s);
     if (s->pool_mem) cudaFree(s->pool_mem);
     for (sdg_grid g : s->scenes) {
         std::lock_guard<std::mutex> gl(g->mu);

@@ -16,43 +16,15 @@ using namespace sdg;
 
 namespace {
 
-// One warp per pixel of an H x W pinhole view, rays formed by pinhole_ray as the serving kernel forms them and
-// walked in-warp as it walks them.
-template <bool BF16, int NSC, int Q>
-__global__ void __launch_bounds__(256, (render_min_blocks<PASS_FWD_TRACE, NSC, Q>()))
-    k_trace_view(GridDev g, int H, int W, Cam6 cam, float tnear, float tfar, float* rays_out, PassArgs a) {
-    __shared__ WarpSmem smem[kWarpsPerBlock];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t pix = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-    if (pix >= (int64_t)H * W) return;  // warp-uniform
-    const int u = (int)(pix % W), v = (int)(pix / W);
-    RayJob j;
-    pinhole_ray(cam.K, cam.T, u, v, j.o, j.d);
-    j.tn = tnear;
-    j.tf = tfar;
-    j.ray_id = (uint32_t)pix;
-    j.idx = pix;
-    j.slot = 0;
-    if (lane == 0) {
-        float4* r = reinterpret_cast<float4*>(rays_out) + 2 * pix;
-        r[0] = make_float4(j.o.x, j.o.y, j.o.z, tnear);
-        r[1] = make_float4(j.d.x, j.d.y, j.d.z, tfar);
-    }
-    ray_program<PASS_FWD_TRACE, BF16, NSC, Q, true>(g, a, j, smem[warp], lane);
-}
-
-template <bool BF16, int NSC>
-int launch_view(const GridDev& gd, int H, int W, const Cam6& cam, float tn, float tf, float* rays_out,
-                const PassArgs& a, int Q, cudaStream_t s) {
-    const unsigned blocks = (unsigned)(((int64_t)H * W + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    switch (Q) {
-        case 2: k_trace_view<BF16, NSC, 2><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
-        case 4: k_trace_view<BF16, NSC, 4><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
-        case 6: k_trace_view<BF16, NSC, 6><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
-        default: k_trace_view<BF16, NSC, 8><<<blocks, 256, 0, s>>>(gd, H, W, cam, tn, tf, rays_out, a); break;
-    }
-    SDG_LAUNCH_CHECK("trace view kernel");
-    return SDG_OK;
+// The rays of an H x W pinhole view, one thread per pixel, formed by pinhole_ray as the serving kernels form them.
+__global__ void __launch_bounds__(256) k_view_rays(int H, int W, Cam6 cam, float tnear, float tfar, float* rays_out) {
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= (int64_t)H * W) return;
+    float3 o, d;
+    pinhole_ray(cam.K, cam.T, (int)(pix % W), (int)(pix / W), o, d);
+    float4* r = reinterpret_cast<float4*>(rays_out) + 2 * pix;
+    r[0] = make_float4(o.x, o.y, o.z, tnear);
+    r[1] = make_float4(d.x, d.y, d.z, tfar);
 }
 
 int pick_q(int N) { return N <= 64 ? 2 : N <= 128 ? 4 : N <= 192 ? 6 : 8; }
@@ -127,16 +99,11 @@ extern "C" int sdg_debug_trace_view(sdg_grid g, int32_t H, int32_t W, const floa
     Cam6 cam;
     for (int i = 0; i < 4; ++i) cam.K[i] = K[i];
     for (int i = 0; i < 12; ++i) cam.T[i] = T[i];
-    const GridDev gd = g->dev();
-    const int Q = pick_q(o->n_samples);
-    const bool bf16 = g->desc.rgb_dtype == SDG_BF16;
-    const int cap = sem_cap(g->desc.n_sem);
-    if (cap == 0)
-        return bf16 ? launch_view<true, 0>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream)
-                    : launch_view<false, 0>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
-    if (cap == kSemCapSmall)
-        return bf16 ? launch_view<true, kSemCapSmall>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream)
-                    : launch_view<false, kSemCapSmall>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
-    return bf16 ? launch_view<true, 32>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream)
-                : launch_view<false, 32>(gd, H, W, cam, tnear, tfar, rays_out, a, Q, g->stream);
+    k_view_rays<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(H, W, cam, tnear, tfar, rays_out);
+    SDG_LAUNCH_CHECK("view rays");
+    // then as the serving loop renders them: the traversal pass, the records kernel and, for rays crossing more
+    // than kWalkCap allocated cells, the in-warp kernel; the jitter's ray id is the pixel index
+    if ((rc = walk_rays(g, rays_out, nullptr, n, a))) return rc;
+    return launch_layout<PASS_FWD_TRACE>(g->desc.rgb_dtype == SDG_BF16, g->desc.n_sem, g->dev(), rays_out, 0u, a,
+                                         pick_q(o->n_samples), g->stream);
 }
