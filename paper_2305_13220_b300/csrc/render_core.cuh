@@ -452,8 +452,7 @@ __device__ __forceinline__ float locate(const GridDev& g, const RayJob& j, const
 // axis lives in the neighbour block on that side, read from the block's neighbour row
 // {self, +x, +y, +xy | +z, +xz, +yz, +xyz}.  Writes their voxel addresses; false if a corner's block is absent.
 __device__ __forceinline__ bool corner_addresses(const GridDev& g, int blk, int lcell, int addr[8]) {
-    const int lx = lcell & 7, ly = (lcell >> 3) & 7, lz = lcell >> 6;
-    const bool ox = lx == 7, oy = ly == 7, oz = lz == 7;
+    const bool ox = (lcell & 7) == 7, oy = (lcell & 56) == 56, oz = lcell >= 448;
     if (!sdg_in_range(g.status, blk, g.n_blocks, SDG_CHECK_BLOCK)) return false;
     const int4 n0 = __ldg(g.nbr + 2 * blk), n1 = __ldg(g.nbr + 2 * blk + 1);
     const int b1 = ox ? n0.y : blk;
@@ -463,18 +462,18 @@ __device__ __forceinline__ bool corner_addresses(const GridDev& g, int blk, int 
     const int b5 = ox ? (oz ? n1.y : n0.y) : b4;
     const int b6 = oy ? (oz ? n1.z : n0.z) : b4;
     const int b7 = ox ? (oy ? (oz ? n1.w : n0.w) : (oz ? n1.y : n0.y)) : b6;
-    const int x0 = lx, x1 = (lx + 1) & 7;
-    const int y0 = ly << 3, y1 = ((ly + 1) & 7) << 3;
-    const int z0 = lz << 6, z1 = ((lz + 1) & 7) << 6;
-    const int q00 = x0 + y0, q10 = x1 + y0, q01 = x0 + y1, q11 = x1 + y1;
-    addr[0] = blk * 512 + q00 + z0;
-    addr[1] = b1 * 512 + q10 + z0;
-    addr[2] = b2 * 512 + q01 + z0;
-    addr[3] = b3 * 512 + q11 + z0;
-    addr[4] = b4 * 512 + q00 + z1;
-    addr[5] = b5 * 512 + q10 + z1;
-    addr[6] = b6 * 512 + q01 + z1;
-    addr[7] = b7 * 512 + q11 + z1;
+    // local index of the +1 corner on each axis: one step (+1, +8, +64), or, past the block's last voxel, the
+    // first voxel of the neighbour block on that side (-7, -56, -448)
+    const int dx = ox ? -7 : 1, dy = oy ? -56 : 8, dz = oz ? -448 : 64;
+    const int l1 = lcell + dx, l2 = lcell + dy, l3 = l1 + dy;
+    addr[0] = blk * 512 + lcell;
+    addr[1] = b1 * 512 + l1;
+    addr[2] = b2 * 512 + l2;
+    addr[3] = b3 * 512 + l3;
+    addr[4] = b4 * 512 + (lcell + dz);
+    addr[5] = b5 * 512 + (l1 + dz);
+    addr[6] = b6 * 512 + (l2 + dz);
+    addr[7] = b7 * 512 + (l3 + dz);
     const bool all = (b1 | b2 | b3 | b4 | b5 | b6 | b7) >= 0;
 #ifdef SDG_CHECKED
     if (all)  // every address the fetch and the scatter will use
