@@ -137,3 +137,35 @@ def test_served_grid_structure_is_fixed(sdg):
     assert e.value.code == sdg._abi.ERR_ARG
     srv.close()
     assert G.activate_keys(far) == 1  # structure free again once the server is gone
+
+
+def test_served_rays_beyond_the_record_capacity(sdg):
+    """Rays that cross more allocated block cells than a traversal record holds (32) are rendered by the serving
+    loop's in-warp kernel over the overflow list, as sdg_debug_trace_view renders them: a view down a slab of
+    40 x 3 x 3 allocated blocks equals its trace bit for bit, and the oracle over the trace's samples on every
+    pixel."""
+    sc = synth.scene_room(0, size=(13.0, 2.0, 2.0), n_objects=0)
+    keys = np.array([(x, y, z) for x in range(40) for y in range(3) for z in range(3)], np.int32)
+    G, O, stored, vals = make_pair(sc, keys, 0.04, 3, 0.02, "bf16")
+    # camera at x = 0.1 looking down +x (its z axis), centred in the slab's cross-section
+    T = np.array([[0.0, 0.0, 1.0, 0.1], [1.0, 0.0, 0.0, 0.48], [0.0, 1.0, 0.0, 0.48]])
+    H = W = 24
+    K = synth.intrinsics(W, H, fov_deg=2.0)  # every ray stays inside the slab to its far end
+    srv = sdg.Server(hbm_budget_bytes=16 << 20, max_slots=2, n_streams=1, chunk_rays=256, max_batch_rays=1024)
+    sid = srv.add_scene(G)
+    t = srv.submit(sid, H, W, K, T, n_samples=64, seed=5)
+    r = srv.wait(t, 60000)
+    rgb, depth, opac = srv.result_tensors(r)
+    tr = sdg.trace_view(G, H, W, K, T, 64, seed=5)
+    assert torch.equal(tr["rgb"].reshape(rgb.shape), rgb) and torch.equal(tr["depth"].reshape(depth.shape), depth)
+    assert torch.equal(tr["opac"].reshape(opac.shape), opac)
+    n_over = int((tr["n_cells"] < 0).sum())
+    assert n_over >= H * W // 4, n_over  # the overflow kernel rendered a good part of the view
+    rays = tr["rays"].cpu().numpy()
+    check_placement(O, rays, tr, 64, seed=5)
+    ref = O.render(rays, 64, seed=5, given=gpu_samples(tr))
+    assert np.abs(rgb.double().cpu().numpy().reshape(-1, 3) - ref["rgb"]).max() < 1e-4
+    assert np.abs(depth.double().cpu().numpy().reshape(-1) - ref["depth"]).max() < 1e-4
+    assert np.abs(opac.double().cpu().numpy().reshape(-1) - ref["opac"]).max() < 1e-4
+    srv.release(t)
+    srv.close()
