@@ -337,7 +337,7 @@ int dalloc(T** p, size_t count, cudaStream_t s) {
 void free_grid_buffers(sdg_grid g) {
     void* ptrs[] = {g->table, g->tmp_table, g->keys, g->nbr, g->dense, g->geo, g->ggeo, g->m_geo, g->v_geo,
                     g->sdf, g->gsdf, g->m_sdf, g->v_sdf, g->rgbh, g->grgb, g->m_rgb, g->v_rgb, g->sem, g->gsem,
-                    g->m_sem, g->v_sem, g->weight, g->sort_buf, g->counters, g->minmax, g->loss_buf,
+                    g->m_sem, g->v_sem, g->weight, g->sort_buf, g->counters, g->minmax, g->loss_buf, g->sum_scratch,
                     g->fuse_cams, g->beta_grad, g->beta_part,
                     g->ssi_dev, g->lat.fp, g->lat.idx, g->lat.skey, g->lat.keys, g->lat.vidx, g->lat.vbary,
                     g->lat.val0, g->lat.val1, g->lat.nb, g->lat.counters, g->lat.fq, g->lat.sr, g->lat.srank,
@@ -562,6 +562,7 @@ extern "C" int sdg_grid_create(const sdg_grid_desc* d, sdg_grid* out) {
         if (g->sort_cap < kSortTile) g->sort_cap = kSortTile;
         if ((r = dalloc(&g->sort_buf, g->sort_cap, s))) return r;
         if ((r = dalloc(&g->counters, 8, s))) return r;
+        if ((r = dalloc(&g->sum_scratch, kSumBlocks + 1, s))) return r;
         if ((r = dalloc(&g->minmax, 6, s))) return r;
         if ((r = dalloc(&g->beta_grad, 1, s))) return r;
         if ((r = dalloc(&g->ssi_dev, 2, s))) return r;

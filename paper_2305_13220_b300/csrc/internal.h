@@ -56,6 +56,9 @@ struct PreparedBatch {
 };
 
 namespace sdg {
+
+// Blocks of the deterministic sums (reduce.cuh: k_sum), one per SM.
+constexpr int kSumBlocks = 148;
 // Device status word of the bounds-checked build (SDG_CHECKED) on `device`, allocated on first use; NULL in the
 // normal build.
 unsigned long long* checked_status_word(int device);
@@ -97,6 +100,7 @@ struct sdg_grid_s {
     int* minmax = nullptr;                     // device [6]
     int* h_minmax = nullptr;                   // pinned host [6]
     float* loss_buf = nullptr;                 // per-ray loss scratch of the fused training pass
+    float* sum_scratch = nullptr;              // device [kSumBlocks + 1]: partials and ticket of the loss sums
     int64_t loss_cap = 0;
     BatchBufs batch;     // ordering and traversal scratch of the passes enqueued on `stream`
     PreparedBatch prep[2];  // training batches prepared ahead on `aux` (sdg_train_prepare)

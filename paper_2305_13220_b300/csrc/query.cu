@@ -300,7 +300,7 @@ extern "C" int sdg_eikonal(sdg_grid g, const float* xyz, int64_t n, float lambda
         k_eikonal<false><<<grid_blocks(n), kThreads, 0, g->stream>>>(gd, xyz, n, lam_n, per_point);
     SDG_LAUNCH_CHECK("eikonal");
     if (loss_sum) {
-        k_sum<<<1, 1024, 0, g->stream>>>(per_point, n, loss_sum);
+        launch_sum(per_point, n, loss_sum, g->sum_scratch, g->stream);
         SDG_LAUNCH_CHECK("eikonal loss sum");
     }
     return SDG_OK;
@@ -338,7 +338,7 @@ extern "C" int sdg_crf_loss(sdg_grid g, int32_t prop, int64_t n, const float* xy
     }
     SDG_LAUNCH_CHECK("crf loss");
     if (loss_sum) {
-        k_sum<<<1, 1024, 0, st>>>(per_point, n, loss_sum);
+        launch_sum(per_point, n, loss_sum, g->sum_scratch, st);
         SDG_LAUNCH_CHECK("crf loss sum");
     }
     return SDG_OK;

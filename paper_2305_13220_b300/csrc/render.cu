@@ -419,7 +419,7 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
         a.beta_part = g->beta_part;
         rc = launch_pass<PASS_TRAIN_BETA>(g, rays, o->ray_id0, a);
         if (rc) return rc;
-        k_sum<true><<<1, 1024, 0, g->stream>>>(g->beta_part, n, g->beta_grad);  // dL/dbeta += sum over rays
+        launch_sum<true>(g->beta_part, n, g->beta_grad, g->sum_scratch, g->stream);  // dL/dbeta += sum over rays
         SDG_LAUNCH_CHECK("beta gradient sum");
         g->beta_grad_pending = true;
     } else {
@@ -427,7 +427,7 @@ extern "C" int sdg_train_step_rays(sdg_grid g, const float* rays, int64_t n, con
         if (rc) return rc;
     }
     if (loss_sum) {
-        k_sum<<<1, 1024, 0, g->stream>>>(per_ray, n, loss_sum);
+        launch_sum(per_ray, n, loss_sum, g->sum_scratch, g->stream);
         SDG_LAUNCH_CHECK("loss sum");
     }
     return SDG_OK;
@@ -471,7 +471,7 @@ extern "C" int sdg_train_step_rays_normal(sdg_grid g, const float* rays, int64_t
     rc = launch_pass_nosem<PASS_TRAIN_NRM>(g, rays, o->ray_id0, a);
     if (rc) return rc;
     if (loss_sum) {
-        k_sum<<<1, 1024, 0, g->stream>>>(per_ray, n, loss_sum);
+        launch_sum(per_ray, n, loss_sum, g->sum_scratch, g->stream);
         SDG_LAUNCH_CHECK("loss sum");
     }
     return SDG_OK;
@@ -494,7 +494,7 @@ extern "C" int sdg_loss_depth_ssi(sdg_grid g, int64_t n, const float* depth, con
     k_ssi_seeds<<<blocks, 256, 0, g->stream>>>(depth, t_depth, n, g->ssi_dev, lambda / (float)n, g_depth, per_ray);
     SDG_LAUNCH_CHECK("depth loss");
     if (loss_sum) {
-        k_sum<<<1, 1024, 0, g->stream>>>(per_ray, n, loss_sum);
+        launch_sum(per_ray, n, loss_sum, g->sum_scratch, g->stream);
         SDG_LAUNCH_CHECK("depth loss sum");
     }
     if (ab_host) {
@@ -566,7 +566,7 @@ extern "C" int sdg_train_step_rays_noalloc(sdg_grid g, const float* rays, int64_
     rc = launch_pass<PASS_TRAIN>(g, rays, o->ray_id0, a);
     if (rc) return rc;
     if (loss_sum) {
-        k_sum<<<1, 1024, 0, g->stream>>>(scratch, n, loss_sum);
+        launch_sum(scratch, n, loss_sum, g->sum_scratch, g->stream);
         SDG_LAUNCH_CHECK("no-alloc loss sum");
     }
     return SDG_OK;
