@@ -35,26 +35,35 @@ __device__ __forceinline__ void load_job(const GridDev& g, const float* rays, co
 }
 
 // One warp per ray.  !INWARP: every slot, cells from the traversal pass's records (a slot without records is
-// skipped).  INWARP: the warp walks its ray, over every slot when there are no records (a.walk.hdr NULL), else
-// over the overflow list a.walk.over[0, *a.walk.n_over) -- launched with one warp per slot like the records
-// kernel: the list is short (0.15% of the room step's rays) and the warps past its end exit at once.  Kept apart,
-// the records kernel needs no shared memory, which leaves L1 to the voxel gathers.
+// skipped: k_render_overflow renders it).  INWARP: every slot, the warp walking its ray (a pass without traversal
+// records).  Kept apart, the records kernel needs no shared memory, which leaves L1 to the voxel gathers.
 template <int MODE, bool BF16, int NSC, int Q, bool INWARP>
 __global__ void __launch_bounds__(256, (render_min_blocks<MODE, NSC, Q>()))
     k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
     __shared__ WarpSmem smem[INWARP ? kWarpsPerBlock : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (w >= a.n) return;  // warp-uniform
     RayJob j;
-    if constexpr (!INWARP) {
-        if (w >= a.n) return;  // warp-uniform
-        load_job(g, rays, a.perm, ray_id0, w, a.n, j);
-        ray_program<MODE, BF16, NSC, Q, false>(g, a, j, smem[0], lane);
-    } else {
-        const bool list = a.walk.hdr != nullptr;
-        const int64_t end = list ? (int64_t)__ldg(a.walk.n_over) : a.n;
-        if (w >= end) return;  // warp-uniform
-        load_job(g, rays, a.perm, ray_id0, list ? (int64_t)__ldg(a.walk.over + w) : w, a.n, j);
+    load_job(g, rays, a.perm, ray_id0, w, a.n, j);
+    ray_program<MODE, BF16, NSC, Q, INWARP>(g, a, j, smem[INWARP ? warp : 0], lane);
+}
+
+// The overflow list a.walk.over[0, *a.walk.n_over) of a pass with traversal records (the rays crossing more than
+// kWalkCap allocated cells, 0.15% of the room step's rays), walked in-warp by a grid of at most kOverflowBlocks
+// blocks striding over the list.  It runs alone after the records kernel, so it takes the registers that keep the
+// loop free of spills (2 blocks per SM) and a grid that is dispatched at once.
+constexpr unsigned kOverflowBlocks = 296;
+
+template <int MODE, bool BF16, int NSC, int Q>
+__global__ void __launch_bounds__(256, 2)
+    k_render_overflow(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
+    __shared__ WarpSmem smem[kWarpsPerBlock];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t end = (int64_t)__ldg(a.walk.n_over), stride = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t q = (int64_t)blockIdx.x * kWarpsPerBlock + warp; q < end; q += stride) {
+        RayJob j;
+        load_job(g, rays, a.perm, ray_id0, (int64_t)__ldg(a.walk.over + q), a.n, j);
         ray_program<MODE, BF16, NSC, Q, true>(g, a, j, smem[warp], lane);
     }
 }
@@ -65,7 +74,9 @@ int launch_one(const GridDev& gd, const float* rays, uint32_t id0, const PassArg
     constexpr bool kNoWalk = MODE == PASS_BWD_STORE;  // samples come from the forward's stored records
     if (kNoWalk || a.walk.hdr) {
         k_render<MODE, BF16, NSC, Q, false><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
-        if (!kNoWalk) k_render<MODE, BF16, NSC, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
+        if constexpr (!kNoWalk)
+            k_render_overflow<MODE, BF16, NSC, Q>
+                <<<blocks < kOverflowBlocks ? blocks : kOverflowBlocks, 256, 0, s>>>(gd, rays, id0, a);
     } else {
         k_render<MODE, BF16, NSC, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
     }

@@ -71,20 +71,11 @@ __global__ void __launch_bounds__(256) k_serve_walk(const GridDev* __restrict__ 
     walk_ray_records(scenes[ch->scene], o, d, ch->tnear, ch->tfar, w, slot);
 }
 
-// One warp per ray.  OVER false: every slot of the batch, cells from the traversal pass's records (a slot without
-// records is left to the overflow kernel); OVER true: the slots of the overflow list, walked in-warp (a grid as
-// large as the batch's, the warps past the list's end exiting at once).  3 CTAs per SM at 4 samples per lane
-// (80 registers), 2 above.
+// The ray of batch slot `slot` rendered by one warp: from the traversal pass's records (OVER false) or walked
+// in-warp (OVER true).
 template <bool BF16, int Q, bool OVER>
-__global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
-    k_serve(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks, int chunk_rays, WalkBufs wb) {
-    __shared__ WarpSmem smem[OVER ? kWarpsPerBlock : 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t slot = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-    if constexpr (OVER) {
-        if (slot >= (int64_t)__ldg(wb.n_over)) return;  // warp-uniform
-        slot = __ldg(wb.over + slot);
-    }
+__device__ __forceinline__ void serve_ray(const GridDev* scenes, const ChunkDesc* chunks, int chunk_rays,
+                                          const WalkBufs& wb, int64_t slot, WarpSmem& sm, int lane) {
     const ChunkDesc* ch;
     RayJob j;
     if (!slot_ray(chunks, chunk_rays, slot, ch, j.idx, j.o, j.d)) return;  // warp-uniform
@@ -101,7 +92,33 @@ __global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
     a.out_depth = ch->depth;
     a.out_opac = ch->opac;
     a.walk = wb;
-    ray_program<PASS_FWD, BF16, 0, Q, OVER>(scenes[ch->scene], a, j, smem[OVER ? warp : 0], lane);
+    ray_program<PASS_FWD, BF16, 0, Q, OVER>(scenes[ch->scene], a, j, sm, lane);
+}
+
+// One warp per slot of the batch, cells from the traversal pass's records (a slot without records is left to
+// k_serve_overflow).  3 CTAs per SM at 4 samples per lane (80 registers), 2 above.
+template <bool BF16, int Q>
+__global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
+    k_serve(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks, int chunk_rays, WalkBufs wb) {
+    __shared__ WarpSmem smem[1];
+    const int64_t slot = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    serve_ray<BF16, Q, false>(scenes, chunks, chunk_rays, wb, slot, smem[0], threadIdx.x & 31);
+}
+
+// The batch's overflow list (rays crossing more than kWalkCap allocated cells), walked in-warp by a grid of at
+// most kServeOverflowBlocks blocks striding over the list; it runs alone after the records kernel on the batch's
+// stream, so it takes the registers that keep the loop free of spills.
+constexpr unsigned kServeOverflowBlocks = 296;
+
+template <bool BF16, int Q>
+__global__ void __launch_bounds__(256, 2)
+    k_serve_overflow(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks, int chunk_rays,
+                     WalkBufs wb) {
+    __shared__ WarpSmem smem[kWarpsPerBlock];
+    const int warp = threadIdx.x >> 5;
+    const int64_t end = (int64_t)__ldg(wb.n_over), stride = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t q = (int64_t)blockIdx.x * kWarpsPerBlock + warp; q < end; q += stride)
+        serve_ray<BF16, Q, true>(scenes, chunks, chunk_rays, wb, __ldg(wb.over + q), smem[warp], threadIdx.x & 31);
 }
 
 double now_ms() {
@@ -336,8 +353,9 @@ struct sdg_server_s {
                                                                                    o.chunk_rays, nslots, wb);
 #define SDG_SERVE(BF, QQ)                                                                                      \
     do {                                                                                                       \
-        k_serve<BF, QQ, false><<<blocks, 256, 0, b->stream>>>(b->d_scenes, b->d_chunks, o.chunk_rays, wb);      \
-        k_serve<BF, QQ, true><<<blocks, 256, 0, b->stream>>>(b->d_scenes, b->d_chunks, o.chunk_rays, wb);       \
+        k_serve<BF, QQ><<<blocks, 256, 0, b->stream>>>(b->d_scenes, b->d_chunks, o.chunk_rays, wb);             \
+        k_serve_overflow<BF, QQ><<<std::min(blocks, kServeOverflowBlocks), 256, 0, b->stream>>>(                \
+            b->d_scenes, b->d_chunks, o.chunk_rays, wb);                                                       \
     } while (0)
             if (bf16) {
                 if (Q == 2) SDG_SERVE(true, 2); else if (Q == 4) SDG_SERVE(true, 4);
