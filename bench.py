@@ -604,6 +604,24 @@ def run_ours(args):
 # ----------------------------------------------------------------------------------------------------------
 # Other workloads: precision variant, serving, apartment
 # ----------------------------------------------------------------------------------------------------------
+def _prepared_steps(sdg, G, batches, train, ray_order):
+    """A step function over `batches` in cyclic order, pipelined as the room step is: after each batch's training
+    pass the next batch's ordering and traversal are enqueued on the grid's auxiliary stream (sdg_train_prepare),
+    beside the optimiser step.  train(batch, seed, prepared_slot) runs the training pass."""
+    st = {"k": 0, "slot": None}
+
+    def step(_b, seed):
+        nb = len(batches)
+        b, nxt = batches[st["k"] % nb], batches[(st["k"] + 1) % nb]
+        train(b, seed, st["slot"])
+        slot = 0 if st["slot"] is None else 1 - st["slot"]
+        sdg.train_prepare(G, nxt["rays"], nxt["depth"], slot, ray_order=ray_order)
+        st["slot"] = slot
+        st["k"] += 1
+        G.adam_step(lr=1e-3)
+    return step
+
+
 def _timed_steps(torch, step, batches, K, W_):
     for i in range(W_):
         step(batches[i % len(batches)], i)
@@ -775,10 +793,9 @@ def measure_precision(args, compact=False):
     del full, stored, ggot
     G.zero_grad()
 
-    def step(b, i):
-        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i,
-                            ray_order=args.ray_order)
-        G.adam_step(lr=1e-3)
+    step = _prepared_steps(sdg, G, batches, lambda b, i, slot: sdg.train_step_rays(
+        G, b["rays"], b["rgb"], b["depth"], b["sem"], n_samples=N_SAMPLES, seed=i, ray_order=args.ray_order,
+        prepared=slot), args.ray_order)
 
     ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
     phases = _phase_times(torch, sdg, G, batches, args.steps, lambda b, i: sdg.train_step_rays(
@@ -926,12 +943,11 @@ def measure_apartment(args, compact=False):
     batches = [synth.training_batch(sc, poses, W, H, K, 1 << 20, seed=b, device=device, order=args.order)
                for b in range(2)]
 
-    def step(b, i):
-        sdg.train_step_rays(G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i,
-                            ray_order=args.ray_order)
-        G.adam_step(lr=1e-3)
-
+    step = _prepared_steps(sdg, G, batches, lambda b, i, slot: sdg.train_step_rays(
+        G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i, ray_order=args.ray_order, prepared=slot),
+        args.ray_order)
     ms = _timed_steps(torch, step, batches, args.steps, args.warmup)
+    torch.cuda.synchronize()
     phases = _phase_times(torch, sdg, G, batches, args.steps, lambda b, i: sdg.train_step_rays(
         G, b["rays"], b["rgb"], b["depth"], n_samples=N_SAMPLES, seed=i, ray_order=args.ray_order))
     G.close()
