@@ -34,15 +34,26 @@ __device__ __forceinline__ void load_job(const GridDev& g, const float* rays, co
     j.slot = slot;
 }
 
+// Warps per block: 4 for the records kernels without logits (a block holds its SM slots until its slowest ray
+// ends, so small blocks keep an SM fuller: 0.950 -> 0.938 ms per room step against 8, 0.989 with 12; the unfused
+// forward 0.695 -> 0.626 ms), 8 for the semantic ones (5.80 ms with 4 against 5.70) and for the in-warp kernels
+// (the shared memory of their walk is per warp).  Blocks per SM scale so the registers per thread stay the same.
+template <int NSC, bool INWARP>
+constexpr int render_wpb() { return INWARP || NSC > 0 ? kWarpsPerBlock : 4; }
+template <int MODE, int NSC, int Q, bool INWARP>
+constexpr int render_blocks_per_sm() {
+    return render_min_blocks<MODE, NSC, Q>() * kWarpsPerBlock / render_wpb<NSC, INWARP>();
+}
+
 // One warp per ray.  !INWARP: every slot, cells from the traversal pass's records (a slot without records is
 // skipped: k_render_overflow renders it).  INWARP: every slot, the warp walking its ray (a pass without traversal
 // records).  Kept apart, the records kernel needs no shared memory, which leaves L1 to the voxel gathers.
 template <int MODE, bool BF16, int NSC, int Q, bool INWARP>
-__global__ void __launch_bounds__(256, (render_min_blocks<MODE, NSC, Q>()))
+__global__ void __launch_bounds__(32 * render_wpb<NSC, INWARP>(), (render_blocks_per_sm<MODE, NSC, Q, INWARP>()))
     k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
     __shared__ WarpSmem smem[INWARP ? kWarpsPerBlock : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    const int64_t w = (int64_t)blockIdx.x * render_wpb<NSC, INWARP>() + warp;
     if (w >= a.n) return;  // warp-uniform
     RayJob j;
     load_job(g, rays, a.perm, ray_id0, w, a.n, j);
@@ -73,7 +84,8 @@ int launch_one(const GridDev& gd, const float* rays, uint32_t id0, const PassArg
     const unsigned blocks = (unsigned)((a.n + kWarpsPerBlock - 1) / kWarpsPerBlock);
     constexpr bool kNoWalk = MODE == PASS_BWD_STORE;  // samples come from the forward's stored records
     if (kNoWalk || a.walk.hdr) {
-        k_render<MODE, BF16, NSC, Q, false><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
+        constexpr int R = render_wpb<NSC, false>();
+        k_render<MODE, BF16, NSC, Q, false><<<(unsigned)((a.n + R - 1) / R), 32 * R, 0, s>>>(gd, rays, id0, a);
         if constexpr (!kNoWalk)
             k_render_overflow<MODE, BF16, NSC, Q>
                 <<<blocks < kOverflowBlocks ? blocks : kOverflowBlocks, 256, 0, s>>>(gd, rays, id0, a);

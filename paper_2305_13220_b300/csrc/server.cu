@@ -96,12 +96,14 @@ __device__ __forceinline__ void serve_ray(const GridDev* scenes, const ChunkDesc
 }
 
 // One warp per slot of the batch, cells from the traversal pass's records (a slot without records is left to
-// k_serve_overflow).  3 CTAs per SM at 4 samples per lane (80 registers), 2 above.
+// k_serve_overflow).  Blocks of kServeWarps warps, 6 per SM at 4 samples per lane (80 registers), 4 above.
+constexpr int kServeWarps = 4;
+
 template <bool BF16, int Q>
-__global__ void __launch_bounds__(256, (Q <= 4 ? 3 : 2))
+__global__ void __launch_bounds__(32 * kServeWarps, (Q <= 4 ? 6 : 4))
     k_serve(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks, int chunk_rays, WalkBufs wb) {
     __shared__ WarpSmem smem[1];
-    const int64_t slot = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t slot = (int64_t)blockIdx.x * kServeWarps + (threadIdx.x >> 5);
     serve_ray<BF16, Q, false>(scenes, chunks, chunk_rays, wb, slot, smem[0], threadIdx.x & 31);
 }
 
@@ -353,7 +355,8 @@ struct sdg_server_s {
                                                                                    o.chunk_rays, nslots, wb);
 #define SDG_SERVE(BF, QQ)                                                                                      \
     do {                                                                                                       \
-        k_serve<BF, QQ><<<blocks, 256, 0, b->stream>>>(b->d_scenes, b->d_chunks, o.chunk_rays, wb);             \
+        k_serve<BF, QQ><<<(unsigned)((nslots + kServeWarps - 1) / kServeWarps), 32 * kServeWarps, 0, b->stream>>>(  \
+            b->d_scenes, b->d_chunks, o.chunk_rays, wb);                                                       \
         k_serve_overflow<BF, QQ><<<std::min(blocks, kServeOverflowBlocks), 256, 0, b->stream>>>(                \
             b->d_scenes, b->d_chunks, o.chunk_rays, wb);                                                       \
     } while (0)
