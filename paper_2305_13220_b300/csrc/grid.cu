@@ -353,6 +353,7 @@ void free_grid_buffers(sdg_grid g) {
     if (g->aux) cudaStreamDestroy(g->aux);
     if (g->h_counters) cudaFreeHost(g->h_counters);
     if (g->h_minmax) cudaFreeHost(g->h_minmax);
+    if (g->h_over) cudaFreeHost(g->h_over);
 }
 
 // Sorts sort_buf[0, n) ascending (pads to a power of two >= 2048 with all-ones).
@@ -568,6 +569,8 @@ extern "C" int sdg_grid_create(const sdg_grid_desc* d, sdg_grid* out) {
         if ((r = dalloc(&g->ssi_dev, 2, s))) return r;
         SDG_CUDA_TRY(cudaMallocHost((void**)&g->h_counters, 8 * sizeof(unsigned long long)));
         SDG_CUDA_TRY(cudaMallocHost((void**)&g->h_minmax, 6 * sizeof(int)));
+        SDG_CUDA_TRY(cudaMallocHost((void**)&g->h_over, sizeof(int)));
+        *g->h_over = 0;
         SDG_CUDA_TRY(cudaStreamSynchronize(s));
         return SDG_OK;
     };

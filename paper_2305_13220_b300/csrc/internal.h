@@ -99,6 +99,7 @@ struct sdg_grid_s {
     unsigned long long* h_counters = nullptr;  // pinned host [8]
     int* minmax = nullptr;                     // device [6]
     int* h_minmax = nullptr;                   // pinned host [6]
+    int* h_over = nullptr;  // pinned host [1]: overflow-list length of the last pass, copied after it (a hint)
     float* loss_buf = nullptr;                 // per-ray loss scratch of the fused training pass
     float* sum_scratch = nullptr;              // device [kSumBlocks + 1]: partials and ticket of the loss sums
     int64_t loss_cap = 0;

@@ -33,6 +33,17 @@ int pass_event(sdg_grid g, int which) {
     return SDG_OK;
 }
 
+// a with the overflow-list sizing hint: the length the grid's last pass with traversal records stored in its
+// pinned word h_over (a kernel writes it as it runs, the host reads whatever is there: it only sizes launches)
+PassArgs with_over_hint(sdg_grid g, const PassArgs& a) {
+    PassArgs b = a;
+    if (a.walk.hdr && g->h_over) {
+        b.over_hint = *reinterpret_cast<volatile int*>(g->h_over);
+        b.over_out = g->h_over;
+    }
+    return b;
+}
+
 template <int MODE>
 int launch_pass(sdg_grid g, const float* rays, uint32_t id0, const PassArgs& a) {
     if (a.n == 0) return SDG_OK;
@@ -40,7 +51,8 @@ int launch_pass(sdg_grid g, const float* rays, uint32_t id0, const PassArgs& a) 
     const int Q = pick_q(a.N);
     int rc = pass_event(g, 0);
     if (rc) return rc;
-    rc = launch_layout<MODE>(g->desc.rgb_dtype == SDG_BF16, g->desc.n_sem, gd, rays, id0, a, Q, g->stream);
+    rc = launch_layout<MODE>(g->desc.rgb_dtype == SDG_BF16, g->desc.n_sem, gd, rays, id0, with_over_hint(g, a), Q,
+                             g->stream);
     return rc ? rc : pass_event(g, 1);
 }
 
@@ -52,8 +64,9 @@ int launch_pass_nosem(sdg_grid g, const float* rays, uint32_t id0, const PassArg
     const int Q = pick_q(a.N);
     int rc = pass_event(g, 0);
     if (rc) return rc;
-    if (g->desc.rgb_dtype == SDG_BF16) rc = launch_q<MODE, true, 0>(gd, rays, id0, a, Q, g->stream);
-    else rc = launch_q<MODE, false, 0>(gd, rays, id0, a, Q, g->stream);
+    const PassArgs b = with_over_hint(g, a);
+    if (g->desc.rgb_dtype == SDG_BF16) rc = launch_q<MODE, true, 0>(gd, rays, id0, b, Q, g->stream);
+    else rc = launch_q<MODE, false, 0>(gd, rays, id0, b, Q, g->stream);
     return rc ? rc : pass_event(g, 1);
 }
 

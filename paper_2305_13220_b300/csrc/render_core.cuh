@@ -78,6 +78,8 @@ struct PassArgs {
     int strat;
     float bg[3];
     int64_t n;  // rays in this launch
+    int64_t over_hint;  // host side: expected length of the overflow list (launch sizing only; 0: unknown)
+    int* over_out;      // nullable, pinned host memory: the overflow kernel stores the list's length there
     float *out_rgb, *out_depth, *out_opac, *out_sem;
     float* rec;    // store mode: [kRecChannels][n][32*Q]
     float* rec_S;  // store mode: [n]

@@ -2,6 +2,8 @@
 // pass) in the render_inst_*.cu files so that they compile in parallel.
 #pragma once
 
+#include <algorithm>
+
 #include "render_core.cuh"
 
 namespace sdg {
@@ -60,6 +62,21 @@ __global__ void __launch_bounds__(32 * render_wpb<NSC, INWARP>(), (render_blocks
     ray_program<MODE, BF16, NSC, Q, INWARP>(g, a, j, smem[INWARP ? warp : 0], lane);
 }
 
+// The first entries of the overflow list, one warp each (no loop, so the in-warp program keeps the registers of
+// the other in-warp kernels without spilling): as many as the grid's previous pass produced, so a scene where
+// many rays cross more than kWalkCap cells (a large apartment: 10%) renders them at full occupancy.
+template <int MODE, bool BF16, int NSC, int Q>
+__global__ void __launch_bounds__(256, (render_min_blocks<MODE, NSC, Q>()))
+    k_render_list(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
+    __shared__ WarpSmem smem[kWarpsPerBlock];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (q >= (int64_t)__ldg(a.walk.n_over)) return;  // warp-uniform
+    RayJob j;
+    load_job(g, rays, a.perm, ray_id0, (int64_t)__ldg(a.walk.over + q), a.n, j);
+    ray_program<MODE, BF16, NSC, Q, true>(g, a, j, smem[warp], lane);
+}
+
 // The overflow list a.walk.over[0, *a.walk.n_over) of a pass with traversal records (the rays crossing more than
 // kWalkCap allocated cells, 0.15% of the room step's rays), walked in-warp by a grid of at most kOverflowBlocks
 // blocks striding over the list.  It runs alone after the records kernel, so it takes the registers that keep the
@@ -68,11 +85,12 @@ constexpr unsigned kOverflowBlocks = 296;
 
 template <int MODE, bool BF16, int NSC, int Q>
 __global__ void __launch_bounds__(256, 2)
-    k_render_overflow(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
+    k_render_overflow(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a, int64_t first) {
     __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t end = (int64_t)__ldg(a.walk.n_over), stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t q = (int64_t)blockIdx.x * kWarpsPerBlock + warp; q < end; q += stride) {
+    if (a.over_out && blockIdx.x == 0 && threadIdx.x == 0) *a.over_out = (int)end;  // the next pass's hint
+    for (int64_t q = first + (int64_t)blockIdx.x * kWarpsPerBlock + warp; q < end; q += stride) {
         RayJob j;
         load_job(g, rays, a.perm, ray_id0, (int64_t)__ldg(a.walk.over + q), a.n, j);
         ray_program<MODE, BF16, NSC, Q, true>(g, a, j, smem[warp], lane);
@@ -86,9 +104,17 @@ int launch_one(const GridDev& gd, const float* rays, uint32_t id0, const PassArg
     if (kNoWalk || a.walk.hdr) {
         constexpr int R = render_wpb<NSC, false>();
         k_render<MODE, BF16, NSC, Q, false><<<(unsigned)((a.n + R - 1) / R), 32 * R, 0, s>>>(gd, rays, id0, a);
-        if constexpr (!kNoWalk)
-            k_render_overflow<MODE, BF16, NSC, Q>
-                <<<blocks < kOverflowBlocks ? blocks : kOverflowBlocks, 256, 0, s>>>(gd, rays, id0, a);
+        if constexpr (!kNoWalk) {
+            // a list longer than the strided kernel takes in one turn: entries [0, 8 * lb) one warp each, sized
+            // from the hint with a margin, the rest (normally none) by the strided kernel
+            const int64_t want = a.over_hint > 2 * (int64_t)kOverflowBlocks * kWarpsPerBlock
+                                     ? a.over_hint + a.over_hint / 4 + 64
+                                     : 0;
+            const unsigned lb = (unsigned)std::min<int64_t>((want + kWarpsPerBlock - 1) / kWarpsPerBlock, blocks);
+            if (lb) k_render_list<MODE, BF16, NSC, Q><<<lb, 256, 0, s>>>(gd, rays, id0, a);
+            k_render_overflow<MODE, BF16, NSC, Q><<<blocks < kOverflowBlocks ? blocks : kOverflowBlocks, 256, 0, s>>>(
+                gd, rays, id0, a, (int64_t)lb * kWarpsPerBlock);
+        }
     } else {
         k_render<MODE, BF16, NSC, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);
     }
