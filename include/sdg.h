@@ -267,8 +267,9 @@ int sdg_render_backward(sdg_ctx ctx, const float* g_rgb_dev, const float* g_dept
  * the same traversal and placement code as the other passes and writes, for
  * each ray i (row i of rays_dev) and sample k, to device buffers:
  *   n_cells [n]      allocated block cells in the ray's traversal record, or -1
- *                    when the ray crossed more than SDG_TRACE_CELLS of them and
- *                    its warp walked it itself (or walk = SDG_WALK_IN_WARP);
+ *                    when the ray crossed more than SDG_TRACE_CELLS of them
+ *                    (rendered from up to twice as many records two per lane,
+ *                    beyond that walked in-warp) or walk = SDG_WALK_IN_WARP;
  *   S [n]            total allocated length (0: the ray meets no block);
  *   t [n][N]         ray parameter t_k of sample k;
  *   cell [n][N][3]   voxel coordinates of the base corner of the sample's cell
@@ -282,7 +283,7 @@ int sdg_render_backward(sdg_ctx ctx, const float* g_rgb_dev, const float* g_dept
  * walk: SDG_WALK_PASS (the traversal pass used by sdg_render_forward,
  * sdg_render_backward, the training passes and the serving loop) or
  * SDG_WALK_IN_WARP (the in-warp traversal used by the allocation-free pass and
- * for the rays that cross more than SDG_TRACE_CELLS allocated cells).
+ * for the rays that cross more than 2 * SDG_TRACE_CELLS allocated cells).
  * Asynchronous on the grid's stream.  Errors: SDG_ERR_ARG (null or
  * misaligned buffer, bad walk), SDG_ERR_OOM, SDG_ERR_CUDA. */
 #define SDG_TRACE_CELLS 32
@@ -604,10 +605,11 @@ int sdg_fuse_finalize(sdg_grid g);
  * several streams, so batches overlap on the device.  A request's result
  * does not depend on what it was batched with: every ray is computed by the
  * same per-ray code, from its own pixel index (a traversal pass over the
- * batch, then the records kernel; rays crossing more than SDG_TRACE_CELLS
- * allocated cells walked in-warp).  Besides the output pool the server holds
- * traversal records for max_batch_rays rays per stream: 8 + 20 *
- * SDG_TRACE_CELLS + 4 bytes a ray (about 170 MB per stream at 2^18 rays). */
+ * batch, then the records kernels -- one record per lane up to
+ * SDG_TRACE_CELLS allocated cells, two up to twice that -- and rays crossing
+ * more walked in-warp).  Besides the output pool the server holds
+ * traversal records for max_batch_rays rays per stream: 8 + 40 *
+ * SDG_TRACE_CELLS + 8 bytes a ray (about 340 MB per stream at 2^18 rays). */
 typedef struct {
     int64_t hbm_budget_bytes; /* device memory for in-flight outputs (the server allocates it once) */
     int32_t max_slots;        /* requests in flight at once, >= 1 */

@@ -569,8 +569,8 @@ extern "C" int sdg_grid_create(const sdg_grid_desc* d, sdg_grid* out) {
         if ((r = dalloc(&g->ssi_dev, 2, s))) return r;
         SDG_CUDA_TRY(cudaMallocHost((void**)&g->h_counters, 8 * sizeof(unsigned long long)));
         SDG_CUDA_TRY(cudaMallocHost((void**)&g->h_minmax, 6 * sizeof(int)));
-        SDG_CUDA_TRY(cudaMallocHost((void**)&g->h_over, sizeof(int)));
-        *g->h_over = 0;
+        SDG_CUDA_TRY(cudaMallocHost((void**)&g->h_over, 2 * sizeof(int)));
+        g->h_over[0] = g->h_over[1] = 0;
         SDG_CUDA_TRY(cudaStreamSynchronize(s));
         return SDG_OK;
     };

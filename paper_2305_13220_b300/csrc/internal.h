@@ -40,7 +40,7 @@ struct BatchBufs {
     int2* walk_hdr = nullptr;
     float* walk_s0 = nullptr;
     int4* walk_rec = nullptr;
-    int* walk_over = nullptr;  // slots without records [walk_cap], their count at [walk_cap]
+    int* walk_over = nullptr;  // overflow list [walk_cap], mid list [walk_cap], their lengths [2] (WalkBufs)
     int64_t walk_cap = 0;
 };
 
@@ -99,7 +99,7 @@ struct sdg_grid_s {
     unsigned long long* h_counters = nullptr;  // pinned host [8]
     int* minmax = nullptr;                     // device [6]
     int* h_minmax = nullptr;                   // pinned host [6]
-    int* h_over = nullptr;  // pinned host [1]: overflow-list length of the last pass, copied after it (a hint)
+    int* h_over = nullptr;  // pinned host [2]: overflow- and mid-list lengths of the last pass (launch hints)
     float* loss_buf = nullptr;                 // per-ray loss scratch of the fused training pass
     float* sum_scratch = nullptr;              // device [kSumBlocks + 1]: partials and ticket of the loss sums
     int64_t loss_cap = 0;

@@ -33,12 +33,14 @@ int pass_event(sdg_grid g, int which) {
     return SDG_OK;
 }
 
-// a with the overflow-list sizing hint: the length the grid's last pass with traversal records stored in its
-// pinned word h_over (a kernel writes it as it runs, the host reads whatever is there: it only sizes launches)
+// a with the list sizing hints: the overflow- and mid-list lengths the grid's last pass with traversal records
+// stored in its pinned words h_over (a kernel writes them as it runs, the host reads whatever is there: they only
+// size launches)
 PassArgs with_over_hint(sdg_grid g, const PassArgs& a) {
     PassArgs b = a;
     if (a.walk.hdr && g->h_over) {
-        b.over_hint = *reinterpret_cast<volatile int*>(g->h_over);
+        b.over_hint = reinterpret_cast<volatile int*>(g->h_over)[0];
+        b.mid_hint = reinterpret_cast<volatile int*>(g->h_over)[1];
         b.over_out = g->h_over;
     }
     return b;
@@ -142,26 +144,29 @@ int walk_scratch(sdg_grid g, BatchBufs& b, int64_t n) {
     b.walk_over = nullptr;
     b.walk_cap = 0;
     SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_hdr, sizeof(int2) * n));
-    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_s0, sizeof(float) * kWalkCap * n));
-    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_rec, sizeof(int4) * kWalkCap * n));
-    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_over, sizeof(int) * (n + 1)));  // list, and its length at [n]
+    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_s0, sizeof(float) * kWalkSlot * n));
+    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_rec, sizeof(int4) * kWalkSlot * n));
+    // the overflow list [n], the mid list [n], their lengths at [2n] and [2n + 1]
+    SDG_CUDA_TRY(cudaMalloc((void**)&b.walk_over, sizeof(int) * (2 * n + 2)));
     b.walk_cap = n;
     return SDG_OK;
 }
 
 // The records of b as the render kernels read them.
 WalkBufs walk_bufs(const BatchBufs& b) {
-    return WalkBufs{b.walk_hdr, b.walk_s0, b.walk_rec, b.walk_over, b.walk_over + b.walk_cap};
+    const int64_t n = b.walk_cap;
+    return WalkBufs{b.walk_hdr,          b.walk_s0,         b.walk_rec,         b.walk_over,
+                    b.walk_over + 2 * n, b.walk_over + n,   b.walk_over + 2 * n + 1};
 }
 
 int walk_rays_into(sdg_grid g, BatchBufs& b, cudaStream_t st, const float* rays, const int* perm, int64_t n,
                    PassArgs& a) {
-    a.walk = WalkBufs{nullptr, nullptr, nullptr, nullptr, nullptr};
+    a.walk = WalkBufs{};
     if (n == 0) return SDG_OK;
     int rc = walk_scratch(g, b, n);
     if (rc) return rc;
     const WalkBufs w = walk_bufs(b);
-    SDG_CUDA_TRY(cudaMemsetAsync(w.n_over, 0, sizeof(int), st));
+    SDG_CUDA_TRY(cudaMemsetAsync(w.n_over, 0, 2 * sizeof(int), st));  // n_over and n_mid
     k_walk<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->dev(), rays, perm, n, w);
     SDG_LAUNCH_CHECK("traversal pass");
     a.walk = w;

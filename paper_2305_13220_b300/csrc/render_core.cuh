@@ -52,21 +52,27 @@ enum PassMode {
     PASS_FWD_TRACE = 7   // PASS_FWD that also writes where every sample was placed (debug export)
 };
 
-// Allocated block cells of a ray kept in the walk records; a ray crossing more takes the in-warp traversal.
+// Allocated block cells of a ray kept in the walk records: up to kWalkCap a ray is rendered by the records kernel
+// (lane m holds record m), up to kWalkSlot by the kernel over the mid list (lane m holds records m and m + 32), a
+// ray crossing more takes the in-warp traversal.
 constexpr int kWalkCap = 32;
+constexpr int kWalkSlot = 2 * kWalkCap;
 
-// Output of k_walk, indexed by processing slot: hdr[slot] = {number of records (-1: more than kWalkCap),
-// bits of S}; record m of the slot at [slot * kWalkCap + m]: s0 = skip-space offset of the cell (sequential FP32
+// Output of k_walk, indexed by processing slot: hdr[slot] = {number of records (-1: more than kWalkSlot),
+// bits of S}; record m of the slot at [slot * kWalkSlot + m]: s0 = skip-space offset of the cell (sequential FP32
 // sum of the lengths before it, so the offsets are monotone and S = s0 + len of the last), and
 // rec = {bits of t_in, bits of len, block index, dense-grid cell}.
-// Slots of rays crossing more than kWalkCap allocated cells are appended to over[0, *n_over) (in no particular
-// order): the records kernel skips them, the in-warp kernel renders them.
+// Slots of rays with kWalkCap + 1 .. kWalkSlot records are appended to mid[0, *n_mid), those of rays crossing
+// more than kWalkSlot allocated cells to over[0, *n_over) (each in no particular order): the records kernel skips
+// both, the mid-list kernel and the in-warp kernels render them.
 struct WalkBufs {
     int2* hdr;
     float* s0;
     int4* rec;
     int* over;
     int* n_over;
+    int* mid;
+    int* n_mid;
 };
 
 // Store-mode record channels per sample: t, sdf (NaN if invalid), r, g, b, block index (int bits).
@@ -78,8 +84,8 @@ struct PassArgs {
     int strat;
     float bg[3];
     int64_t n;  // rays in this launch
-    int64_t over_hint;  // host side: expected length of the overflow list (launch sizing only; 0: unknown)
-    int* over_out;      // nullable, pinned host memory: the overflow kernel stores the list's length there
+    int64_t over_hint, mid_hint;  // host side: expected lengths of the overflow and mid lists (launch sizing only)
+    int* over_out;  // nullable, pinned host memory [2]: k_render_rest stores the two lists' lengths there
     float *out_rgb, *out_depth, *out_opac, *out_sem;
     float* rec;    // store mode: [kRecChannels][n][32*Q]
     float* rec_S;  // store mode: [n]
@@ -332,10 +338,10 @@ __device__ __forceinline__ void walk_ray_records(const GridDev& g, const float3&
     float S = 0.f;
     if (clip_to_grid(g, o, d, t0, t1)) {
         const float3 invd = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
-        float* s0 = w.s0 + slot * kWalkCap;
-        int4* rec = w.rec + slot * kWalkCap;
+        float* s0 = w.s0 + slot * kWalkSlot;
+        int4* rec = w.rec + slot * kWalkSlot;
         walk_cells_pipelined<8>(g, o, d, invd, t0, t1, [&](float x0, float x1, int cell, int blk) {
-            if (cnt == kWalkCap) {
+            if (cnt == kWalkSlot) {
                 cnt = -1;  // more cells than records: the render warp walks this ray itself
                 return false;
             }
@@ -349,6 +355,7 @@ __device__ __forceinline__ void walk_ray_records(const GridDev& g, const float3&
     }
     w.hdr[slot] = make_int2(cnt, __float_as_int(S));
     if (cnt < 0) w.over[atomicAdd(w.n_over, 1)] = (int)slot;
+    else if (cnt > kWalkCap) w.mid[atomicAdd(w.n_mid, 1)] = (int)slot;
 }
 
 struct Pieces {
@@ -583,11 +590,13 @@ __device__ __forceinline__ T pick(const T (&a)[Q], int i) {
 // The per-ray program
 // ---------------------------------------------------------------------------
 // INWARP: the warp walks its ray itself (walk_pieces); otherwise the ray's cells come from the traversal pass's
-// records (a ray without records -- more cells than kWalkCap -- is left to the INWARP kernel).  NSC: semantic
-// channels the program is unrolled for (0: no logits; else a multiple of 4 >= the grid's n_sem).
-template <int MODE, bool BF16, int NSC, int Q, bool INWARP>
+// records, RPL per lane: RPL = 1 renders rays with at most kWalkCap records (others are left to the mid-list and
+// in-warp kernels), RPL = 2 those of the mid list.  NSC: semantic channels the program is unrolled for (0: no
+// logits; else a multiple of 4 >= the grid's n_sem).
+template <int MODE, bool BF16, int NSC, int Q, bool INWARP, int RPL = 1>
 __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a, const RayJob& j, WarpSmem& sm,
                                             int lane) {
+    static_assert(RPL == 1 || RPL == 2, "one or two records per lane");
     constexpr bool kStoreIn = MODE == PASS_BWD_STORE;
     constexpr bool kStoreOut = MODE == PASS_FWD_STORE;
     constexpr bool kTrain = MODE == PASS_TRAIN || MODE == PASS_TRAIN_BETA || MODE == PASS_TRAIN_NRM;
@@ -609,33 +618,41 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     Pieces pc;
     float t1 = 0.f;
     float S;
-    // walk records of this ray (lane m holds record m), when the traversal ran as its own pass
+    // walk records of this ray (lane m holds record m, and m + 32 when RPL = 2), when the traversal ran as its own
+    // pass
     bool by_rec = false;
     int n_rec = 0;
-    float my_s0 = 0.f;
-    int4 my_rec = make_int4(0, 0, -1, -1);
+    float my_s0 = 0.f, my_s0b = 0.f;
+    int4 my_rec = make_int4(0, 0, -1, -1), my_recb = make_int4(0, 0, -1, -1);
     if constexpr (kStoreIn) {
         S = a.rec_S[j.idx];
     } else {
         if constexpr (!INWARP) {
             const int2 h = __ldg(a.walk.hdr + j.slot);
-            if (h.x < 0) return;  // warp-uniform: the INWARP kernel renders this ray
+            if (h.x < 0 || (RPL == 1 && h.x > kWalkCap)) return;  // warp-uniform: the mid-list or in-warp kernels
             by_rec = true;
             n_rec = h.x;
             S = __int_as_float(h.y);
             if (lane < n_rec) {
-                my_s0 = __ldg(a.walk.s0 + j.slot * kWalkCap + lane);
-                my_rec = __ldg(a.walk.rec + j.slot * kWalkCap + lane);
+                my_s0 = __ldg(a.walk.s0 + j.slot * kWalkSlot + lane);
+                my_rec = __ldg(a.walk.rec + j.slot * kWalkSlot + lane);
+            }
+            if constexpr (RPL == 2) {
+                if (lane + kWalkCap < n_rec) {
+                    my_s0b = __ldg(a.walk.s0 + j.slot * kWalkSlot + kWalkCap + lane);
+                    my_recb = __ldg(a.walk.rec + j.slot * kWalkSlot + kWalkCap + lane);
+                }
             }
         } else {
             S = walk_pieces(g, j, sm, lane, pc, t1);
         }
         if constexpr (kTrace) {
+            // the export keeps SDG_TRACE_CELLS = kWalkCap records: -1 for a ray with more
             if (lane == 0) {
                 a.tr_S[j.idx] = S;
-                a.tr_ncell[j.idx] = by_rec ? n_rec : -1;
+                a.tr_ncell[j.idx] = by_rec && n_rec <= kWalkCap ? n_rec : -1;
             }
-            if (a.tr_seg && by_rec && lane < n_rec) {
+            if (a.tr_seg && by_rec && n_rec <= kWalkCap && lane < n_rec) {
                 a.tr_seg[(j.idx * kWalkCap + lane) * 2] = __int_as_float(my_rec.x);
                 a.tr_seg[(j.idx * kWalkCap + lane) * 2 + 1] = __int_as_float(my_rec.y);
             }
@@ -704,30 +721,70 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
             // a time, the record's fields fetched again only when some lane moved
             const float sq = k < N ? s_[i] : 0.f;
             bool moved = i == 0;
-            if (i == 0) {
-                rm = 0;
+            if constexpr (RPL == 1) {
+                if (i == 0) {
+                    rm = 0;
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const float v = __shfl_sync(kFull, my_s0, rm + step);
-                    if (rm + step < n_rec && v <= sq) rm += step;
-                }
-            } else {
-                for (int it = 0; it < kWalkCap; ++it) {
-                    const float v = __shfl_sync(kFull, my_s0, rm + 1 < kWalkCap ? rm + 1 : kWalkCap - 1);
-                    const bool adv = rm + 1 < n_rec && v <= sq;
-                    if (!__any_sync(kFull, adv)) break;
-                    if (adv) {
-                        ++rm;
-                        moved = true;
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const float v = __shfl_sync(kFull, my_s0, rm + step);
+                        if (rm + step < n_rec && v <= sq) rm += step;
+                    }
+                } else {
+                    for (int it = 0; it < kWalkCap; ++it) {
+                        const float v = __shfl_sync(kFull, my_s0, rm + 1 < kWalkCap ? rm + 1 : kWalkCap - 1);
+                        const bool adv = rm + 1 < n_rec && v <= sq;
+                        if (!__any_sync(kFull, adv)) break;
+                        if (adv) {
+                            ++rm;
+                            moved = true;
+                        }
                     }
                 }
-            }
-            if (__any_sync(kFull, moved)) {
-                r_s0 = __shfl_sync(kFull, my_s0, rm);
-                r_tin = __int_as_float(__shfl_sync(kFull, my_rec.x, rm));
-                r_len = __int_as_float(__shfl_sync(kFull, my_rec.y, rm));
-                r_blk = __shfl_sync(kFull, my_rec.z, rm);
-                r_cell = __shfl_sync(kFull, my_rec.w, rm);
+                if (__any_sync(kFull, moved)) {
+                    r_s0 = __shfl_sync(kFull, my_s0, rm);
+                    r_tin = __int_as_float(__shfl_sync(kFull, my_rec.x, rm));
+                    r_len = __int_as_float(__shfl_sync(kFull, my_rec.y, rm));
+                    r_blk = __shfl_sync(kFull, my_rec.z, rm);
+                    r_cell = __shfl_sync(kFull, my_rec.w, rm);
+                }
+            } else {
+                // record r lives in lane r % 32, in its first (r < 32) or second register set: both shuffled, the
+                // caller's half selected
+                auto s0_of = [&](int r) {
+                    const float lo = __shfl_sync(kFull, my_s0, r & 31), hi = __shfl_sync(kFull, my_s0b, r & 31);
+                    return r < kWalkCap ? lo : hi;
+                };
+                if (i == 0) {
+                    rm = 0;
+#pragma unroll
+                    for (int step = 32; step > 0; step >>= 1) {
+                        const float v = s0_of(rm + step < kWalkSlot ? rm + step : kWalkSlot - 1);
+                        if (rm + step < n_rec && v <= sq) rm += step;
+                    }
+                } else {
+                    for (int it = 0; it < kWalkSlot; ++it) {
+                        const float v = s0_of(rm + 1 < kWalkSlot ? rm + 1 : kWalkSlot - 1);
+                        const bool adv = rm + 1 < n_rec && v <= sq;
+                        if (!__any_sync(kFull, adv)) break;
+                        if (adv) {
+                            ++rm;
+                            moved = true;
+                        }
+                    }
+                }
+                if (__any_sync(kFull, moved)) {
+                    const bool hi = rm >= kWalkCap;
+                    const int src = rm & 31;
+                    r_s0 = s0_of(rm);
+                    const int x0 = __shfl_sync(kFull, my_rec.x, src), x1 = __shfl_sync(kFull, my_recb.x, src);
+                    const int y0 = __shfl_sync(kFull, my_rec.y, src), y1 = __shfl_sync(kFull, my_recb.y, src);
+                    const int z0 = __shfl_sync(kFull, my_rec.z, src), z1 = __shfl_sync(kFull, my_recb.z, src);
+                    const int w0 = __shfl_sync(kFull, my_rec.w, src), w1 = __shfl_sync(kFull, my_recb.w, src);
+                    r_tin = __int_as_float(hi ? x1 : x0);
+                    r_len = __int_as_float(hi ? y1 : y0);
+                    r_blk = hi ? z1 : z0;
+                    r_cell = hi ? w1 : w0;
+                }
             }
             blk = r_blk;
             cell = r_cell;

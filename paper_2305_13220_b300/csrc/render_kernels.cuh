@@ -47,9 +47,10 @@ constexpr int render_blocks_per_sm() {
     return render_min_blocks<MODE, NSC, Q>() * kWarpsPerBlock / render_wpb<NSC, INWARP>();
 }
 
-// One warp per ray.  !INWARP: every slot, cells from the traversal pass's records (a slot without records is
-// skipped: k_render_overflow renders it).  INWARP: every slot, the warp walking its ray (a pass without traversal
-// records).  Kept apart, the records kernel needs no shared memory, which leaves L1 to the voxel gathers.
+// One warp per ray.  !INWARP: every slot, cells from the traversal pass's records (a slot with more than kWalkCap
+// is skipped: the mid- and overflow-list kernels render it).  INWARP: every slot, the warp walking its ray (a pass
+// without traversal records).  Kept apart, the records kernel needs no shared memory, which leaves L1 to the voxel
+// gathers.
 template <int MODE, bool BF16, int NSC, int Q, bool INWARP>
 __global__ void __launch_bounds__(32 * render_wpb<NSC, INWARP>(), (render_blocks_per_sm<MODE, NSC, Q, INWARP>()))
     k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
@@ -62,12 +63,31 @@ __global__ void __launch_bounds__(32 * render_wpb<NSC, INWARP>(), (render_blocks
     ray_program<MODE, BF16, NSC, Q, INWARP>(g, a, j, smem[INWARP ? warp : 0], lane);
 }
 
-// The first entries of the overflow list, one warp each (no loop, so the in-warp program keeps the registers of
-// the other in-warp kernels without spilling): as many as the grid's previous pass produced, so a scene where
-// many rays cross more than kWalkCap cells (a large apartment: 10%) renders them at full occupancy.
+// Rays beyond the records kernel, of a pass with traversal records: the mid list a.walk.mid[0, *a.walk.n_mid)
+// (kWalkCap + 1 .. kWalkSlot allocated cells, rendered from their records two per lane) and the overflow list
+// a.walk.over[0, *a.walk.n_over) (more cells, walked in-warp).  A long list -- longer than k_render_rest takes in
+// one turn, going by the length the grid's previous pass left in its pinned words (PassArgs::over_out) -- first
+// goes to a kernel with one warp per entry (no loop, so the program keeps the register budget of the records
+// kernel without spilling: full occupancy for a scene where many rays cross walls, a large apartment); what is
+// left of both lists (normally all of a short list, none of a long one) to k_render_rest, a grid of at most
+// kRestBlocks blocks striding over them that runs alone after the records kernel (2 blocks per SM, no spills).
+constexpr unsigned kRestBlocks = 296;
+
+template <int MODE, bool BF16, int NSC, int Q>
+__global__ void __launch_bounds__(32 * render_wpb<NSC, false>(), (render_blocks_per_sm<MODE, NSC, Q, false>()))
+    k_render_mid_list(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
+    __shared__ WarpSmem smem[1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * render_wpb<NSC, false>() + warp;
+    if (q >= (int64_t)__ldg(a.walk.n_mid)) return;  // warp-uniform
+    RayJob j;
+    load_job(g, rays, a.perm, ray_id0, (int64_t)__ldg(a.walk.mid + q), a.n, j);
+    ray_program<MODE, BF16, NSC, Q, false, 2>(g, a, j, smem[0], lane);
+}
+
 template <int MODE, bool BF16, int NSC, int Q>
 __global__ void __launch_bounds__(256, (render_min_blocks<MODE, NSC, Q>()))
-    k_render_list(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
+    k_render_over_list(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
     __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
@@ -77,24 +97,34 @@ __global__ void __launch_bounds__(256, (render_min_blocks<MODE, NSC, Q>()))
     ray_program<MODE, BF16, NSC, Q, true>(g, a, j, smem[warp], lane);
 }
 
-// The overflow list a.walk.over[0, *a.walk.n_over) of a pass with traversal records (the rays crossing more than
-// kWalkCap allocated cells, 0.15% of the room step's rays), walked in-warp by a grid of at most kOverflowBlocks
-// blocks striding over the list.  It runs alone after the records kernel, so it takes the registers that keep the
-// loop free of spills (2 blocks per SM) and a grid that is dispatched at once.
-constexpr unsigned kOverflowBlocks = 296;
-
 template <int MODE, bool BF16, int NSC, int Q>
-__global__ void __launch_bounds__(256, 2)
-    k_render_overflow(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a, int64_t first) {
+__global__ void __launch_bounds__(256, 2) k_render_rest(GridDev g, const float* __restrict__ rays, uint32_t ray_id0,
+                                                        PassArgs a, int64_t first_mid, int64_t first_over) {
     __shared__ WarpSmem smem[kWarpsPerBlock];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t end = (int64_t)__ldg(a.walk.n_over), stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    if (a.over_out && blockIdx.x == 0 && threadIdx.x == 0) *a.over_out = (int)end;  // the next pass's hint
-    for (int64_t q = first + (int64_t)blockIdx.x * kWarpsPerBlock + warp; q < end; q += stride) {
+    const int64_t n_mid = (int64_t)__ldg(a.walk.n_mid), n_over = (int64_t)__ldg(a.walk.n_over);
+    const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp, stride = (int64_t)gridDim.x * kWarpsPerBlock;
+    if (a.over_out && blockIdx.x == 0 && threadIdx.x == 0) {  // the next pass's hints
+        a.over_out[0] = (int)n_over;
+        a.over_out[1] = (int)n_mid;
+    }
+    for (int64_t q = first_mid + w; q < n_mid; q += stride) {
+        RayJob j;
+        load_job(g, rays, a.perm, ray_id0, (int64_t)__ldg(a.walk.mid + q), a.n, j);
+        ray_program<MODE, BF16, NSC, Q, false, 2>(g, a, j, smem[warp], lane);
+    }
+    for (int64_t q = first_over + w; q < n_over; q += stride) {
         RayJob j;
         load_job(g, rays, a.perm, ray_id0, (int64_t)__ldg(a.walk.over + q), a.n, j);
         ray_program<MODE, BF16, NSC, Q, true>(g, a, j, smem[warp], lane);
     }
+}
+
+// Blocks of a list kernel for a list the hint says is long (0: leave the list to k_render_rest).
+inline unsigned list_blocks(int64_t hint, int warps_per_block, unsigned cap) {
+    if (hint <= 2 * (int64_t)kRestBlocks * kWarpsPerBlock) return 0;
+    const int64_t want = hint + hint / 4 + 64;  // a margin for a longer list than the last pass's
+    return (unsigned)std::min<int64_t>((want + warps_per_block - 1) / warps_per_block, cap);
 }
 
 template <int MODE, bool BF16, int NSC, int Q>
@@ -103,17 +133,15 @@ int launch_one(const GridDev& gd, const float* rays, uint32_t id0, const PassArg
     constexpr bool kNoWalk = MODE == PASS_BWD_STORE;  // samples come from the forward's stored records
     if (kNoWalk || a.walk.hdr) {
         constexpr int R = render_wpb<NSC, false>();
-        k_render<MODE, BF16, NSC, Q, false><<<(unsigned)((a.n + R - 1) / R), 32 * R, 0, s>>>(gd, rays, id0, a);
+        const unsigned rblocks = (unsigned)((a.n + R - 1) / R);
+        k_render<MODE, BF16, NSC, Q, false><<<rblocks, 32 * R, 0, s>>>(gd, rays, id0, a);
         if constexpr (!kNoWalk) {
-            // a list longer than the strided kernel takes in one turn: entries [0, 8 * lb) one warp each, sized
-            // from the hint with a margin, the rest (normally none) by the strided kernel
-            const int64_t want = a.over_hint > 2 * (int64_t)kOverflowBlocks * kWarpsPerBlock
-                                     ? a.over_hint + a.over_hint / 4 + 64
-                                     : 0;
-            const unsigned lb = (unsigned)std::min<int64_t>((want + kWarpsPerBlock - 1) / kWarpsPerBlock, blocks);
-            if (lb) k_render_list<MODE, BF16, NSC, Q><<<lb, 256, 0, s>>>(gd, rays, id0, a);
-            k_render_overflow<MODE, BF16, NSC, Q><<<blocks < kOverflowBlocks ? blocks : kOverflowBlocks, 256, 0, s>>>(
-                gd, rays, id0, a, (int64_t)lb * kWarpsPerBlock);
+            const unsigned lm = list_blocks(a.mid_hint, R, rblocks);
+            const unsigned lo = list_blocks(a.over_hint, kWarpsPerBlock, blocks);
+            if (lm) k_render_mid_list<MODE, BF16, NSC, Q><<<lm, 32 * R, 0, s>>>(gd, rays, id0, a);
+            if (lo) k_render_over_list<MODE, BF16, NSC, Q><<<lo, 256, 0, s>>>(gd, rays, id0, a);
+            k_render_rest<MODE, BF16, NSC, Q><<<blocks < kRestBlocks ? blocks : kRestBlocks, 256, 0, s>>>(
+                gd, rays, id0, a, (int64_t)lm * R, (int64_t)lo * kWarpsPerBlock);
         }
     } else {
         k_render<MODE, BF16, NSC, Q, true><<<blocks, 256, 0, s>>>(gd, rays, id0, a);

@@ -71,9 +71,9 @@ __global__ void __launch_bounds__(256) k_serve_walk(const GridDev* __restrict__ 
     walk_ray_records(scenes[ch->scene], o, d, ch->tnear, ch->tfar, w, slot);
 }
 
-// The ray of batch slot `slot` rendered by one warp: from the traversal pass's records (OVER false) or walked
-// in-warp (OVER true).
-template <bool BF16, int Q, bool OVER>
+// The ray of batch slot `slot` rendered by one warp: from the traversal pass's records, RPL per lane (OVER false),
+// or walked in-warp (OVER true).
+template <bool BF16, int Q, bool OVER, int RPL = 1>
 __device__ __forceinline__ void serve_ray(const GridDev* scenes, const ChunkDesc* chunks, int chunk_rays,
                                           const WalkBufs& wb, int64_t slot, WarpSmem& sm, int lane) {
     const ChunkDesc* ch;
@@ -92,11 +92,11 @@ __device__ __forceinline__ void serve_ray(const GridDev* scenes, const ChunkDesc
     a.out_depth = ch->depth;
     a.out_opac = ch->opac;
     a.walk = wb;
-    ray_program<PASS_FWD, BF16, 0, Q, OVER>(scenes[ch->scene], a, j, sm, lane);
+    ray_program<PASS_FWD, BF16, 0, Q, OVER, RPL>(scenes[ch->scene], a, j, sm, lane);
 }
 
 // One warp per slot of the batch, cells from the traversal pass's records (a slot without records is left to
-// k_serve_overflow).  Blocks of kServeWarps warps, 6 per SM at 4 samples per lane (80 registers), 4 above.
+// k_serve_rest).  Blocks of kServeWarps warps, 6 per SM at 4 samples per lane (80 registers), 4 above.
 constexpr int kServeWarps = 4;
 
 template <bool BF16, int Q>
@@ -107,20 +107,24 @@ __global__ void __launch_bounds__(32 * kServeWarps, (Q <= 4 ? 6 : 4))
     serve_ray<BF16, Q, false>(scenes, chunks, chunk_rays, wb, slot, smem[0], threadIdx.x & 31);
 }
 
-// The batch's overflow list (rays crossing more than kWalkCap allocated cells), walked in-warp by a grid of at
-// most kServeOverflowBlocks blocks striding over the list; it runs alone after the records kernel on the batch's
-// stream, so it takes the registers that keep the loop free of spills.
-constexpr unsigned kServeOverflowBlocks = 296;
+// The batch's rays beyond the records kernel: the mid list (kWalkCap + 1 .. kWalkSlot allocated cells, from their
+// records two per lane), then the overflow list (more cells, walked in-warp), by a grid of at most
+// kServeRestBlocks blocks striding over them; it runs alone after the records kernel on the batch's stream, so it
+// takes the registers that keep the loops free of spills (2 blocks per SM).
+constexpr unsigned kServeRestBlocks = 296;
 
 template <bool BF16, int Q>
 __global__ void __launch_bounds__(256, 2)
-    k_serve_overflow(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks, int chunk_rays,
-                     WalkBufs wb) {
+    k_serve_rest(const GridDev* __restrict__ scenes, const ChunkDesc* __restrict__ chunks, int chunk_rays,
+                 WalkBufs wb) {
     __shared__ WarpSmem smem[kWarpsPerBlock];
-    const int warp = threadIdx.x >> 5;
-    const int64_t end = (int64_t)__ldg(wb.n_over), stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t q = (int64_t)blockIdx.x * kWarpsPerBlock + warp; q < end; q += stride)
-        serve_ray<BF16, Q, true>(scenes, chunks, chunk_rays, wb, __ldg(wb.over + q), smem[warp], threadIdx.x & 31);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n_mid = (int64_t)__ldg(wb.n_mid), n_over = (int64_t)__ldg(wb.n_over);
+    const int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + warp, stride = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t q = w; q < n_mid; q += stride)
+        serve_ray<BF16, Q, false, 2>(scenes, chunks, chunk_rays, wb, __ldg(wb.mid + q), smem[warp], lane);
+    for (int64_t q = w; q < n_over; q += stride)
+        serve_ray<BF16, Q, true>(scenes, chunks, chunk_rays, wb, __ldg(wb.over + q), smem[warp], lane);
 }
 
 double now_ms() {
@@ -350,14 +354,14 @@ struct sdg_server_s {
             const int64_t nslots = (int64_t)nch * o.chunk_rays;
             const unsigned blocks = (unsigned)((nslots + kWarpsPerBlock - 1) / kWarpsPerBlock);
             const int Q = pick_q(maxN);
-            cudaMemsetAsync(wb.n_over, 0, sizeof(int), b->stream);
+            cudaMemsetAsync(wb.n_over, 0, 2 * sizeof(int), b->stream);  // n_over and n_mid
             k_serve_walk<<<(unsigned)((nslots + 255) / 256), 256, 0, b->stream>>>(b->d_scenes, b->d_chunks,
                                                                                    o.chunk_rays, nslots, wb);
 #define SDG_SERVE(BF, QQ)                                                                                      \
     do {                                                                                                       \
         k_serve<BF, QQ><<<(unsigned)((nslots + kServeWarps - 1) / kServeWarps), 32 * kServeWarps, 0, b->stream>>>(  \
             b->d_scenes, b->d_chunks, o.chunk_rays, wb);                                                       \
-        k_serve_overflow<BF, QQ><<<std::min(blocks, kServeOverflowBlocks), 256, 0, b->stream>>>(                \
+        k_serve_rest<BF, QQ><<<std::min(blocks, kServeRestBlocks), 256, 0, b->stream>>>(                        \
             b->d_scenes, b->d_chunks, o.chunk_rays, wb);                                                       \
     } while (0)
             if (bf16) {
@@ -441,17 +445,20 @@ extern "C" int sdg_server_create(const sdg_server_opts* o, sdg_server* out) {
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cleanup(cuda_fail(e, "server stream"));
         s->streams.push_back(st);
-        // traversal records for max_batch_rays slots: 8 + kWalkCap * 20 bytes a slot, and the overflow list
+        // traversal records for max_batch_rays slots: 8 + kWalkSlot * 20 bytes a slot, the overflow and mid lists
+        // and their lengths (one allocation: over [R], mid [R], n_over, n_mid)
         const int64_t R = o->max_batch_rays;
         WalkBufs w{};
         if ((e = cudaMalloc((void**)&w.hdr, sizeof(int2) * R)) != cudaSuccess ||
-            (e = cudaMalloc((void**)&w.s0, sizeof(float) * kWalkCap * R)) != cudaSuccess ||
-            (e = cudaMalloc((void**)&w.rec, sizeof(int4) * kWalkCap * R)) != cudaSuccess ||
-            (e = cudaMalloc((void**)&w.over, sizeof(int) * (R + 1))) != cudaSuccess) {
+            (e = cudaMalloc((void**)&w.s0, sizeof(float) * kWalkSlot * R)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&w.rec, sizeof(int4) * kWalkSlot * R)) != cudaSuccess ||
+            (e = cudaMalloc((void**)&w.over, sizeof(int) * (2 * R + 2))) != cudaSuccess) {
             s->walk.push_back(w);
             return cleanup(cuda_fail(e, "server traversal records"));
         }
-        w.n_over = w.over + R;
+        w.mid = w.over + R;
+        w.n_over = w.over + 2 * R;
+        w.n_mid = w.over + 2 * R + 1;
         s->walk.push_back(w);
     }
     const int max_chunks = o->max_batch_rays / o->chunk_rays;

@@ -1,7 +1,9 @@
-"""Rays crossing more allocated block cells than a traversal record holds (32): a pass whose overflow list is longer
-than the strided overflow kernel takes in one turn renders its first entries with one warp each (sized from the
-list length the grid's previous pass left), the rest with the strided kernel.  Both paths run the same in-warp
-program, so the outputs equal the trace's (strided kernel) bit for bit, and the oracle over the trace's samples."""
+"""Rays crossing more allocated block cells than the records kernel takes (32): with up to 64 they are rendered from
+their records two per lane (the mid list), with more walked in-warp (the overflow list).  A slab of 40 blocks sends
+every ray to the mid list, one of 80 to the overflow list; there a pass whose list is longer than the strided
+overflow kernel takes in one turn renders its first entries with one warp each (sized from the list length the
+grid's previous pass left), the rest with the strided kernel.  The outputs equal the trace's bit for bit (the
+trace takes the strided kernels), and the oracle over the trace's samples."""
 import numpy as np
 import pytest
 import torch
@@ -15,17 +17,18 @@ pytestmark = pytest.mark.gpu
 N = 64
 
 
-@pytest.fixture(scope="module")
-def slab():
+@pytest.fixture(scope="module", params=[40, 80], ids=["mid-list", "overflow-list"])
+def slab(request):
     import paper_2305_13220_b300 as sdg
-    # 40 x 3 x 3 allocated blocks (0.04 m voxels, 0.32 m blocks) viewed down x from one end through a narrow field
-    # of view: every ray crosses about 41 cells
-    sc = synth.scene_room(0, size=(13.0, 2.0, 2.0), n_objects=0)
-    keys = np.array([(x, y, z) for x in range(40) for y in range(3) for z in range(3)], np.int32)
+    # L x 3 x 3 allocated blocks (0.04 m voxels, 0.32 m blocks) viewed down x from one end through a narrow field
+    # of view: every ray crosses about L + 1 cells
+    L = request.param
+    sc = synth.scene_room(0, size=(0.32 * L + 1.0, 2.0, 2.0), n_objects=0)
+    keys = np.array([(x, y, z) for x in range(L) for y in range(3) for z in range(3)], np.int32)
     G, O, _, _ = make_pair(sc, keys, 0.04, 3, 0.02, "f32")
     T = np.array([[0.0, 0.0, 1.0, 0.1], [1.0, 0.0, 0.0, 0.48], [0.0, 1.0, 0.0, 0.48]])
     W = H = 80  # 6,400 rays, more than the strided kernel's 4,736 warps
-    rays = synth.view_rays(T, W, H, synth.intrinsics(W, H, fov_deg=2.0))
+    rays = synth.view_rays(T, W, H, synth.intrinsics(W, H, fov_deg=1.5))
     return sdg, G, O, rays
 
 

@@ -140,10 +140,10 @@ def test_served_grid_structure_is_fixed(sdg):
 
 
 def test_served_rays_beyond_the_record_capacity(sdg):
-    """Rays that cross more allocated block cells than a traversal record holds (32) are rendered by the serving
-    loop's in-warp kernel over the overflow list, as sdg_debug_trace_view renders them: a view down a slab of
-    40 x 3 x 3 allocated blocks equals its trace bit for bit, and the oracle over the trace's samples on every
-    pixel."""
+    """Rays that cross more allocated block cells than the records kernel takes (32) are rendered by the serving
+    loop's kernel over the mid list (their records two per lane), as sdg_debug_trace_view renders them: a view down
+    a slab of 40 x 3 x 3 allocated blocks equals its trace bit for bit, and the oracle over the trace's samples on
+    every pixel."""
     sc = synth.scene_room(0, size=(13.0, 2.0, 2.0), n_objects=0)
     keys = np.array([(x, y, z) for x in range(40) for y in range(3) for z in range(3)], np.int32)
     G, O, stored, vals = make_pair(sc, keys, 0.04, 3, 0.02, "bf16")
@@ -160,7 +160,7 @@ def test_served_rays_beyond_the_record_capacity(sdg):
     assert torch.equal(tr["rgb"].reshape(rgb.shape), rgb) and torch.equal(tr["depth"].reshape(depth.shape), depth)
     assert torch.equal(tr["opac"].reshape(opac.shape), opac)
     n_over = int((tr["n_cells"] < 0).sum())
-    assert n_over >= H * W // 4, n_over  # the overflow kernel rendered a good part of the view
+    assert n_over >= H * W // 4, n_over  # a good part of the view beyond the records kernel (trace: n_cells -1)
     rays = tr["rays"].cpu().numpy()
     check_placement(O, rays, tr, 64, seed=5)
     ref = O.render(rays, 64, seed=5, given=gpu_samples(tr))
