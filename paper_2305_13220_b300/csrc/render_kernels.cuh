@@ -54,6 +54,8 @@ constexpr int render_blocks_per_sm() {
 template <int MODE, bool BF16, int NSC, int Q, bool INWARP>
 __global__ void __launch_bounds__(32 * render_wpb<NSC, INWARP>(), (render_blocks_per_sm<MODE, NSC, Q, INWARP>()))
     k_render(GridDev g, const float* __restrict__ rays, uint32_t ray_id0, PassArgs a) {
+    // the semantic records program keeps a voxel table per warp for at most kWarpsPerBlock warps
+    static_assert(render_wpb<NSC, INWARP>() <= kWarpsPerBlock, "warps per block");
     __shared__ WarpSmem smem[INWARP ? kWarpsPerBlock : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * render_wpb<NSC, INWARP>() + warp;

@@ -22,7 +22,7 @@ def test_parity_suite_under_bounds_checks():
     files = ["tests/test_gpu_render.py", "tests/test_gpu_fullsize.py", "tests/test_gpu_serve.py",
              "tests/test_gpu_normal.py", "tests/test_gpu_beta_ssi.py", "tests/test_gpu_query.py",
              "tests/test_gpu_ray_order.py", "tests/test_gpu_adam.py", "tests/test_gpu_activation.py",
-             "tests/test_gpu_overflow.py", "tests/test_gpu_prepare.py"]
+             "tests/test_gpu_overflow.py", "tests/test_gpu_prepare.py", "tests/test_gpu_sem_table.py"]
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider", *files],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
     tail = "\n".join((r.stdout + r.stderr).strip().splitlines()[-15:])
