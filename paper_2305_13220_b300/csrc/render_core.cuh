@@ -1182,15 +1182,21 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     constexpr bool kTab = SEM && !INWARP && RPL == 1;
     constexpr int kTabSlots = 512;
     __shared__ __align__(16) int tab_key[kTab ? kWarpsPerBlock : 1][kTab ? kTabSlots : 1];
-    __shared__ __align__(16) float2 tab_val[kTab ? kWarpsPerBlock : 1][kTab ? kTabSlots : 1];
+    // the two sums in arrays of their own, so that a slot's atomics fall in 32 banks rather than the 16 even ones of
+    // an interleaved pair (5.57 -> 5.53 ms)
+    __shared__ __align__(16) float tab_s[kTab ? kWarpsPerBlock : 1][kTab ? kTabSlots : 1];
+    __shared__ __align__(16) float tab_w[kTab ? kWarpsPerBlock : 1][kTab ? kTabSlots : 1];
     const int wib = kTab ? (threadIdx.x >> 5) : 0;
     if constexpr (kTab) {
         int4* k4 = reinterpret_cast<int4*>(tab_key[wib]);
-        float4* v4 = reinterpret_cast<float4*>(tab_val[wib]);
+        float4* s4 = reinterpret_cast<float4*>(tab_s[wib]);
+        float4* w4 = reinterpret_cast<float4*>(tab_w[wib]);
 #pragma unroll
-        for (int u = 0; u < kTabSlots / 128; ++u) k4[lane + 32 * u] = make_int4(-1, -1, -1, -1);
-#pragma unroll
-        for (int u = 0; u < kTabSlots / 64; ++u) v4[lane + 32 * u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < kTabSlots / 128; ++u) {
+            k4[lane + 32 * u] = make_int4(-1, -1, -1, -1);
+            s4[lane + 32 * u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            w4[lane + 32 * u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         __syncwarp();
     }
     // the gradients of one voxel from sums (as, aw) over runs
@@ -1251,8 +1257,8 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                         for (int probe = 0; probe < 32; ++probe) {
                             const int old = atomicCAS(&tab_key[wib][h], -1, key);
                             if (old == -1 || old == key) {
-                                atomicAdd(&tab_val[wib][h].x, aS[e]);
-                                atomicAdd(&tab_val[wib][h].y, aW[e]);
+                                atomicAdd(&tab_s[wib][h], aS[e]);
+                                atomicAdd(&tab_w[wib][h], aW[e]);
                                 done = true;
                                 break;
                             }
@@ -1273,10 +1279,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 #pragma unroll 1
                 for (int u = lane; u < kTabSlots; u += 32) {
                     const int key = tab_key[wib][u];
-                    if (key >= 0) {
-                        const float2 v = tab_val[wib][u];
-                        scatter_voxel(key, v.x, v.y);
-                    }
+                    if (key >= 0) scatter_voxel(key, tab_s[wib][u], tab_w[wib][u]);
                 }
             }
         } else {
