@@ -34,7 +34,9 @@ LAMBDA_D = 0.1
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=50,
+                   help="timed steps (50 room steps are about 80 ms of device time, so that one stalled step moves "
+                        "the mean by little)")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--rays", type=int, default=1 << 18)
