@@ -1229,6 +1229,11 @@ def run_crf(args):
 
 def main():
     args = parse()
+    single = {"room_bf16_sem", "serve", "apartment", "fusion", "query", "crf"}
+    if args.impl != "reference" and args.config in single and int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        # one-GPU measurements: under a multi-process launch rank 0 runs them (on its own GPU), the others exit
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "room_bf16_sem":

@@ -41,3 +41,23 @@ def test_single_process_is_identity():
     import bench
     assert bench.reduce_max(4.5) == 4.5
     assert bench.aggregate_rays_per_s(1, 1000, 2.0) == 500000.0
+
+
+def test_one_gpu_configs_run_on_rank_zero_only(monkeypatch):
+    """The precision, serving, apartment, fusion, query and CRF measurements are one-GPU runs: under a
+    multi-process launch every rank but 0 returns without measuring."""
+    import sys
+    import bench
+    called = []
+    for name in ("run_precision", "run_serve", "run_apartment", "run_fusion", "run_query", "run_crf"):
+        monkeypatch.setattr(bench, name, lambda args, n=name: called.append(n))
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    for cfg in ("room_bf16_sem", "serve", "apartment", "fusion", "query", "crf"):
+        monkeypatch.setattr(sys, "argv", ["bench.py", "--config", cfg])
+        monkeypatch.setenv("RANK", "1")
+        bench.main()
+        assert called == []
+        monkeypatch.setenv("RANK", "0")
+        bench.main()
+        assert len(called) == 1
+        called.clear()
