@@ -1184,7 +1184,10 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
     __shared__ __align__(16) int tab_key[kTab ? kWarpsPerBlock : 1][kTab ? kTabSlots : 1];
     // the two sums in arrays of their own, so that a slot's atomics fall in 32 banks rather than the 16 even ones of
     // an interleaved pair (5.57 -> 5.53 ms)
-    __shared__ __align__(16) float tab_s[kTab ? kWarpsPerBlock : 1][kTab ? kTabSlots : 1];
+    // With BF16 colour the SDF gradient has an array of its own: a run's SDF seeds go straight to it with scalar
+    // atomics and the table keeps only the weights, one shared-memory atomic less per corner (5.53 -> 5.34 ms)
+    constexpr bool kTabS = kTab && !BF16;
+    __shared__ __align__(16) float tab_s[kTabS ? kWarpsPerBlock : 1][kTabS ? kTabSlots : 1];
     __shared__ __align__(16) float tab_w[kTab ? kWarpsPerBlock : 1][kTab ? kTabSlots : 1];
     const int wib = kTab ? (threadIdx.x >> 5) : 0;
     if constexpr (kTab) {
@@ -1194,17 +1197,17 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 #pragma unroll
         for (int u = 0; u < kTabSlots / 128; ++u) {
             k4[lane + 32 * u] = make_int4(-1, -1, -1, -1);
-            s4[lane + 32 * u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (kTabS) s4[lane + 32 * u] = make_float4(0.f, 0.f, 0.f, 0.f);
             w4[lane + 32 * u] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncwarp();
     }
-    // the gradients of one voxel from sums (as, aw) over runs
-    auto scatter_voxel = [&](int ad, float as_, float aw_) {
+    // the gradients of one voxel from sums (as, aw) over runs (sdf false: its SDF seed already sent)
+    auto scatter_voxel = [&](int ad, float as_, float aw_, bool sdf = true) {
         if constexpr (!BF16) {
             red_add_v4(g.ggeo + ad, as_, gC0 * aw_, gC1 * aw_, gC2 * aw_);
         } else {
-            atomicAdd(g.gsdf + ad, as_);
+            if (sdf) atomicAdd(g.gsdf + ad, as_);
             red_add_v4(g.grgb + ad, gC0 * aw_, gC1 * aw_, gC2 * aw_, 0.f);
         }
         if (SEM && sem_grad) {
@@ -1252,19 +1255,20 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
                 for (int e = 0; e < 8; ++e) {
                     if constexpr (kTab) {
                         const int key = addr[e];
+                        if constexpr (!kTabS) atomicAdd(g.gsdf + key, aS[e]);
                         unsigned h = ((unsigned)key * 2654435761u) >> 23;  // 9 bits: kTabSlots = 512
                         bool done = false;
                         for (int probe = 0; probe < 32; ++probe) {
                             const int old = atomicCAS(&tab_key[wib][h], -1, key);
                             if (old == -1 || old == key) {
-                                atomicAdd(&tab_s[wib][h], aS[e]);
+                                if constexpr (kTabS) atomicAdd(&tab_s[wib][h], aS[e]);
                                 atomicAdd(&tab_w[wib][h], aW[e]);
                                 done = true;
                                 break;
                             }
                             h = (h + 1) & (kTabSlots - 1);
                         }
-                        if (!done) scatter_voxel(key, aS[e], aW[e]);  // a crowded table: straight to memory
+                        if (!done) scatter_voxel(key, aS[e], aW[e], kTabS);  // a crowded table: straight to memory
                     } else {
                         scatter_voxel(addr[e], aS[e], aW[e]);
                     }
@@ -1279,7 +1283,7 @@ __device__ __forceinline__ void ray_program(const GridDev& g, const PassArgs& a,
 #pragma unroll 1
                 for (int u = lane; u < kTabSlots; u += 32) {
                     const int key = tab_key[wib][u];
-                    if (key >= 0) scatter_voxel(key, tab_s[wib][u], tab_w[wib][u]);
+                    if (key >= 0) scatter_voxel(key, kTabS ? tab_s[wib][u] : 0.f, tab_w[wib][u], kTabS);
                 }
             }
         } else {
